@@ -1,0 +1,171 @@
+/*
+ * nasch.h: C ABI of the GB300 (sm_103a) Nagel-Schreckenberg library.
+ *
+ * The operation is the synchronous time step of the 1-D Nagel-Schreckenberg
+ * model on a ring road of L cells (van Zon & Ponce, "Parallelizing a 1-Dim
+ * Nagel-Schreckenberg Traffic Model", EduHPC-23; Handout, "The
+ * Nagel-Schreckenberg traffic model", rules 1-4), applied to every car at
+ * once:
+ *     v <- min(v + 1, vmax)                      rule 1, accelerate
+ *     v <- min(v, d - 1), d = headway ahead      rule 2, brake
+ *     v <- max(v - 1, 0) with probability p      rule 3, random slowdown
+ *     x <- (x + v) mod L                         rule 4, move on the ring
+ * The model's parameters are those of the handout's parameter file
+ * (Handout, "Starter Code": L, T, N, p, vmax, seed).
+ *
+ * Randomness.  The rule-3 draw of the car that sits on cell c at the start
+ * of step t is word 0 of Philox4x32-10 (Salmon et al., SC'11) of counter
+ * (c, t mod 2^32, road_id, 0) under key (seed mod 2^32, seed >> 32); the car
+ * slows down iff that word is below ceil(p * 2^32).  That is the handout's
+ * "draw r uniform on [0,1), slow down iff r < p" with r = word * 2^-32, and
+ * it makes every result independent of how the work is split over threads,
+ * tiles, launches or batches (the assignment's reproducibility requirement,
+ * item 1).  Initial positions are N distinct cells chosen by Floyd's
+ * algorithm from Philox counters (m, 0, road_id, 1), sorted; all v = 0.
+ *
+ * Representations ("Concepts Covered"): agent-based (int32 positions x[N],
+ * uint8 velocities v[N], cars in cyclic order, the car ahead of car i is car
+ * (i+1) mod N) and grid (int8 cells[L], -1 empty, else the velocity of the
+ * car on that cell).  Both give identical results.
+ *
+ * Statistics.  Every step records two exact integers: sum_v, the sum of the
+ * velocities used for the move (flux J = sum_v / L, mean velocity
+ * sum_v / N), and crossings, the number of cars whose move passes from cell
+ * L-1 to cell 0.
+ *
+ * Conventions.
+ *   - Every function returns NASCH_OK (0) or a negative status; on error,
+ *     nasch_last_error() returns a message for the calling thread.  No C++
+ *     exception crosses this interface.
+ *   - Pointers named *_host are caller-owned host memory; the library copies
+ *     from or into them and keeps no reference.  Device state is owned by
+ *     the library and freed by nasch_destroy / nasch_batch_destroy.
+ *   - Work is enqueued on the handle's CUDA stream and runs asynchronously;
+ *     functions that return results to the host synchronise that stream.
+ *   - Limits: 1 <= L <= 2^31, 0 <= N <= L, 0 <= vmax <= 127, 0 <= p <= 1
+ *     (p = 1 always slows a moving car down).  Anything else is
+ *     NASCH_EINVAL.
+ *   - A handle is not thread-safe; distinct handles may be used from
+ *     distinct threads.
+ */
+#ifndef NASCH_H
+#define NASCH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define NASCH_OK 0
+#define NASCH_EINVAL (-1)    /* invalid argument or state */
+#define NASCH_ENOMEM (-2)    /* device or host allocation failed, or budget exceeded */
+#define NASCH_ECUDA (-3)     /* a CUDA runtime call failed (message has the CUDA error) */
+#define NASCH_ETIMEOUT (-4)  /* a bounded wait ran out; the work is still in flight */
+#define NASCH_EBUSY (-5)     /* the object is in use by enqueued work */
+#define NASCH_ECANCELED (-6) /* the batch or request was cancelled */
+
+/* State layouts. */
+#define NASCH_LAYOUT_AUTO 0  /* agent below the crossover density, grid above */
+#define NASCH_LAYOUT_AGENT 1
+#define NASCH_LAYOUT_GRID 2
+
+typedef struct nasch_road *nasch_handle;
+typedef struct nasch_batch_s *nasch_batch;
+
+/* Parameters of one road.  Fill with nasch_params_init, then set fields. */
+typedef struct nasch_params {
+    int64_t L;        /* ring length in cells, 1..2^31 */
+    int64_t N;        /* number of cars, 0..L */
+    int32_t vmax;     /* maximum velocity, 0..127 */
+    double p;         /* slowdown probability, 0..1 */
+    uint64_t seed;    /* Philox key */
+    uint32_t road_id; /* Philox counter word 2: distinguishes roads sharing a seed */
+    int32_t layout;   /* NASCH_LAYOUT_* */
+    int32_t k;        /* steps fused per launch (temporal blocking); 0 = library choice */
+    int32_t tile;     /* cars (agent) or cells (grid) per tile; 0 = library choice */
+    void *stream;     /* cudaStream_t to enqueue on; NULL = a stream owned by the handle */
+} nasch_params;
+
+/* Read-only description of a handle. */
+typedef struct nasch_info {
+    int64_t L, N;
+    int32_t vmax;
+    int32_t layout;       /* NASCH_LAYOUT_AGENT or NASCH_LAYOUT_GRID, as resolved */
+    int32_t k;            /* fusion depth in use */
+    int32_t tile;         /* tile in use (cars or cells) */
+    uint64_t step;        /* global index of the next step to run */
+    uint64_t stats_first; /* first step whose statistics are kept */
+    uint64_t threshold;   /* ceil(p * 2^32) */
+    int32_t ring_kernel;  /* 1 if the whole ring runs in one thread block */
+    int32_t blocks;       /* thread blocks of the tiled kernel (persistent grid) */
+} nasch_info;
+
+/* Defaults: L = N = 0, vmax = 5, p = 0, seed = 0, road 0, AUTO, k = tile = 0, stream NULL. */
+void nasch_params_init(nasch_params *prm);
+
+/* Create one road with Floyd-sampled start positions and v = 0 at step 0
+ * (Handout, "Starter Code": cars start from random positions on a ring).
+ * Allocates the device state on the current CUDA device. */
+int nasch_create(int64_t L, int64_t N, int vmax, double p, uint64_t seed, nasch_handle *out);
+
+/* As nasch_create with every parameter of nasch_params. */
+int nasch_create_ex(const nasch_params *prm, nasch_handle *out);
+
+/* Replace the state: N cars (N must equal the handle's N) at positions
+ * x_host[0..N-1] (distinct, in [0, L), in cyclic order: a rotation of an
+ * increasing sequence) with velocities v_host[0..N-1] <= vmax; the next
+ * step run is `step`.  Statistics kept so far are dropped.  Copies the host
+ * arrays to the device on the handle's stream and returns once the copy is
+ * complete. */
+int nasch_set_state(nasch_handle h, const int32_t *x_host, const uint8_t *v_host, int64_t N,
+                    uint64_t step);
+
+/* Enqueue `steps` synchronous time steps (each: rules 1-4 for every car,
+ * then the per-step sum_v and crossings).  Asynchronous. */
+int nasch_run(nasch_handle h, int64_t steps);
+
+/* Copy the current state to the host.  Agent layout: cars in their cyclic
+ * order.  Grid layout: cars in increasing cell order.  cap is the capacity
+ * of both arrays in elements and must be >= N.  Synchronises the stream. */
+int nasch_read_state(nasch_handle h, int32_t *x_host, uint8_t *v_host, int64_t cap);
+
+/* Copy the current state as a grid (cells_host[0..L-1], -1 empty, else the
+ * velocity).  cap must be >= L.  Synchronises the stream. */
+int nasch_read_grid(nasch_handle h, int8_t *cells_host, int64_t cap);
+
+/* Copy the statistics of steps first_step .. first_step+count-1 (global
+ * step indices; they must lie between nasch_info.stats_first and the
+ * current step).  Either output may be NULL.  Synchronises the stream. */
+int nasch_stats(nasch_handle h, uint64_t first_step, int64_t count, uint64_t *sum_v_host,
+                uint64_t *crossings_host);
+
+int nasch_get_info(nasch_handle h, nasch_info *info);
+
+/* Block until all work enqueued on the handle has finished. */
+int nasch_synchronize(nasch_handle h);
+
+/* Free the handle and its device memory (synchronises first).  NULL is a no-op. */
+void nasch_destroy(nasch_handle h);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char *nasch_last_error(void);
+
+/* The library's slowdown threshold ceil(p * 2^32) (2^32 for p = 1). */
+uint64_t nasch_slow_threshold(double p);
+
+/* The library's Floyd initialisation on the host: N sorted distinct cells of
+ * the ring for (seed, road_id), written to x_host[0..N-1]. */
+int nasch_floyd_init(int64_t L, int64_t N, uint64_t seed, uint32_t road_id, int32_t *x_host);
+
+/* Philox4x32-10 evaluated by the library's device code, for testing: for
+ * i < n, out_host[4i..4i+3] = Philox(ctr_host[4i..4i+3], key (seed lo, seed
+ * hi)).  Runs one kernel and synchronises. */
+int nasch_philox_device(int64_t n, const uint32_t *ctr_host, uint64_t seed, uint32_t *out_host);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NASCH_H */

@@ -1,0 +1,90 @@
+// Device primitives of the NaSch step: Philox4x32-10 in registers and the
+// per-car application of the four rules (Handout, "The Nagel-Schreckenberg
+// traffic model", rules 1-4).
+#pragma once
+
+#include <stdint.h>
+
+namespace nasch {
+
+// Philox4x32-10 constants (Salmon, Moraes, Dror & Shaw, SC'11): the two round
+// multipliers and the two Weyl increments of the key schedule.
+constexpr uint32_t kMulA = 0xD2511F53u;
+constexpr uint32_t kMulB = 0xCD9E8D57u;
+constexpr uint32_t kWeylA = 0x9E3779B9u;
+constexpr uint32_t kWeylB = 0xBB67AE85u;
+
+// Counter word 3 separates the library's two uses of the stream.
+constexpr uint32_t kTagSlowdown = 0u;
+constexpr uint32_t kTagInit = 1u;
+
+struct Words4 {
+    uint32_t w0, w1, w2, w3;
+};
+
+// Full Philox4x32-10; usable on host (Floyd initialisation) and device.
+__host__ __device__ __forceinline__ Words4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2,
+                                                         uint32_t c3, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        const uint64_t pa = (uint64_t)kMulA * c0;
+        const uint64_t pb = (uint64_t)kMulB * c2;
+        const uint32_t n0 = (uint32_t)(pb >> 32) ^ c1 ^ k0;
+        const uint32_t n2 = (uint32_t)(pa >> 32) ^ c3 ^ k1;
+        c1 = (uint32_t)pb;
+        c3 = (uint32_t)pa;
+        c0 = n0;
+        c2 = n2;
+        k0 += kWeylA;
+        k1 += kWeylB;
+    }
+    return Words4{c0, c1, c2, c3};
+}
+
+// Word 0 only, as the rule-3 draw needs.  The last round needs just the high
+// half of one product; the compiler drops the rest.
+__device__ __forceinline__ uint32_t philox_word0(uint32_t c0, uint32_t c1, uint32_t c2,
+                                                 uint32_t c3, uint32_t k0, uint32_t k1)
+{
+    return philox4x32_10(c0, c1, c2, c3, k0, k1).w0;
+}
+
+// Parameters every step kernel shares.
+struct RoadConst {
+    uint32_t L;        // ring length, 1..2^31
+    uint32_t vmax;     // 0..127
+    uint64_t thr;      // ceil(p * 2^32): 0 never slows, 2^32 always slows
+    uint32_t key0;     // seed low word
+    uint32_t key1;     // seed high word
+    uint32_t road;     // Philox counter word 2
+};
+
+// Rule 3 for the car on `cell` at the start of `step`.
+__device__ __forceinline__ bool slows_down(const RoadConst &rc, uint32_t cell, uint32_t step)
+{
+    if (rc.thr == 0) return false;
+    if (rc.thr > 0xFFFFFFFFull) return true;
+    return philox_word0(cell, step, rc.road, kTagSlowdown, rc.key0, rc.key1) < (uint32_t)rc.thr;
+}
+
+// Rules 1-3 for one car with velocity v and `gap` empty cells ahead (gap =
+// headway - 1); returns the velocity used by rule 4.
+__device__ __forceinline__ uint32_t new_velocity(const RoadConst &rc, uint32_t v, uint32_t gap,
+                                                 uint32_t cell, uint32_t step)
+{
+    uint32_t vel = min(v + 1u, rc.vmax);   // rule 1
+    vel = min(vel, gap);                    // rule 2
+    if (vel > 0u && slows_down(rc, cell, step)) vel -= 1u;   // rule 3
+    return vel;
+}
+
+// Empty cells between a car at x and the car ahead at `lead` on the ring
+// (positions in [0, L)); a car that is its own leader sees L - 1.
+__device__ __forceinline__ uint32_t agent_gap(uint32_t x, uint32_t lead, uint32_t L)
+{
+    const uint32_t headway = lead > x ? lead - x : lead + L - x;   // in [1, L]
+    return headway - 1u;
+}
+
+}  // namespace nasch

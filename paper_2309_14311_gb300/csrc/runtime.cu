@@ -1,0 +1,627 @@
+// C-ABI runtime of the NaSch library: road handles, argument validation,
+// device memory, the per-step statistics series, launch planning (layout,
+// fusion depth, whole-ring vs tiled kernel) and the host-side Floyd
+// initialisation.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/nasch.h"
+#include "kernels.h"
+#include "runtime_internal.h"
+
+namespace nasch {
+
+static thread_local std::string g_last_error;
+
+int fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what)
+{
+    return fail(NASCH_ECUDA, "%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));
+}
+
+void clear_error() { g_last_error.clear(); }
+
+uint64_t slow_threshold(double p)
+{
+    // r = u * 2^-32 < p  <=>  u < ceil(p * 2^32); the scaling by 2^32 is exact.
+    if (!(p > 0.0)) return 0;
+    if (p >= 1.0) return 1ull << 32;
+    return (uint64_t)std::ceil(std::ldexp(p, 32));
+}
+
+int validate_params(const nasch_params *prm)
+{
+    if (!prm) return fail(NASCH_EINVAL, "params is NULL");
+    if (prm->L < 1 || prm->L > (int64_t(1) << 31))
+        return fail(NASCH_EINVAL, "L=%lld outside 1..2^31", (long long)prm->L);
+    if (prm->N < 0 || prm->N > prm->L)
+        return fail(NASCH_EINVAL, "N=%lld outside 0..L=%lld", (long long)prm->N, (long long)prm->L);
+    if (prm->vmax < 0 || prm->vmax > 127) return fail(NASCH_EINVAL, "vmax=%d outside 0..127", prm->vmax);
+    if (!(prm->p >= 0.0 && prm->p <= 1.0)) return fail(NASCH_EINVAL, "p=%g outside [0, 1]", prm->p);
+    if (prm->layout < NASCH_LAYOUT_AUTO || prm->layout > NASCH_LAYOUT_GRID)
+        return fail(NASCH_EINVAL, "layout=%d unknown", prm->layout);
+    if (prm->k < 0 || prm->k > kMaxFusedSteps)
+        return fail(NASCH_EINVAL, "k=%d outside 0..%d", prm->k, kMaxFusedSteps);
+    if (prm->tile != 0 && prm->tile != kAgentTileSpan && prm->tile != kGridTileCells)
+        return fail(NASCH_EINVAL, "tile=%d not supported (0, %d or %d)", prm->tile, kAgentTileSpan,
+                    kGridTileCells);
+    return NASCH_OK;
+}
+
+// Floyd's sampling algorithm (Bentley & Floyd, CACM 1987): for m = 0..N-1
+// with j = L-N+m, draw t uniform on 0..j (Lemire's multiply-shift of the
+// 64-bit Philox word pair of counter (m, 0, road, 1)) and take t, or j if t
+// is already taken.  A bitmap over the ring holds the set, so a scan of it
+// yields the positions sorted.
+int floyd_init_host(int64_t L, int64_t N, uint64_t seed, uint32_t road, int32_t *x)
+{
+    if (L < 1 || L > (int64_t(1) << 31) || N < 0 || N > L) return fail(NASCH_EINVAL, "floyd: bad L/N");
+    if (N == 0) return NASCH_OK;
+    std::vector<uint64_t> taken;
+    try {
+        taken.assign((size_t)((L + 63) / 64), 0ull);
+    } catch (const std::bad_alloc &) {
+        return fail(NASCH_ENOMEM, "floyd: host bitmap of %lld bits", (long long)L);
+    }
+    const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    // The draws do not depend on the set, so they are made a batch ahead and
+    // the bitmap words they will test are prefetched (the bitmap is far
+    // larger than the caches for long roads); the set updates stay in order.
+    constexpr int kBatch = 64;
+    uint64_t draws[kBatch];
+    for (int64_t m0 = 0; m0 < N; m0 += kBatch) {
+        const int nb = (int)std::min<int64_t>(kBatch, N - m0);
+        for (int b = 0; b < nb; ++b) {
+            const int64_t m = m0 + b;
+            const uint64_t j = (uint64_t)(L - N + m);
+            const Words4 w = philox4x32_10((uint32_t)m, 0u, road, kTagInit, k0, k1);
+            const uint64_t r = ((uint64_t)w.w1 << 32) | w.w0;
+            draws[b] = (uint64_t)(((unsigned __int128)r * (j + 1)) >> 64);
+            __builtin_prefetch(&taken[draws[b] >> 6], 1);
+        }
+        for (int b = 0; b < nb; ++b) {
+            const uint64_t j = (uint64_t)(L - N + m0 + b);
+            const uint64_t t = draws[b];
+            const uint64_t pick = (taken[t >> 6] >> (t & 63)) & 1ull ? j : t;
+            taken[pick >> 6] |= 1ull << (pick & 63);
+        }
+    }
+    int64_t n = 0;
+    for (size_t wi = 0; wi < taken.size(); ++wi) {
+        uint64_t word = taken[wi];
+        while (word) {
+            const int b = __builtin_ctzll(word);
+            word &= word - 1;
+            x[n++] = (int32_t)(wi * 64 + (size_t)b);
+        }
+    }
+    return n == N ? NASCH_OK : fail(NASCH_EINVAL, "floyd: internal count mismatch");
+}
+
+// Positions must be distinct, in [0, L), and a rotation of an increasing
+// sequence (the cars' cyclic order on the ring).
+int validate_state(int64_t L, int64_t N, int vmax, const int32_t *x, const uint8_t *v, bool need_cyclic)
+{
+    int64_t descents = 0;
+    for (int64_t i = 0; i < N; ++i) {
+        if (x[i] < 0 || x[i] >= L) return fail(NASCH_EINVAL, "x[%lld]=%d outside [0, L)", (long long)i, x[i]);
+        if (v[i] > vmax) return fail(NASCH_EINVAL, "v[%lld]=%d above vmax=%d", (long long)i, v[i], vmax);
+        if (N >= 2) {
+            const int32_t nx = x[(i + 1) % N];
+            if (nx == x[i]) return fail(NASCH_EINVAL, "two cars on cell %d", x[i]);
+            if (nx < x[i]) ++descents;
+        }
+    }
+    if (N >= 2 && need_cyclic && descents != 1)
+        return fail(NASCH_EINVAL, "positions are not in cyclic order (%lld descents)", (long long)descents);
+    if (N >= 2 && !need_cyclic) {
+        std::vector<int32_t> s(x, x + N);
+        std::sort(s.begin(), s.end());
+        for (int64_t i = 1; i < N; ++i)
+            if (s[i] == s[i - 1]) return fail(NASCH_EINVAL, "two cars on cell %d", s[i]);
+    }
+    return NASCH_OK;
+}
+
+int device_info(int *device, int *sms)
+{
+    cudaError_t e = cudaGetDevice(device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    e = cudaDeviceGetAttribute(sms, cudaDevAttrMultiProcessorCount, *device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute(SM count)");
+    return NASCH_OK;
+}
+
+}  // namespace nasch
+
+using namespace nasch;
+
+struct nasch_road {
+    int64_t L = 0, N = 0;
+    int vmax = 0;
+    double p = 0;
+    uint64_t thr = 0, seed = 0;
+    uint32_t road = 0;
+    int layout = NASCH_LAYOUT_AGENT;
+    int k = 1;
+    int device = 0, sms = 1;
+    bool ring = false;
+    int blocks = 1;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int32_t *x[2] = {nullptr, nullptr};
+    uint8_t *v[2] = {nullptr, nullptr};
+    int8_t *cells[2] = {nullptr, nullptr};
+    int cur = 0;
+    uint64_t step = 0;
+    uint64_t stats_first = 0;
+    unsigned long long *d_sum = nullptr, *d_cross = nullptr;
+    int64_t stats_cap = 0;
+};
+
+namespace {
+
+RoadConst road_const(const nasch_road *h)
+{
+    RoadConst rc;
+    rc.L = (uint32_t)h->L;
+    rc.vmax = (uint32_t)h->vmax;
+    rc.thr = h->thr;
+    rc.key0 = (uint32_t)h->seed;
+    rc.key1 = (uint32_t)(h->seed >> 32);
+    rc.road = h->road;
+    return rc;
+}
+
+void free_road(nasch_road *h)
+{
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    for (int i = 0; i < 2; ++i) {
+        cudaFree(h->x[i]);
+        cudaFree(h->v[i]);
+        cudaFree(h->cells[i]);
+    }
+    cudaFree(h->d_sum);
+    cudaFree(h->d_cross);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+}
+
+// Grow the device statistics series so that steps [stats_first, upto) fit.
+int ensure_stats(nasch_road *h, int64_t needed)
+{
+    if (needed <= h->stats_cap) return NASCH_OK;
+    int64_t cap = std::max<int64_t>(needed, std::max<int64_t>(1024, 2 * h->stats_cap));
+    unsigned long long *ns = nullptr, *nc = nullptr;
+    cudaError_t e = cudaMalloc(&ns, (size_t)cap * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc(&nc, (size_t)cap * sizeof(unsigned long long));
+    if (e != cudaSuccess) {
+        cudaFree(ns);
+        return cuda_fail(e, "cudaMalloc(statistics)");
+    }
+    const int64_t used = (int64_t)(h->step - h->stats_first);
+    if (used > 0 && h->d_sum) {
+        e = cudaMemcpyAsync(ns, h->d_sum, (size_t)used * 8, cudaMemcpyDeviceToDevice, h->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(nc, h->d_cross, (size_t)used * 8, cudaMemcpyDeviceToDevice, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) {
+            cudaFree(ns);
+            cudaFree(nc);
+            return cuda_fail(e, "copy statistics");
+        }
+    }
+    cudaFree(h->d_sum);
+    cudaFree(h->d_cross);
+    h->d_sum = ns;
+    h->d_cross = nc;
+    h->stats_cap = cap;
+    return NASCH_OK;
+}
+
+// Upload agent state (host arrays) into the handle's current buffers.
+int upload_state(nasch_road *h, const int32_t *x, const uint8_t *v)
+{
+    const int64_t N = h->N;
+    cudaError_t e = cudaSuccess;
+    if (h->layout == NASCH_LAYOUT_AGENT) {
+        if (N > 0) {
+            e = cudaMemcpyAsync(h->x[h->cur], x, (size_t)N * 4, cudaMemcpyHostToDevice, h->stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(h->v[h->cur], v, (size_t)N, cudaMemcpyHostToDevice, h->stream);
+        }
+    } else {
+        int32_t *dx = nullptr;
+        uint8_t *dv = nullptr;
+        e = cudaMemsetAsync(h->cells[h->cur], 0xFF, (size_t)h->L, h->stream);
+        if (e == cudaSuccess && N > 0) {
+            e = cudaMallocAsync(&dx, (size_t)N * 4, h->stream);
+            if (e == cudaSuccess) e = cudaMallocAsync(&dv, (size_t)N, h->stream);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(dx, x, (size_t)N * 4, cudaMemcpyHostToDevice, h->stream);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(dv, v, (size_t)N, cudaMemcpyHostToDevice, h->stream);
+            if (e == cudaSuccess) e = launch_scatter_agent_to_grid(dx, dv, (uint32_t)N, h->cells[h->cur], h->stream);
+            if (dx) cudaFreeAsync(dx, h->stream);
+            if (dv) cudaFreeAsync(dv, h->stream);
+        }
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "upload state");
+    return NASCH_OK;
+}
+
+int choose_layout(const nasch_params *prm)
+{
+    if (prm->layout != NASCH_LAYOUT_AUTO) return prm->layout;
+    // State bytes per step: agent 10 per car (read + write x and v), grid 2
+    // per cell; equal at density 0.2.
+    return (double)prm->N < 0.2 * (double)prm->L ? NASCH_LAYOUT_AGENT : NASCH_LAYOUT_GRID;
+}
+
+}  // namespace
+
+extern "C" {
+
+void nasch_params_init(nasch_params *prm)
+{
+    if (!prm) return;
+    std::memset(prm, 0, sizeof(*prm));
+    prm->vmax = 5;
+    prm->layout = NASCH_LAYOUT_AUTO;
+}
+
+const char *nasch_last_error(void) { return g_last_error.c_str(); }
+
+uint64_t nasch_slow_threshold(double p) { return slow_threshold(p); }
+
+int nasch_floyd_init(int64_t L, int64_t N, uint64_t seed, uint32_t road_id, int32_t *x_host)
+{
+    clear_error();
+    if (!x_host && N > 0) return fail(NASCH_EINVAL, "x_host is NULL");
+    return floyd_init_host(L, N, seed, road_id, x_host);
+}
+
+int nasch_create_ex(const nasch_params *prm, nasch_handle *out)
+{
+    clear_error();
+    if (!out) return fail(NASCH_EINVAL, "out is NULL");
+    *out = nullptr;
+    int st = validate_params(prm);
+    if (st) return st;
+    nasch_road *h = new (std::nothrow) nasch_road();
+    if (!h) return fail(NASCH_ENOMEM, "host allocation");
+    h->L = prm->L;
+    h->N = prm->N;
+    h->vmax = prm->vmax;
+    h->p = prm->p;
+    h->thr = slow_threshold(prm->p);
+    h->seed = prm->seed;
+    h->road = prm->road_id;
+    h->layout = choose_layout(prm);
+    st = device_info(&h->device, &h->sms);
+    if (st) {
+        delete h;
+        return st;
+    }
+    cudaError_t e;
+    if (prm->stream) {
+        h->stream = (cudaStream_t)prm->stream;
+    } else {
+        e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            delete h;
+            return cuda_fail(e, "cudaStreamCreate");
+        }
+        h->own_stream = true;
+    }
+    // tile == 0: the whole-ring kernel when the ring fits one block; an
+    // explicit tile always selects the tiled kernel.
+    if (h->layout == NASCH_LAYOUT_AGENT) {
+        if (prm->tile != 0 && prm->tile != kAgentTileSpan) {
+            free_road(h);
+            return fail(NASCH_EINVAL, "agent tile must be %d", kAgentTileSpan);
+        }
+        h->ring = prm->tile == 0 && h->N <= kAgentRingMaxCars;
+        h->k = prm->k ? prm->k : 4;
+        h->blocks = h->sms * agent_tiled_blocks_per_sm();
+        const size_t n = (size_t)std::max<int64_t>(h->N, 1);
+        e = cudaSuccess;
+        for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+            e = cudaMalloc(&h->x[i], n * 4);
+            if (e == cudaSuccess) e = cudaMalloc(&h->v[i], n);
+        }
+    } else {
+        if (prm->tile != 0 && prm->tile != kGridTileCells) {
+            free_road(h);
+            return fail(NASCH_EINVAL, "grid tile must be %d", kGridTileCells);
+        }
+        h->ring = prm->tile == 0 && h->L <= kGridRingMaxCells;
+        h->k = prm->k ? prm->k : 8;
+        // the tiled kernel's buffer (tile + two halos) must not wrap the ring twice
+        if (!h->ring && h->L < (int64_t)kGridTileCells + 2 * (int64_t)grid_halo(h->k, (uint32_t)h->vmax)) {
+            free_road(h);
+            return fail(NASCH_EINVAL, "L=%lld too short for the tiled grid kernel with k=%d, vmax=%d",
+                        (long long)h->L, h->k, h->vmax);
+        }
+        h->blocks = h->sms * grid_tiled_blocks_per_sm();
+        e = cudaSuccess;
+        for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaMalloc(&h->cells[i], (size_t)h->L + 16);
+    }
+    if (e != cudaSuccess) {
+        free_road(h);
+        return e == cudaErrorMemoryAllocation ? fail(NASCH_ENOMEM, "device state: %s", cudaGetErrorString(e))
+                                              : cuda_fail(e, "cudaMalloc(state)");
+    }
+    // Floyd start, v = 0, step 0
+    std::vector<int32_t> x;
+    std::vector<uint8_t> v;
+    try {
+        x.resize((size_t)h->N);
+        v.assign((size_t)h->N, 0);
+    } catch (const std::bad_alloc &) {
+        free_road(h);
+        return fail(NASCH_ENOMEM, "host staging");
+    }
+    st = floyd_init_host(h->L, h->N, h->seed, h->road, x.data());
+    if (!st) st = upload_state(h, x.data(), v.data());
+    if (!st) st = ensure_stats(h, 1024);
+    if (st) {
+        free_road(h);
+        return st;
+    }
+    *out = h;
+    return NASCH_OK;
+}
+
+int nasch_create(int64_t L, int64_t N, int vmax, double p, uint64_t seed, nasch_handle *out)
+{
+    nasch_params prm;
+    nasch_params_init(&prm);
+    prm.L = L;
+    prm.N = N;
+    prm.vmax = vmax;
+    prm.p = p;
+    prm.seed = seed;
+    return nasch_create_ex(&prm, out);
+}
+
+int nasch_set_state(nasch_handle h, const int32_t *x_host, const uint8_t *v_host, int64_t N, uint64_t step)
+{
+    clear_error();
+    if (!h) return fail(NASCH_EINVAL, "handle is NULL");
+    if (N != h->N) return fail(NASCH_EINVAL, "N=%lld differs from the handle's N=%lld", (long long)N, (long long)h->N);
+    if (N > 0 && (!x_host || !v_host)) return fail(NASCH_EINVAL, "NULL state array");
+    int st = validate_state(h->L, N, h->vmax, x_host, v_host, h->layout == NASCH_LAYOUT_AGENT);
+    if (st) return st;
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    st = upload_state(h, x_host, v_host);
+    if (st) return st;
+    h->step = step;
+    h->stats_first = step;
+    return NASCH_OK;
+}
+
+int nasch_run(nasch_handle h, int64_t steps)
+{
+    clear_error();
+    if (!h) return fail(NASCH_EINVAL, "handle is NULL");
+    if (steps < 0) return fail(NASCH_EINVAL, "steps=%lld < 0", (long long)steps);
+    if (steps == 0) return NASCH_OK;
+    const int64_t used = (int64_t)(h->step - h->stats_first);
+    int st = ensure_stats(h, used + steps);
+    if (st) return st;
+    unsigned long long *sum = h->d_sum + used;
+    unsigned long long *cross = h->d_cross + used;
+    cudaError_t e = cudaMemsetAsync(sum, 0, (size_t)steps * 8, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(cross, 0, (size_t)steps * 8, h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(statistics)");
+    const RoadConst rc = road_const(h);
+
+    if (h->layout == NASCH_LAYOUT_AGENT) {
+        AgentStep a;
+        a.N = (uint32_t)h->N;
+        a.rc = rc;
+        if (h->N == 0) {
+            h->step += (uint64_t)steps;
+            return NASCH_OK;
+        }
+        if (h->ring) {
+            // the whole run in launches of up to 2^20 steps
+            for (int64_t done = 0; done < steps;) {
+                const int64_t kk = std::min<int64_t>(steps - done, 1 << 20);
+                a.x_in = h->x[h->cur];
+                a.v_in = h->v[h->cur];
+                a.x_out = h->x[h->cur ^ 1];
+                a.v_out = h->v[h->cur ^ 1];
+                a.step0 = (uint32_t)(h->step + (uint64_t)done);
+                a.ksteps = (int)kk;
+                a.sum_v = sum + done;
+                a.crossings = cross + done;
+                e = launch_agent_ring(a, h->stream);
+                if (e != cudaSuccess) return cuda_fail(e, "agent ring kernel");
+                h->cur ^= 1;
+                done += kk;
+            }
+        } else {
+            for (int64_t done = 0; done < steps;) {
+                const int kk = (int)std::min<int64_t>(steps - done, h->k);
+                a.x_in = h->x[h->cur];
+                a.v_in = h->v[h->cur];
+                a.x_out = h->x[h->cur ^ 1];
+                a.v_out = h->v[h->cur ^ 1];
+                a.step0 = (uint32_t)(h->step + (uint64_t)done);
+                a.ksteps = kk;
+                a.sum_v = sum + done;
+                a.crossings = cross + done;
+                e = launch_agent_tiled(a, h->blocks, h->stream);
+                if (e != cudaSuccess) return cuda_fail(e, "agent tiled kernel");
+                h->cur ^= 1;
+                done += kk;
+            }
+        }
+    } else {
+        GridStep g;
+        g.rc = rc;
+        for (int64_t done = 0; done < steps;) {
+            const int kk = h->ring ? (int)std::min<int64_t>(steps - done, 1 << 20)
+                                   : (int)std::min<int64_t>(steps - done, h->k);
+            g.c_in = h->cells[h->cur];
+            g.c_out = h->cells[h->cur ^ 1];
+            g.step0 = (uint32_t)(h->step + (uint64_t)done);
+            g.ksteps = kk;
+            g.sum_v = sum + done;
+            g.crossings = cross + done;
+            e = h->ring ? launch_grid_ring(g, h->stream) : launch_grid_tiled(g, h->blocks, h->stream);
+            if (e != cudaSuccess) return cuda_fail(e, h->ring ? "grid ring kernel" : "grid tiled kernel");
+            h->cur ^= 1;
+            done += kk;
+        }
+    }
+    h->step += (uint64_t)steps;
+    return NASCH_OK;
+}
+
+int nasch_read_state(nasch_handle h, int32_t *x_host, uint8_t *v_host, int64_t cap)
+{
+    clear_error();
+    if (!h) return fail(NASCH_EINVAL, "handle is NULL");
+    if (cap < h->N) return fail(NASCH_EINVAL, "cap=%lld < N=%lld", (long long)cap, (long long)h->N);
+    if (h->N > 0 && (!x_host || !v_host)) return fail(NASCH_EINVAL, "NULL output array");
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    if (h->N == 0) return NASCH_OK;
+    if (h->layout == NASCH_LAYOUT_AGENT) {
+        e = cudaMemcpyAsync(x_host, h->x[h->cur], (size_t)h->N * 4, cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(v_host, h->v[h->cur], (size_t)h->N, cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "read state");
+        return NASCH_OK;
+    }
+    std::vector<int8_t> cells;
+    try {
+        cells.resize((size_t)h->L);
+    } catch (const std::bad_alloc &) {
+        return fail(NASCH_ENOMEM, "host grid staging");
+    }
+    e = cudaMemcpy(cells.data(), h->cells[h->cur], (size_t)h->L, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "read grid");
+    int64_t n = 0;
+    for (int64_t c = 0; c < h->L; ++c) {
+        if (cells[(size_t)c] >= 0) {
+            if (n >= h->N) return fail(NASCH_EINVAL, "grid holds more than N cars");
+            x_host[n] = (int32_t)c;
+            v_host[n] = (uint8_t)cells[(size_t)c];
+            ++n;
+        }
+    }
+    if (n != h->N) return fail(NASCH_EINVAL, "grid holds %lld cars, expected %lld", (long long)n, (long long)h->N);
+    return NASCH_OK;
+}
+
+int nasch_read_grid(nasch_handle h, int8_t *cells_host, int64_t cap)
+{
+    clear_error();
+    if (!h) return fail(NASCH_EINVAL, "handle is NULL");
+    if (cap < h->L || !cells_host) return fail(NASCH_EINVAL, "cap=%lld < L=%lld", (long long)cap, (long long)h->L);
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    if (h->layout == NASCH_LAYOUT_GRID) {
+        e = cudaMemcpy(cells_host, h->cells[h->cur], (size_t)h->L, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(e, "read grid");
+        return NASCH_OK;
+    }
+    int8_t *d = nullptr;
+    e = cudaMallocAsync(&d, (size_t)h->L, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d, 0xFF, (size_t)h->L, h->stream);
+    if (e == cudaSuccess) e = launch_scatter_agent_to_grid(h->x[h->cur], h->v[h->cur], (uint32_t)h->N, d, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(cells_host, d, (size_t)h->L, cudaMemcpyDeviceToHost, h->stream);
+    if (d) cudaFreeAsync(d, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "agent to grid");
+    return NASCH_OK;
+}
+
+int nasch_stats(nasch_handle h, uint64_t first_step, int64_t count, uint64_t *sum_v_host, uint64_t *crossings_host)
+{
+    clear_error();
+    if (!h) return fail(NASCH_EINVAL, "handle is NULL");
+    if (count < 0 || first_step < h->stats_first || first_step + (uint64_t)count > h->step)
+        return fail(NASCH_EINVAL, "steps [%llu, %llu) outside the kept range [%llu, %llu)",
+                    (unsigned long long)first_step, (unsigned long long)(first_step + (uint64_t)count),
+                    (unsigned long long)h->stats_first, (unsigned long long)h->step);
+    if (count == 0) return NASCH_OK;
+    const size_t off = (size_t)(first_step - h->stats_first);
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e == cudaSuccess && sum_v_host)
+        e = cudaMemcpy(sum_v_host, h->d_sum + off, (size_t)count * 8, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && crossings_host)
+        e = cudaMemcpy(crossings_host, h->d_cross + off, (size_t)count * 8, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "read statistics");
+    return NASCH_OK;
+}
+
+int nasch_get_info(nasch_handle h, nasch_info *info)
+{
+    clear_error();
+    if (!h || !info) return fail(NASCH_EINVAL, "NULL argument");
+    info->L = h->L;
+    info->N = h->N;
+    info->vmax = h->vmax;
+    info->layout = h->layout;
+    info->k = h->k;
+    info->tile = h->layout == NASCH_LAYOUT_AGENT ? kAgentTileSpan : kGridTileCells;
+    info->step = h->step;
+    info->stats_first = h->stats_first;
+    info->threshold = h->thr;
+    info->ring_kernel = h->ring ? 1 : 0;
+    info->blocks = h->blocks;
+    return NASCH_OK;
+}
+
+int nasch_synchronize(nasch_handle h)
+{
+    clear_error();
+    if (!h) return fail(NASCH_EINVAL, "handle is NULL");
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    return e == cudaSuccess ? NASCH_OK : cuda_fail(e, "cudaStreamSynchronize");
+}
+
+void nasch_destroy(nasch_handle h) { free_road(h); }
+
+int nasch_philox_device(int64_t n, const uint32_t *ctr_host, uint64_t seed, uint32_t *out_host)
+{
+    clear_error();
+    if (n < 0 || (n > 0 && (!ctr_host || !out_host))) return fail(NASCH_EINVAL, "bad arguments");
+    if (n == 0) return NASCH_OK;
+    uint32_t *dc = nullptr, *dout = nullptr;
+    cudaError_t e = cudaMalloc(&dc, (size_t)n * 16);
+    if (e == cudaSuccess) e = cudaMalloc(&dout, (size_t)n * 16);
+    if (e == cudaSuccess) e = cudaMemcpy(dc, ctr_host, (size_t)n * 16, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = launch_philox_test(dc, (uint32_t)seed, (uint32_t)(seed >> 32), dout, n, nullptr);
+    if (e == cudaSuccess) e = cudaMemcpy(out_host, dout, (size_t)n * 16, cudaMemcpyDeviceToHost);
+    cudaFree(dc);
+    cudaFree(dout);
+    return e == cudaSuccess ? NASCH_OK : cuda_fail(e, "philox test kernel");
+}
+
+}  // extern "C"

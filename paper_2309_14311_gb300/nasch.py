@@ -1,0 +1,216 @@
+"""Python binding of the NaSch C ABI (``include/nasch.h``).
+
+Argument marshalling only: every step of the simulation runs in the CUDA
+kernels of ``_build/libnasch.so``.  The library must be built (``build.py``)
+and a CUDA device present; nothing here falls back to a CPU path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+OK = 0
+EINVAL = -1
+ENOMEM = -2
+ECUDA = -3
+ETIMEOUT = -4
+EBUSY = -5
+ECANCELED = -6
+
+LAYOUT_AUTO = 0
+LAYOUT_AGENT = 1
+LAYOUT_GRID = 2
+LAYOUTS = {"auto": LAYOUT_AUTO, "agent": LAYOUT_AGENT, "grid": LAYOUT_GRID}
+
+_STATUS = {EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA", ETIMEOUT: "ETIMEOUT", EBUSY: "EBUSY",
+           ECANCELED: "ECANCELED"}
+
+
+class NaschError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int64), ("N", ctypes.c_int64), ("vmax", ctypes.c_int32),
+                ("p", ctypes.c_double), ("seed", ctypes.c_uint64), ("road_id", ctypes.c_uint32),
+                ("layout", ctypes.c_int32), ("k", ctypes.c_int32), ("tile", ctypes.c_int32),
+                ("stream", ctypes.c_void_p)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int64), ("N", ctypes.c_int64), ("vmax", ctypes.c_int32),
+                ("layout", ctypes.c_int32), ("k", ctypes.c_int32), ("tile", ctypes.c_int32),
+                ("step", ctypes.c_uint64), ("stats_first", ctypes.c_uint64),
+                ("threshold", ctypes.c_uint64), ("ring_kernel", ctypes.c_int32),
+                ("blocks", ctypes.c_int32)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False) -> ctypes.CDLL:
+    """Load libnasch.so; raises if it is missing (no fallback exists)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(_build.LIB):
+            if not build_if_missing:
+                raise RuntimeError(f"{_build.LIB} is missing: build it with "
+                                   "`python -m paper_2309_14311_gb300.build` (needs nvcc)")
+            _build.build()
+        lib = ctypes.CDLL(_build.LIB)
+        _declare(lib)
+        _lib = lib
+        return lib
+
+
+def _declare(lib) -> None:
+    P, i64, u64, i32, u32, dbl = (ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint64, ctypes.c_int32,
+                                  ctypes.c_uint32, ctypes.c_double)
+    H = ctypes.c_void_p
+    sig = {
+        "nasch_params_init": (None, [P]),
+        "nasch_create": (ctypes.c_int, [i64, i64, ctypes.c_int, dbl, u64, P]),
+        "nasch_create_ex": (ctypes.c_int, [P, P]),
+        "nasch_set_state": (ctypes.c_int, [H, P, P, i64, u64]),
+        "nasch_run": (ctypes.c_int, [H, i64]),
+        "nasch_read_state": (ctypes.c_int, [H, P, P, i64]),
+        "nasch_read_grid": (ctypes.c_int, [H, P, i64]),
+        "nasch_stats": (ctypes.c_int, [H, u64, i64, P, P]),
+        "nasch_get_info": (ctypes.c_int, [H, P]),
+        "nasch_synchronize": (ctypes.c_int, [H]),
+        "nasch_destroy": (None, [H]),
+        "nasch_last_error": (ctypes.c_char_p, []),
+        "nasch_slow_threshold": (u64, [dbl]),
+        "nasch_floyd_init": (ctypes.c_int, [i64, i64, u64, u32, P]),
+        "nasch_philox_device": (ctypes.c_int, [i64, P, u64, P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+
+
+def _check(status: int) -> None:
+    if status != OK:
+        msg = load().nasch_last_error()
+        raise NaschError(status, msg.decode() if msg else "")
+
+
+def _ptr(a: np.ndarray):
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def slow_threshold(p: float) -> int:
+    return int(load().nasch_slow_threshold(float(p)))
+
+
+def floyd_init(L: int, N: int, seed: int, road: int = 0) -> np.ndarray:
+    x = np.zeros(max(N, 1), dtype=np.int32)
+    _check(load().nasch_floyd_init(L, N, seed, road, _ptr(x)))
+    return x[:N].copy()
+
+
+def philox_device(ctr: np.ndarray, seed: int) -> np.ndarray:
+    c = np.ascontiguousarray(np.asarray(ctr, dtype=np.uint32).reshape(-1, 4))
+    out = np.zeros_like(c)
+    _check(load().nasch_philox_device(len(c), _ptr(c), seed, _ptr(out)))
+    return out
+
+
+class Road:
+    """One ring road with device-resident state (a ``nasch_handle``)."""
+
+    def __init__(self, L: int, N: int, vmax: int = 5, p: float = 0.0, seed: int = 0, road_id: int = 0,
+                 layout: str | int = "auto", k: int = 0, tile: int = 0, stream=None):
+        lib = load()
+        prm = Params()
+        lib.nasch_params_init(ctypes.byref(prm))
+        prm.L, prm.N, prm.vmax, prm.p, prm.seed, prm.road_id = L, N, vmax, float(p), seed, road_id
+        prm.layout = LAYOUTS[layout] if isinstance(layout, str) else int(layout)
+        prm.k, prm.tile = k, tile
+        prm.stream = _stream_handle(stream)
+        self._stream_ref = stream
+        h = ctypes.c_void_p()
+        _check(lib.nasch_create_ex(ctypes.byref(prm), ctypes.byref(h)))
+        self._h = h
+        self.L, self.N, self.vmax, self.p, self.seed, self.road_id = L, N, vmax, p, seed, road_id
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            load().nasch_destroy(self._h)
+            self._h = None
+
+    __del__ = close
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self) -> Info:
+        inf = Info()
+        _check(load().nasch_get_info(self._h, ctypes.byref(inf)))
+        return inf
+
+    @property
+    def step(self) -> int:
+        return int(self.info().step)
+
+    def set_state(self, x, v, step: int = 0) -> None:
+        x = np.ascontiguousarray(x, dtype=np.int32)
+        v = np.ascontiguousarray(v, dtype=np.uint8)
+        _check(load().nasch_set_state(self._h, _ptr(x), _ptr(v), len(x), step))
+
+    def run(self, steps: int) -> None:
+        _check(load().nasch_run(self._h, steps))
+
+    def synchronize(self) -> None:
+        _check(load().nasch_synchronize(self._h))
+
+    def read_state(self, out_x: np.ndarray | None = None, out_v: np.ndarray | None = None):
+        x = out_x if out_x is not None else np.empty(max(self.N, 1), dtype=np.int32)
+        v = out_v if out_v is not None else np.empty(max(self.N, 1), dtype=np.uint8)
+        _check(load().nasch_read_state(self._h, _ptr(x), _ptr(v), min(len(x), len(v))))
+        return x[: self.N], v[: self.N]
+
+    def read_grid(self) -> np.ndarray:
+        c = np.empty(self.L, dtype=np.int8)
+        _check(load().nasch_read_grid(self._h, _ptr(c), self.L))
+        return c
+
+    def stats(self, first_step: int | None = None, count: int | None = None):
+        inf = self.info()
+        first = int(inf.stats_first) if first_step is None else first_step
+        n = int(inf.step) - first if count is None else count
+        sv = np.zeros(max(n, 1), dtype=np.uint64)
+        cr = np.zeros(max(n, 1), dtype=np.uint64)
+        _check(load().nasch_stats(self._h, first, n, _ptr(sv), _ptr(cr)))
+        return sv[:n], cr[:n]
+
+
+def _stream_handle(stream):
+    """cudaStream_t of a torch.cuda.Stream (or a raw integer handle), else None."""
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
