@@ -399,6 +399,29 @@ class _Null:
         return False
 
 
+def run_profile_case(args):
+    """A small case of one kernel for ncu captures: inputs larger than L2 but a
+    few hundred MiB on the device; `--profile-launches` launches after two
+    warm-up launches.  Prints nothing but a one-line summary."""
+    import torch
+
+    from paper_2309_14311_gb300 import nasch as NS
+    torch.cuda.set_device(0)
+    NS.load(build_if_missing=True)
+    layout = args.profile
+    k = args.k or WL.LARGE_ROAD_K[layout]
+    # density 1/16 like the large road; agent 2^25 cars (160 MiB of state),
+    # grid 2^28 cells (256 MiB)
+    L, N = (2**29, 2**25) if layout == "agent" else (2**28, 2**24)
+    road = NS.Road(L, N, 5, 0.13, 1, 0, layout=layout, k=k)
+    road.run(2 * k)
+    road.run(args.profile_launches * k)
+    road.synchronize()
+    print(f"profile case {layout} k={k} L={L} N={N} launches={2 + args.profile_launches}")
+    road.close()
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -414,7 +437,12 @@ def main(argv=None):
     ap.add_argument("--cpu-steps", type=int, default=10)
     ap.add_argument("--ref-steps-per-step", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", choices=["agent", "grid"], default=None,
+                    help="run the small ncu profiling case of one layout and exit")
+    ap.add_argument("--profile-launches", type=int, default=3)
     args = ap.parse_args(argv)
+    if args.profile:
+        return run_profile_case(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -164,6 +164,13 @@ int nasch_floyd_init(int64_t L, int64_t N, uint64_t seed, uint32_t road_id, int3
  * hi)).  Runs one kernel and synchronises. */
 int nasch_philox_device(int64_t n, const uint32_t *ctr_host, uint64_t seed, uint32_t *out_host);
 
+/* Calibration: the rate (draws per second) at which the GPU evaluates the
+ * rule-3 draw, word 0 of Philox4x32-10, with nothing else to do - the
+ * integer-pipe ceiling of the step, one draw per car-step.  Runs one
+ * kernel of draws_per_thread draws per thread on a full grid and
+ * synchronises; seconds (may be NULL) receives the kernel's duration. */
+int nasch_calibrate_philox(int64_t draws_per_thread, double *draws_per_second, double *seconds);
+
 #ifdef __cplusplus
 }
 #endif

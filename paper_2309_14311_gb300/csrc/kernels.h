@@ -12,11 +12,14 @@ namespace nasch {
 // shared memory for the whole launch).
 constexpr int kMaxFusedSteps = 64;
 
-// Agent tiled kernel geometry: 256 threads x 8 cars = 2048 cars per tile,
-// of which the last round_up(k, 8) are look-ahead halo.
-constexpr int kAgentThreads = 256;
-constexpr int kAgentCarsPerThread = 8;
-constexpr int kAgentTileSpan = kAgentThreads * kAgentCarsPerThread;
+// Agent tiled kernel geometry: each warp holds a tile of 32 lanes x R cars
+// (R = 16: 512 cars, the default; R = 8: 256 cars), of which the last
+// round_up(k, R) are look-ahead halo; blocks of 128 threads (4 independent
+// warps).
+constexpr int kAgentThreads = 128;
+constexpr int kAgentCarsPerThread = 16;
+constexpr int kAgentTileSpan = 32 * kAgentCarsPerThread;
+constexpr int kAgentTileSpanSmall = 32 * 8;
 
 // Whole-ring agent kernel: one block of up to 1024 threads x 8 cars.
 constexpr int kAgentRingMaxCars = 1024 * 8;
@@ -26,10 +29,14 @@ constexpr int kAgentRingMaxCars = 1024 * 8;
 constexpr int kGridThreads = 256;
 constexpr int kGridTileCells = 8192;
 
+// Status word bits set by kernels (read by the host after a launch).
+constexpr unsigned int kStatusTimeout = 1u;   // a bounded wait on an async copy ran out
+
 // Whole-ring grid kernel: the ring (and its successor) in shared memory.
 constexpr int kGridRingMaxCells = 32768;
 
 struct AgentStep {
+    unsigned int *status;        // device status word (nonzero: a bounded wait ran out)
     const int32_t *x_in;
     const uint8_t *v_in;
     int32_t *x_out;
@@ -43,6 +50,7 @@ struct AgentStep {
 };
 
 struct GridStep {
+    unsigned int *status;
     const int8_t *c_in;
     int8_t *c_out;
     RoadConst rc;
@@ -52,15 +60,19 @@ struct GridStep {
     unsigned long long *crossings;
 };
 
-// Owned cars per tile for fusion depth k.
-inline uint32_t agent_tile_owned(int k) { return (uint32_t)(kAgentTileSpan - ((k + 7) / 8) * 8); }
+// Owned cars per warp-tile of `span` cars (32 lanes x span/32) for fusion depth k.
+inline uint32_t agent_tile_owned(int k, int span)
+{
+    const int r = span / 32;
+    return (uint32_t)(span - ((k + r - 1) / r) * r);
+}
 // Halo cells per side for the grid tile.
 inline uint32_t grid_halo(int k, uint32_t vmax) { return ((uint32_t)k * vmax + 15u) / 16u * 16u; }
 
 int agent_tiled_blocks_per_sm();
 int grid_tiled_blocks_per_sm();
 
-cudaError_t launch_agent_tiled(const AgentStep &a, int blocks, cudaStream_t s);
+cudaError_t launch_agent_tiled(const AgentStep &a, int span, int blocks, cudaStream_t s);
 cudaError_t launch_agent_ring(const AgentStep &a, cudaStream_t s);
 cudaError_t launch_grid_tiled(const GridStep &g, int blocks, cudaStream_t s);
 cudaError_t launch_grid_ring(const GridStep &g, cudaStream_t s);

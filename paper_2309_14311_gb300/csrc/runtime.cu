@@ -60,9 +60,10 @@ int validate_params(const nasch_params *prm)
         return fail(NASCH_EINVAL, "layout=%d unknown", prm->layout);
     if (prm->k < 0 || prm->k > kMaxFusedSteps)
         return fail(NASCH_EINVAL, "k=%d outside 0..%d", prm->k, kMaxFusedSteps);
-    if (prm->tile != 0 && prm->tile != kAgentTileSpan && prm->tile != kGridTileCells)
-        return fail(NASCH_EINVAL, "tile=%d not supported (0, %d or %d)", prm->tile, kAgentTileSpan,
-                    kGridTileCells);
+    if (prm->tile != 0 && prm->tile != kAgentTileSpan && prm->tile != kAgentTileSpanSmall &&
+        prm->tile != kGridTileCells)
+        return fail(NASCH_EINVAL, "tile=%d not supported (0, %d, %d or %d)", prm->tile, kAgentTileSpanSmall,
+                    kAgentTileSpan, kGridTileCells);
     return NASCH_OK;
 }
 
@@ -165,6 +166,8 @@ struct nasch_road {
     int device = 0, sms = 1;
     bool ring = false;
     int blocks = 1;
+    int tile = 0;                       // agent warp-tile span or grid tile cells
+    unsigned int *d_status = nullptr;   // kernels set bits here when a bounded wait runs out
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     int32_t *x[2] = {nullptr, nullptr};
@@ -178,6 +181,23 @@ struct nasch_road {
 };
 
 namespace {
+
+// Wait for the handle's stream, then report a kernel that gave up a bounded
+// wait (the status word is cleared for the next launch).
+int sync_and_check(nasch_road *h)
+{
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    unsigned int status = 0;
+    e = cudaMemcpy(&status, h->d_status, sizeof(status), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "read status word");
+    if (status) {
+        cudaMemset(h->d_status, 0, sizeof(status));
+        return fail(NASCH_ETIMEOUT, "a kernel's bounded wait on an asynchronous copy ran out (status 0x%x); "
+                    "the state of this road is undefined", status);
+    }
+    return NASCH_OK;
+}
 
 RoadConst road_const(const nasch_road *h)
 {
@@ -202,6 +222,7 @@ void free_road(nasch_road *h)
     }
     cudaFree(h->d_sum);
     cudaFree(h->d_cross);
+    cudaFree(h->d_status);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;
 }
@@ -335,11 +356,12 @@ int nasch_create_ex(const nasch_params *prm, nasch_handle *out)
     // tile == 0: the whole-ring kernel when the ring fits one block; an
     // explicit tile always selects the tiled kernel.
     if (h->layout == NASCH_LAYOUT_AGENT) {
-        if (prm->tile != 0 && prm->tile != kAgentTileSpan) {
+        if (prm->tile != 0 && prm->tile != kAgentTileSpan && prm->tile != kAgentTileSpanSmall) {
             free_road(h);
-            return fail(NASCH_EINVAL, "agent tile must be %d", kAgentTileSpan);
+            return fail(NASCH_EINVAL, "agent tile must be %d or %d", kAgentTileSpanSmall, kAgentTileSpan);
         }
         h->ring = prm->tile == 0 && h->N <= kAgentRingMaxCars;
+        h->tile = prm->tile ? prm->tile : kAgentTileSpan;
         h->k = prm->k ? prm->k : 4;
         h->blocks = h->sms * agent_tiled_blocks_per_sm();
         const size_t n = (size_t)std::max<int64_t>(h->N, 1);
@@ -354,6 +376,7 @@ int nasch_create_ex(const nasch_params *prm, nasch_handle *out)
             return fail(NASCH_EINVAL, "grid tile must be %d", kGridTileCells);
         }
         h->ring = prm->tile == 0 && h->L <= kGridRingMaxCells;
+        h->tile = kGridTileCells;
         h->k = prm->k ? prm->k : 8;
         // the tiled kernel's buffer (tile + two halos) must not wrap the ring twice
         if (!h->ring && h->L < (int64_t)kGridTileCells + 2 * (int64_t)grid_halo(h->k, (uint32_t)h->vmax)) {
@@ -365,6 +388,8 @@ int nasch_create_ex(const nasch_params *prm, nasch_handle *out)
         e = cudaSuccess;
         for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaMalloc(&h->cells[i], (size_t)h->L + 16);
     }
+    if (e == cudaSuccess) e = cudaMalloc(&h->d_status, sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMemset(h->d_status, 0, sizeof(unsigned int));
     if (e != cudaSuccess) {
         free_road(h);
         return e == cudaErrorMemoryAllocation ? fail(NASCH_ENOMEM, "device state: %s", cudaGetErrorString(e))
@@ -438,6 +463,7 @@ int nasch_run(nasch_handle h, int64_t steps)
 
     if (h->layout == NASCH_LAYOUT_AGENT) {
         AgentStep a;
+        a.status = h->d_status;
         a.N = (uint32_t)h->N;
         a.rc = rc;
         if (h->N == 0) {
@@ -472,7 +498,7 @@ int nasch_run(nasch_handle h, int64_t steps)
                 a.ksteps = kk;
                 a.sum_v = sum + done;
                 a.crossings = cross + done;
-                e = launch_agent_tiled(a, h->blocks, h->stream);
+                e = launch_agent_tiled(a, h->tile, h->blocks, h->stream);
                 if (e != cudaSuccess) return cuda_fail(e, "agent tiled kernel");
                 h->cur ^= 1;
                 done += kk;
@@ -480,6 +506,7 @@ int nasch_run(nasch_handle h, int64_t steps)
         }
     } else {
         GridStep g;
+        g.status = h->d_status;
         g.rc = rc;
         for (int64_t done = 0; done < steps;) {
             const int kk = h->ring ? (int)std::min<int64_t>(steps - done, 1 << 20)
@@ -506,8 +533,9 @@ int nasch_read_state(nasch_handle h, int32_t *x_host, uint8_t *v_host, int64_t c
     if (!h) return fail(NASCH_EINVAL, "handle is NULL");
     if (cap < h->N) return fail(NASCH_EINVAL, "cap=%lld < N=%lld", (long long)cap, (long long)h->N);
     if (h->N > 0 && (!x_host || !v_host)) return fail(NASCH_EINVAL, "NULL output array");
-    cudaError_t e = cudaStreamSynchronize(h->stream);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    int st = sync_and_check(h);
+    if (st) return st;
+    cudaError_t e = cudaSuccess;
     if (h->N == 0) return NASCH_OK;
     if (h->layout == NASCH_LAYOUT_AGENT) {
         e = cudaMemcpyAsync(x_host, h->x[h->cur], (size_t)h->N * 4, cudaMemcpyDeviceToHost, h->stream);
@@ -543,8 +571,9 @@ int nasch_read_grid(nasch_handle h, int8_t *cells_host, int64_t cap)
     clear_error();
     if (!h) return fail(NASCH_EINVAL, "handle is NULL");
     if (cap < h->L || !cells_host) return fail(NASCH_EINVAL, "cap=%lld < L=%lld", (long long)cap, (long long)h->L);
-    cudaError_t e = cudaStreamSynchronize(h->stream);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    int st = sync_and_check(h);
+    if (st) return st;
+    cudaError_t e = cudaSuccess;
     if (h->layout == NASCH_LAYOUT_GRID) {
         e = cudaMemcpy(cells_host, h->cells[h->cur], (size_t)h->L, cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) return cuda_fail(e, "read grid");
@@ -571,8 +600,10 @@ int nasch_stats(nasch_handle h, uint64_t first_step, int64_t count, uint64_t *su
                     (unsigned long long)h->stats_first, (unsigned long long)h->step);
     if (count == 0) return NASCH_OK;
     const size_t off = (size_t)(first_step - h->stats_first);
-    cudaError_t e = cudaStreamSynchronize(h->stream);
-    if (e == cudaSuccess && sum_v_host)
+    int st = sync_and_check(h);
+    if (st) return st;
+    cudaError_t e = cudaSuccess;
+    if (sum_v_host)
         e = cudaMemcpy(sum_v_host, h->d_sum + off, (size_t)count * 8, cudaMemcpyDeviceToHost);
     if (e == cudaSuccess && crossings_host)
         e = cudaMemcpy(crossings_host, h->d_cross + off, (size_t)count * 8, cudaMemcpyDeviceToHost);
@@ -589,7 +620,7 @@ int nasch_get_info(nasch_handle h, nasch_info *info)
     info->vmax = h->vmax;
     info->layout = h->layout;
     info->k = h->k;
-    info->tile = h->layout == NASCH_LAYOUT_AGENT ? kAgentTileSpan : kGridTileCells;
+    info->tile = h->tile;
     info->step = h->step;
     info->stats_first = h->stats_first;
     info->threshold = h->thr;
@@ -602,8 +633,7 @@ int nasch_synchronize(nasch_handle h)
 {
     clear_error();
     if (!h) return fail(NASCH_EINVAL, "handle is NULL");
-    cudaError_t e = cudaStreamSynchronize(h->stream);
-    return e == cudaSuccess ? NASCH_OK : cuda_fail(e, "cudaStreamSynchronize");
+    return sync_and_check(h);
 }
 
 void nasch_destroy(nasch_handle h) { free_road(h); }

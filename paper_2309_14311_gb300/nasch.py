@@ -97,6 +97,7 @@ def _declare(lib) -> None:
         "nasch_slow_threshold": (u64, [dbl]),
         "nasch_floyd_init": (ctypes.c_int, [i64, i64, u64, u32, P]),
         "nasch_philox_device": (ctypes.c_int, [i64, P, u64, P]),
+        "nasch_calibrate_philox": (ctypes.c_int, [i64, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -129,6 +130,14 @@ def philox_device(ctr: np.ndarray, seed: int) -> np.ndarray:
     out = np.zeros_like(c)
     _check(load().nasch_philox_device(len(c), _ptr(c), seed, _ptr(out)))
     return out
+
+
+def calibrate_philox(draws_per_thread: int = 1 << 14) -> float:
+    """Draws per second of the bare rule-3 Philox draw on this GPU."""
+    rate = ctypes.c_double()
+    secs = ctypes.c_double()
+    _check(load().nasch_calibrate_philox(draws_per_thread, ctypes.byref(rate), ctypes.byref(secs)))
+    return rate.value
 
 
 class Road:

@@ -79,15 +79,15 @@ def test_example_parameter_file_case():
     orc = oracle_run(s.L, s.N, s.vmax, s.p, s.seed, s.T)
     for layout in ("agent", "grid"):
         assert_same(lib_run(s.L, s.N, s.vmax, s.p, s.seed, s.T, layout=layout), orc, s.L, layout)
-    assert_same(lib_run(s.L, s.N, s.vmax, s.p, s.seed, s.T, layout="agent", tile=2048, k=7), orc, s.L, "agent")
+    assert_same(lib_run(s.L, s.N, s.vmax, s.p, s.seed, s.T, layout="agent", tile=512, k=7), orc, s.L, "agent")
 
 
 AGENT_TILED = [  # (L, N, vmax, p, k, T)
     (100000, 30000, 5, 0.13, 1, 30),
     (100000, 30000, 5, 0.13, 4, 41),
     (100000, 30000, 5, 0.13, 64, 130),
-    (50000, 2040 * 3, 8, 0.5, 8, 20),          # exactly three tiles
-    (50000, 2040 * 3 + 5, 3, 0.25, 8, 20),     # ragged last tile
+    (50000, 496 * 12, 8, 0.5, 8, 20),          # exactly twelve warp-tiles
+    (50000, 496 * 12 + 5, 3, 0.25, 8, 20),     # ragged last tile
     (70001, 9999, 20, 0.3, 5, 33),
     (1000, 7, 5, 0.13, 8, 50),                 # tile holds the ring many times over
     (1000, 1, 9, 0.2, 3, 40),                  # a car alone
@@ -103,8 +103,17 @@ AGENT_TILED = [  # (L, N, vmax, p, k, T)
 def test_agent_tiled_matches_oracle(L, N, vmax, p, k, T):
     seed = 1000 + L % 97 + N % 13
     orc = oracle_run(L, N, vmax, p, seed, T, road=3)
-    lib = lib_run(L, N, vmax, p, seed, T, road=3, layout="agent", k=k, tile=2048)
+    lib = lib_run(L, N, vmax, p, seed, T, road=3, layout="agent", k=k, tile=512)
     x, v, sv, cr, _ = lib
+    assert np.array_equal(x, orc[0]) and np.array_equal(v, orc[1])
+    assert np.array_equal(sv, orc[2]) and np.array_equal(cr, orc[3])
+
+
+@pytest.mark.parametrize("L,N,vmax,p,k,T", [AGENT_TILED[i] for i in (1, 4, 6, 7, 12)])
+def test_agent_small_tile_matches_oracle(L, N, vmax, p, k, T):
+    seed = 2000 + L % 89 + N % 7
+    orc = oracle_run(L, N, vmax, p, seed, T, road=4)
+    x, v, sv, cr, _ = lib_run(L, N, vmax, p, seed, T, road=4, layout="agent", k=k, tile=256)
     assert np.array_equal(x, orc[0]) and np.array_equal(v, orc[1])
     assert np.array_equal(sv, orc[2]) and np.array_equal(cr, orc[3])
 
@@ -143,9 +152,9 @@ def test_whole_ring_kernels(L, N, vmax, p, T):
 def test_layout_and_fusion_depth_independence():
     """Same road, every launch configuration: identical results."""
     L, N, vmax, p, T, seed = 50000, 6000, 5, 0.2, 96, 9
-    want = lib_run(L, N, vmax, p, seed, T, layout="agent", k=1, tile=2048)
+    want = lib_run(L, N, vmax, p, seed, T, layout="agent", k=1, tile=512)
     for k in (2, 3, 4, 8, 16, 32, 64):
-        got = lib_run(L, N, vmax, p, seed, T, layout="agent", k=k, tile=2048)
+        got = lib_run(L, N, vmax, p, seed, T, layout="agent", k=k, tile=512)
         for a, b in zip(want, got):
             assert np.array_equal(a, b), k
     for k in (1, 2, 5, 8, 13, 64):
@@ -153,12 +162,12 @@ def test_layout_and_fusion_depth_independence():
         for a, b in zip(want[2:], got[2:]):
             assert np.array_equal(a, b), k
     # launches split at odd places
-    got = lib_run(L, N, vmax, p, seed, T, layout="agent", k=8, tile=2048, chunks=[1, 7, 30, 58])
+    got = lib_run(L, N, vmax, p, seed, T, layout="agent", k=8, tile=512, chunks=[1, 7, 30, 58])
     for a, b in zip(want, got):
         assert np.array_equal(a, b)
 
 
-@pytest.mark.parametrize("layout,tile", [("agent", 0), ("agent", 2048), ("grid", 0), ("grid", 8192)])
+@pytest.mark.parametrize("layout,tile", [("agent", 0), ("agent", 512), ("grid", 0), ("grid", 8192)])
 def test_resume_from_state_is_bit_exact(layout, tile):
     L, N, vmax, p, seed = 40000, 5000, 5, 0.13, 21
     T1, T2 = 37, 45
