@@ -164,6 +164,65 @@ int nasch_floyd_init(int64_t L, int64_t N, uint64_t seed, uint32_t road_id, int3
  * hi)).  Runs one kernel and synchronises. */
 int nasch_philox_device(int64_t n, const uint32_t *ctr_host, uint64_t seed, uint32_t *out_host);
 
+/* ------------------------------------------------------------------------
+ * Batches: many independent roads (a parameter study run as one job - the
+ * paper's "Variations": a series of parameter cases as embarrassingly
+ * parallel work).  Road i has parameters roads[i] (layout AUTO picks agent or
+ * grid by density; k and tile may be left 0) and runs steps[i] steps from a
+ * Floyd start keyed by (roads[i].seed, roads[i].road_id).  All roads advance
+ * together in super-steps: one persistent launch per super-step pulls
+ * (road, tile) items from a work-list, each item running that road's k fused
+ * steps; the launch sequence is captured in CUDA graphs.  Every road's result
+ * equals the same road run alone with nasch_create_ex/nasch_run.
+ * The stream of roads[0] is used (NULL: the batch owns one).  The call
+ * returns once the work is enqueued.
+ * ------------------------------------------------------------------------ */
+typedef struct nasch_batch_info {
+    int64_t n_roads;
+    int64_t super_steps;    /* launches in the job */
+    int64_t items;          /* (road, tile) items of the first super-step */
+    int64_t device_bytes;   /* device memory held by the batch */
+    int64_t vehicle_steps;  /* sum over roads of N * steps */
+    int64_t cell_steps;     /* sum over roads of L * steps */
+    int32_t blocks;         /* persistent thread blocks per launch */
+    int32_t graphs;         /* CUDA graphs the launches were captured in */
+} nasch_batch_info;
+
+int nasch_submit(const nasch_params *roads, int64_t n_roads, const int64_t *steps, nasch_batch *out);
+
+/* Wait up to timeout_ms (< 0: no limit) for the batch to finish.  Returns
+ * NASCH_OK, NASCH_ETIMEOUT if it is still running (nothing is lost; wait
+ * again), or NASCH_ECANCELED if it was cancelled. */
+int nasch_batch_wait(nasch_batch b, int64_t timeout_ms);
+
+/* Ask the batch to stop: launches still to run skip their work.  The batch
+ * must still be waited for before its results (then undefined) or memory
+ * are released. */
+int nasch_batch_cancel(nasch_batch b);
+
+/* Final state and statistics of road i (after nasch_batch_wait returned OK).
+ * Statistics are indexed by the road's global step (0 .. steps[i]-1). */
+int nasch_batch_read_state(nasch_batch b, int64_t i, int32_t *x_host, uint8_t *v_host, int64_t cap);
+int nasch_batch_read_grid(nasch_batch b, int64_t i, int8_t *cells_host, int64_t cap);
+int nasch_batch_stats(nasch_batch b, int64_t i, uint64_t first_step, int64_t count, uint64_t *sum_v_host,
+                      uint64_t *crossings_host);
+/* Sums of the per-step statistics of road i over steps [first, first + count). */
+int nasch_batch_stats_sum(nasch_batch b, int64_t i, uint64_t first_step, int64_t count, uint64_t *sum_v_total,
+                          uint64_t *crossings_total);
+int nasch_batch_get_info(nasch_batch b, nasch_batch_info *info);
+/* Layout chosen for road i (NASCH_LAYOUT_AGENT or NASCH_LAYOUT_GRID). */
+int nasch_batch_road_layout(nasch_batch b, int64_t i, int32_t *layout);
+
+/* Wait for the batch (no limit) and free it.  NULL is a no-op. */
+void nasch_batch_destroy(nasch_batch b);
+
+/* Tuning of the automatic choices (process-wide; the autotuner sets these):
+ * rho_star - density below which AUTO picks the agent layout (default 0.2,
+ * the state-byte crossover 10 rho = 2); k_agent, k_grid - fused steps per
+ * launch of tiled roads (0 leaves a value unchanged). */
+int nasch_set_tuning(double rho_star, int32_t k_agent, int32_t k_grid);
+int nasch_get_tuning(double *rho_star, int32_t *k_agent, int32_t *k_grid);
+
 /* Calibration: the rate (draws per second) at which the GPU evaluates the
  * rule-3 draw, word 0 of Philox4x32-10, with nothing else to do - the
  * integer-pipe ceiling of the step, one draw per car-step.  Runs one

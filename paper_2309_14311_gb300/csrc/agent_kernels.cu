@@ -18,141 +18,10 @@
 //
 // Ring kernel.  For N <= 8192 one block holds the whole ring and runs any
 // number of steps in one launch, with the exact ring neighbour and no halo.
-#include "kernels.h"
+#include "tile_device.cuh"
 
 namespace nasch {
 namespace {
-
-// R consecutive cars starting at car g (g a multiple of 8): x by 16-byte
-// loads, v by 8-byte loads.
-template <int R>
-__device__ __forceinline__ void load_cars_vec(const int32_t *__restrict__ x_in,
-                                              const uint8_t *__restrict__ v_in, uint32_t g,
-                                              uint32_t (&x)[R], uint32_t (&v)[R])
-{
-    static_assert(R % 8 == 0, "vector path loads 8 cars at a time");
-#pragma unroll
-    for (int q = 0; q < R / 4; ++q) {
-        const int4 xq = __ldg(reinterpret_cast<const int4 *>(x_in + g) + q);
-        x[4 * q] = (uint32_t)xq.x;
-        x[4 * q + 1] = (uint32_t)xq.y;
-        x[4 * q + 2] = (uint32_t)xq.z;
-        x[4 * q + 3] = (uint32_t)xq.w;
-    }
-#pragma unroll
-    for (int q = 0; q < R / 8; ++q) {
-        const uint2 vv = __ldg(reinterpret_cast<const uint2 *>(v_in + g) + q);
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            v[8 * q + r] = (vv.x >> (8 * r)) & 0xFFu;
-            v[8 * q + r + 4] = (vv.y >> (8 * r)) & 0xFFu;
-        }
-    }
-}
-
-template <int R>
-__device__ __forceinline__ void store_cars_vec(int32_t *__restrict__ x_out,
-                                               uint8_t *__restrict__ v_out, uint32_t g,
-                                               const uint32_t (&x)[R], const uint32_t (&v)[R])
-{
-    static_assert(R % 8 == 0, "vector path stores 8 cars at a time");
-#pragma unroll
-    for (int q = 0; q < R / 4; ++q)
-        reinterpret_cast<int4 *>(x_out + g)[q] =
-            make_int4((int)x[4 * q], (int)x[4 * q + 1], (int)x[4 * q + 2], (int)x[4 * q + 3]);
-#pragma unroll
-    for (int q = 0; q < R / 8; ++q) {
-        uint2 vv;
-        vv.x = v[8 * q] | (v[8 * q + 1] << 8) | (v[8 * q + 2] << 16) | (v[8 * q + 3] << 24);
-        vv.y = v[8 * q + 4] | (v[8 * q + 5] << 8) | (v[8 * q + 6] << 16) | (v[8 * q + 7] << 24);
-        reinterpret_cast<uint2 *>(v_out + g)[q] = vv;
-    }
-}
-
-// How rule 3 is decided for a whole launch: p = 0 never slows down, p = 1
-// always does (no draw needed), anything else draws.
-enum class Draw { kNever, kAlways, kPhilox };
-
-// One warp-tile: 32 lanes x R consecutive cars in registers.  kFull: the
-// tile lies inside [0, N) and every owned car of a lane is owned (lanes are
-// either all-owned or all-halo), so no per-car ownership test is needed.
-template <int R, Draw D, bool kFull>
-__device__ __forceinline__ void agent_warp_tile(const AgentStep &a, uint32_t t0, uint32_t owned,
-                                                unsigned long long *s_sum, unsigned long long *s_cross)
-{
-    const uint32_t lane = threadIdx.x & 31u;
-    const uint32_t e0 = lane * R;
-    const uint32_t N = a.N;
-    const uint32_t L = a.rc.L;
-    const uint32_t Lm1 = L - 1u;
-    const uint32_t vmax = a.rc.vmax;
-    const uint32_t thr = (uint32_t)a.rc.thr;
-    uint32_t x[R], v[R];
-    if (kFull) {
-        load_cars_vec<R>(a.x_in, a.v_in, t0 + e0, x, v);
-    } else {
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const uint32_t g = (t0 + e0 + (uint32_t)r) % N;   // halo wraps round the ring
-            x[r] = (uint32_t)a.x_in[g];
-            v[r] = a.v_in[g];
-        }
-    }
-    // cars of this lane that the tile owns (statistics and write-back)
-    const uint32_t own_end = min(owned, N - t0);
-    const uint32_t n_own = e0 >= own_end ? 0u : min((uint32_t)R, own_end - e0);
-
-    for (int s = 0; s < a.ksteps; ++s) {
-        const uint32_t step = a.step0 + (uint32_t)s;
-        // leader of the lane's last car: the next lane's first car (start-of-step)
-        const uint32_t lead_last = __shfl_down_sync(0xFFFFFFFFu, x[0], 1);
-        uint32_t tsum = 0, tcross = 0;
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const uint32_t xi = x[r];
-            const uint32_t lead = (r + 1 < R) ? x[r + 1] : lead_last;
-            // empty cells ahead on the ring: (lead - x - 1) mod L, or L - 1 if
-            // the car is its own leader; as the smaller of two unsigned values
-            const uint32_t d = lead - xi;
-            const uint32_t gap = min(d - 1u, d + Lm1);
-            uint32_t vel = min(min(v[r] + 1u, vmax), gap);            // rules 1, 2
-            if (D == Draw::kAlways) {
-                vel -= vel > 0u ? 1u : 0u;                              // rule 3, p = 1
-            } else if (D == Draw::kPhilox) {
-                const uint32_t u = philox_word0(xi, step, a.rc.road, kTagSlowdown, a.rc.key0, a.rc.key1);
-                vel -= (vel > 0u && u < thr) ? 1u : 0u;                 // rule 3
-            }
-            uint32_t nx = xi + vel;                                     // rule 4
-            const bool wrap = nx >= L;
-            nx = wrap ? nx - L : nx;
-            x[r] = nx;
-            v[r] = vel;
-            if (kFull || (uint32_t)r < n_own) {
-                tsum += vel;
-                tcross += wrap ? 1u : 0u;
-            }
-        }
-        if (kFull && n_own == 0u) tsum = tcross = 0u;   // halo lanes
-        tsum = __reduce_add_sync(0xFFFFFFFFu, tsum);
-        tcross = __reduce_add_sync(0xFFFFFFFFu, tcross);
-        if (lane == 0 && (tsum | tcross)) {
-            atomicAdd(&s_sum[s], (unsigned long long)tsum);
-            atomicAdd(&s_cross[s], (unsigned long long)tcross);
-        }
-    }
-
-    if (n_own == (uint32_t)R) {
-        store_cars_vec<R>(a.x_out, a.v_out, t0 + e0, x, v);
-    } else {
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            if ((uint32_t)r < n_own) {
-                a.x_out[t0 + e0 + r] = (int32_t)x[r];
-                a.v_out[t0 + e0 + r] = (uint8_t)v[r];
-            }
-        }
-    }
-}
 
 // Persistent grid of independent warps; warp w takes warp-tiles w, w + W, ...
 template <int R, Draw D>
@@ -183,87 +52,15 @@ __global__ void __launch_bounds__(kAgentThreads) agent_tiled_kernel(const AgentS
     }
 }
 
-// Whole ring in one block: thread t holds cars [t*R, t*R + R) of the N cars;
-// the car after thread t's last car is thread t+1's first, or car 0.
+// Whole ring in one block (N <= 1024 * R).
 template <int R>
 __global__ void __launch_bounds__(1024) agent_ring_kernel(const AgentStep a)
 {
-    __shared__ uint32_t s_first[2][1024];
-    __shared__ uint32_t s_psum[2][32];
-    __shared__ uint32_t s_pcross[2][32];
-
-    const uint32_t N = a.N;
-    const uint32_t tid = threadIdx.x;
-    const uint32_t lane = tid & 31u, warp = tid >> 5;
-    const uint32_t nwarps = blockDim.x >> 5;
-    const uint32_t e0 = tid * R;
-    const int cnt = e0 < N ? (int)min((uint32_t)R, N - e0) : 0;
-    const uint32_t next_owner = (e0 + R < N) ? tid + 1 : 0u;
-    const RoadConst rc = a.rc;
-
-    uint32_t x[R], v[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        x[r] = r < cnt ? (uint32_t)a.x_in[e0 + r] : 0u;
-        v[r] = r < cnt ? (uint32_t)a.v_in[e0 + r] : 0u;
-    }
-
-    for (int s = 0; s < a.ksteps; ++s) {
-        const uint32_t ph = (uint32_t)s & 1u;
-        const uint32_t step = a.step0 + (uint32_t)s;
-        if (cnt > 0) s_first[ph][tid] = x[0];
-        __syncthreads();
-        if (tid == 0 && s > 0) {
-            unsigned long long sv = 0, cr = 0;
-            for (uint32_t w = 0; w < nwarps; ++w) {
-                sv += s_psum[ph ^ 1u][w];
-                cr += s_pcross[ph ^ 1u][w];
-            }
-            a.sum_v[s - 1] = sv;
-            a.crossings[s - 1] = cr;
-        }
-        const uint32_t lead_last = s_first[ph][next_owner];
-        uint32_t tsum = 0, tcross = 0;
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            if (r < cnt) {
-                const uint32_t xi = x[r];
-                const uint32_t lead = (r + 1 < cnt) ? x[r + 1] : lead_last;
-                const uint32_t vel = new_velocity(rc, v[r], agent_gap(xi, lead, rc.L), xi, step);
-                uint32_t nx = xi + vel;
-                const bool wrap = nx >= rc.L;
-                if (wrap) nx -= rc.L;
-                x[r] = nx;
-                v[r] = vel;
-                tsum += vel;
-                tcross += wrap ? 1u : 0u;
-            }
-        }
-        tsum = __reduce_add_sync(0xFFFFFFFFu, tsum);
-        tcross = __reduce_add_sync(0xFFFFFFFFu, tcross);
-        if (lane == 0) {
-            s_psum[ph][warp] = tsum;
-            s_pcross[ph][warp] = tcross;
-        }
-    }
-    __syncthreads();
-    if (tid == 0 && a.ksteps > 0) {
-        const uint32_t ph = (uint32_t)(a.ksteps - 1) & 1u;
-        unsigned long long sv = 0, cr = 0;
-        for (uint32_t w = 0; w < nwarps; ++w) {
-            sv += s_psum[ph][w];
-            cr += s_pcross[ph][w];
-        }
-        a.sum_v[a.ksteps - 1] = sv;
-        a.crossings[a.ksteps - 1] = cr;
-    }
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        if (r < cnt) {
-            a.x_out[e0 + r] = (int32_t)x[r];
-            a.v_out[e0 + r] = (uint8_t)v[r];
-        }
-    }
+    __shared__ uint32_t s_first[2 * 1024];
+    __shared__ uint32_t s_psum[2 * 32];
+    __shared__ uint32_t s_pcross[2 * 32];
+    agent_ring_steps<R>(a.x_in, a.v_in, a.x_out, a.v_out, a.N, a.rc, a.step0, a.ksteps, a.sum_v, a.crossings,
+                        s_first, s_psum, s_pcross);
 }
 
 __global__ void scatter_agent_to_grid_kernel(const int32_t *__restrict__ x,

@@ -1,0 +1,63 @@
+// Device-side structures of batched runs (internal to the library).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "kernels.h"
+
+namespace nasch {
+
+// How one road of a batch is stepped.
+enum BatchType : uint32_t {
+    kBatchAgentTile = 0,   // agent layout, warp-tiles of 256 cars, 8 per item
+    kBatchGridTile = 1,    // grid layout, one staged 8192-cell span per item
+    kBatchAgentRing = 2,   // agent layout, N <= 2048: the whole ring in one item
+    kBatchGridRing = 3,    // grid layout, L <= 8192: the whole ring in one item
+};
+
+constexpr int kBatchThreads = 256;
+constexpr int kBatchAgentR = 8;                                       // cars per lane
+constexpr uint32_t kBatchAgentSpan = 32u * kBatchAgentR;              // cars per warp-tile
+constexpr uint32_t kBatchRingCars = kBatchThreads * kBatchAgentR;     // 2048
+constexpr uint32_t kBatchRingCells = (uint32_t)kGridSpan;             // 8192
+
+struct BatchRoadDev {
+    uint32_t L, N, vmax, type;
+    uint64_t thr;
+    uint32_t key0, key1, road_id, k;   // k: steps per super-step
+    uint32_t T;                        // steps to run
+    uint32_t step0;                    // global index of the first step
+    uint32_t halo;                     // grid: H cells per side; agent: halo cars per warp-tile
+    uint32_t tile;                     // grid: owned cells per item; agent: owned cars per warp-tile
+    int32_t *x[2];
+    uint8_t *v[2];
+    int8_t *cells[2];
+    unsigned long long *sum_v;         // [T]
+    unsigned long long *crossings;     // [T]
+};
+
+struct BatchItem {
+    uint32_t road;
+    uint32_t tile;
+};
+
+struct BatchLaunch {
+    const BatchRoadDev *roads;
+    const BatchItem *items;
+    uint32_t n_items;                  // active items this super-step (a prefix of the list)
+    uint32_t super_step;
+    uint32_t *counter;                 // work-list cursor of this super-step (starts at 0)
+    const volatile uint32_t *cancel;   // host-mapped; nonzero: skip remaining work
+    uint32_t padded;                   // grid buffer length (max over the batch's grid roads)
+};
+
+size_t batch_smem_bytes(uint32_t padded);
+int batch_blocks_per_sm(uint32_t padded);
+cudaError_t launch_batch_super_step(const BatchLaunch &bl, int blocks, cudaStream_t s);
+// Floyd initial positions for every road: bit maps, then x[0] (agent) or
+// cells[0] (grid; cells must already hold -1).
+cudaError_t launch_batch_floyd(const BatchRoadDev *roads, uint32_t n, uint64_t *const *bitmaps, int sms,
+                               cudaStream_t s);
+
+}  // namespace nasch

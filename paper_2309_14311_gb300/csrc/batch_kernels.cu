@@ -1,0 +1,336 @@
+// Batched NaSch: many independent roads advanced together (the paper's
+// "Variations": a parameter study as embarrassingly parallel work).
+//
+// One launch per super-step.  A persistent grid of 256-thread blocks pulls
+// items from the super-step's work-list with an atomic cursor; an item is a
+// piece of one road and runs that road's k fused steps:
+//   agent tile: 8 warp-tiles of 256 consecutive cars (32 lanes x 8 cars in
+//               registers, leader by warp shuffle, halo of round_up(k, 8));
+//   grid tile:  one staged 8192-cell span (tile + halos of round_up(k*vmax,16));
+//   agent ring: a whole ring of N <= 2048 cars in one block;
+//   grid ring:  a whole ring of L <= 8192 cells in shared memory.
+// The step code is the single-road kernels' (tile_device.cuh), so a road in
+// a batch computes exactly what it computes alone.  Per-step statistics are
+// reduced per block and added to the road's series.  A host-mapped flag lets
+// the host cancel: items pulled after it is set do nothing.
+//
+// Initial positions come from Floyd's algorithm run on the GPU, one thread
+// per road, into a bit map of the road's cells (sorted positions are then
+// the set bits in order).
+#include "batch_internal.h"
+#include "tile_device.cuh"
+
+namespace nasch {
+namespace {
+
+template <Draw D>
+__device__ __forceinline__ void batch_agent_tile(const BatchRoadDev &rd, const RoadConst &rc, uint32_t item_tile,
+                                                 uint32_t par, uint32_t step0, int kk, unsigned long long *s_sum,
+                                                 unsigned long long *s_cross)
+{
+    const uint32_t warp = threadIdx.x >> 5;
+    const uint32_t owned = rd.tile;
+    const uint32_t t0 = (item_tile * (uint32_t)(kBatchThreads / 32) + warp) * owned;
+    if (t0 >= rd.N) return;
+    AgentStep a;
+    a.status = nullptr;
+    // select by branch, not by index, so the descriptor stays in registers
+    a.x_in = par ? rd.x[1] : rd.x[0];
+    a.v_in = par ? rd.v[1] : rd.v[0];
+    a.x_out = par ? rd.x[0] : rd.x[1];
+    a.v_out = par ? rd.v[0] : rd.v[1];
+    a.N = rd.N;
+    a.rc = rc;
+    a.step0 = step0;
+    a.ksteps = kk;
+    a.sum_v = nullptr;
+    a.crossings = nullptr;
+    if (t0 + kBatchAgentSpan <= rd.N)
+        agent_warp_tile<kBatchAgentR, D, true>(a, t0, owned, s_sum, s_cross);
+    else
+        agent_warp_tile<kBatchAgentR, D, false>(a, t0, owned, s_sum, s_cross);
+}
+
+template <Draw D, bool kWide>
+__device__ __forceinline__ void batch_grid_tile(const BatchRoadDev &rd, const RoadConst &rc, uint32_t item_tile,
+                                                uint32_t par, uint32_t step0, int kk, uint32_t padded, int8_t *pool,
+                                                uint16_t (*s_list)[1024], unsigned long long *s_sum,
+                                                unsigned long long *s_cross)
+{
+    const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+    const uint32_t L = rd.L, H = rd.halo, C = rd.tile;
+    const uint32_t W = (uint32_t)kGridSpan;
+    GridTileGeom geo;
+    geo.halo = H;
+    geo.tile = C;
+    geo.padded = padded;
+    geo.n_tiles = 0;
+    geo.nwork = 3;
+    int8_t *stage = pool;
+    auto work = [&](uint32_t b) { return pool + (1u + b) * padded; };
+    const int8_t *c_in = par ? rd.cells[1] : rd.cells[0];
+    int8_t *c_out = par ? rd.cells[0] : rd.cells[1];
+    const uint32_t t0 = item_tile * C;
+    const uint32_t own_cells = min(C, L - t0);
+    const uint32_t base = t0 >= H ? t0 - H : t0 + L - H;
+
+    if (t0 >= H && t0 + C + H <= L) {
+        const uint4 *src = reinterpret_cast<const uint4 *>(c_in + (t0 - H));
+        for (uint32_t c = tid; c < W / 16u; c += kBatchThreads) reinterpret_cast<uint4 *>(stage)[c] = __ldg(src + c);
+    } else {
+        for (uint32_t i = tid; i < W; i += kBatchThreads) {
+            uint32_t cell = base + i;
+            if (cell >= L) cell -= L;
+            stage[i] = c_in[cell];
+        }
+    }
+    for (uint32_t c = W / 16u + tid; c < padded / 16u; c += kBatchThreads) reinterpret_cast<uint4 *>(stage)[c] = kEmpty4;
+    for (uint32_t c = tid; c < padded / 16u; c += kBatchThreads) reinterpret_cast<uint4 *>(work(0))[c] = kEmpty4;
+    __syncthreads();
+
+    const int8_t *cur = stage;
+    for (int s = 0; s < kk; ++s) {
+        const uint32_t o = (uint32_t)s % 3u;
+        int8_t *nxt = work(o);
+        int8_t *clr = work(o == 2u ? 0u : o + 1u);
+        uint32_t tsum = 0, tcross = 0;
+        grid_step<D, kWide>(rc, cur, nxt, clr, geo, own_cells, base, step0 + (uint32_t)s, s_list[warp], tsum, tcross);
+        tsum = __reduce_add_sync(0xFFFFFFFFu, tsum);
+        tcross = __reduce_add_sync(0xFFFFFFFFu, tcross);
+        if (lane == 0 && (tsum | tcross)) {
+            atomicAdd(&s_sum[s], (unsigned long long)tsum);
+            atomicAdd(&s_cross[s], (unsigned long long)tcross);
+        }
+        __syncthreads();
+        cur = nxt;
+    }
+    if (own_cells == C) {
+        const uint4 *f4 = reinterpret_cast<const uint4 *>(cur + H);
+        uint4 *dst = reinterpret_cast<uint4 *>(c_out + t0);
+        for (uint32_t c = tid; c < C / 16u; c += kBatchThreads) dst[c] = f4[c];
+    } else {
+        for (uint32_t i = tid; i < own_cells; i += kBatchThreads) c_out[t0 + i] = cur[H + i];
+    }
+}
+
+template <Draw D>
+__device__ __forceinline__ void batch_item(const BatchRoadDev &rd, const RoadConst &rc, uint32_t item_tile,
+                                           uint32_t par, uint32_t step0, int kk, uint32_t padded, int8_t *pool,
+                                           uint16_t (*s_list)[1024], uint32_t *s_first, uint32_t *s_psum,
+                                           uint32_t *s_pcross, unsigned long long *s_sum, unsigned long long *s_cross)
+{
+    switch (rd.type) {
+    case kBatchAgentTile:
+        batch_agent_tile<D>(rd, rc, item_tile, par, step0, kk, s_sum, s_cross);
+        break;
+    case kBatchGridTile:
+        if (rd.vmax > 16u)
+            batch_grid_tile<D, true>(rd, rc, item_tile, par, step0, kk, padded, pool, s_list, s_sum, s_cross);
+        else
+            batch_grid_tile<D, false>(rd, rc, item_tile, par, step0, kk, padded, pool, s_list, s_sum, s_cross);
+        break;
+    case kBatchAgentRing:
+        agent_ring_steps<kBatchAgentR>(par ? rd.x[1] : rd.x[0], par ? rd.v[1] : rd.v[0], par ? rd.x[0] : rd.x[1],
+                                       par ? rd.v[0] : rd.v[1], rd.N, rc, step0, kk, s_sum, s_cross, s_first, s_psum,
+                                       s_pcross);
+        break;
+    default:
+        grid_ring_steps(par ? rd.cells[1] : rd.cells[0], par ? rd.cells[0] : rd.cells[1], rc, step0, kk, pool,
+                        pool + padded, s_sum, s_cross, s_psum, s_pcross);
+        break;
+    }
+}
+
+__global__ void __launch_bounds__(kBatchThreads, 3) batch_kernel(const BatchLaunch bl)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ uint16_t s_list[kBatchThreads / 32][1024];
+    __shared__ uint32_t s_first[2 * kBatchThreads];
+    __shared__ uint32_t s_psum[2 * 32];
+    __shared__ uint32_t s_pcross[2 * 32];
+    __shared__ unsigned long long s_sum[kMaxFusedSteps];
+    __shared__ unsigned long long s_cross[kMaxFusedSteps];
+    __shared__ uint32_t s_item;
+    int8_t *const pool = reinterpret_cast<int8_t *>(smem);
+    const uint32_t tid = threadIdx.x;
+
+    for (;;) {
+        if (tid == 0) {
+            uint32_t i = atomicAdd(bl.counter, 1u);
+            if (*bl.cancel) i = 0xFFFFFFFFu;
+            s_item = i;
+        }
+        __syncthreads();
+        const uint32_t i = s_item;
+        if (i >= bl.n_items) break;
+        const BatchItem it = bl.items[i];
+        const BatchRoadDev rd = bl.roads[it.road];
+        const uint32_t s0 = bl.super_step * rd.k;
+        const int kk = (int)min(rd.k, rd.T - s0);
+        const uint32_t par = bl.super_step & 1u;
+        const uint32_t step0 = rd.step0 + s0;
+        RoadConst rc;
+        rc.L = rd.L;
+        rc.vmax = rd.vmax;
+        rc.thr = rd.thr;
+        rc.key0 = rd.key0;
+        rc.key1 = rd.key1;
+        rc.road = rd.road_id;
+        for (int j = tid; j < kk; j += kBatchThreads) {
+            s_sum[j] = 0ull;
+            s_cross[j] = 0ull;
+        }
+        __syncthreads();
+        switch (draw_mode(rd.thr)) {
+        case Draw::kNever:
+            batch_item<Draw::kNever>(rd, rc, it.tile, par, step0, kk, bl.padded, pool, s_list, s_first, s_psum,
+                                     s_pcross, s_sum, s_cross);
+            break;
+        case Draw::kAlways:
+            batch_item<Draw::kAlways>(rd, rc, it.tile, par, step0, kk, bl.padded, pool, s_list, s_first, s_psum,
+                                      s_pcross, s_sum, s_cross);
+            break;
+        default:
+            batch_item<Draw::kPhilox>(rd, rc, it.tile, par, step0, kk, bl.padded, pool, s_list, s_first, s_psum,
+                                      s_pcross, s_sum, s_cross);
+            break;
+        }
+        __syncthreads();
+        for (int j = tid; j < kk; j += kBatchThreads) {
+            if (s_sum[j]) atomicAdd(&rd.sum_v[s0 + j], s_sum[j]);
+            if (s_cross[j]) atomicAdd(&rd.crossings[s0 + j], s_cross[j]);
+        }
+    }
+}
+
+// Floyd's algorithm (Bentley & Floyd, CACM 1987), one thread per road: for
+// m = 0..N-1 with j = L-N+m, draw t uniform on 0..j (Lemire's multiply-shift
+// of the Philox word pair of counter (m, 0, road, 1)) and set bit t, or bit
+// j if t is already set.  The draws do not depend on the set, so eight are
+// made at a time and their bit-map words loaded together; the set updates
+// then go in order, an earlier pick of the same group counting as set.
+constexpr int kFloydGroup = 8;
+
+__global__ void batch_floyd_bits_kernel(const BatchRoadDev *roads, uint32_t n, uint64_t *const *bitmaps)
+{
+    const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const BatchRoadDev rd = roads[r];
+    uint64_t *bm = bitmaps[r];
+    const uint64_t L = rd.L, N = rd.N;
+    for (uint64_t m0 = 0; m0 < N; m0 += kFloydGroup) {
+        uint64_t t[kFloydGroup], word[kFloydGroup], pick[kFloydGroup];
+#pragma unroll
+        for (int b = 0; b < kFloydGroup; ++b) {
+            const uint64_t m = m0 + (uint64_t)b;
+            t[b] = 0;
+            word[b] = 0;
+            if (m < N) {
+                const uint64_t j = L - N + m;
+                const Words4 w = philox4x32_10((uint32_t)m, 0u, rd.road_id, kTagInit, rd.key0, rd.key1);
+                const uint64_t rr = ((uint64_t)w.w1 << 32) | w.w0;
+                t[b] = __umul64hi(rr, j + 1);
+                word[b] = __ldcg(reinterpret_cast<const unsigned long long *>(bm) + (t[b] >> 6));
+            }
+        }
+#pragma unroll
+        for (int b = 0; b < kFloydGroup; ++b) {
+            const uint64_t m = m0 + (uint64_t)b;
+            pick[b] = 0;
+            if (m < N) {
+                const uint64_t j = L - N + m;
+                bool taken = (word[b] >> (t[b] & 63)) & 1ull;
+#pragma unroll
+                for (int b2 = 0; b2 < b; ++b2) taken = taken || pick[b2] == t[b];
+                pick[b] = taken ? j : t[b];
+                atomicOr(reinterpret_cast<unsigned long long *>(bm + (pick[b] >> 6)), 1ull << (pick[b] & 63));
+            }
+        }
+    }
+}
+
+// Bit map -> state, one block per road: agent roads get their sorted
+// positions (a block-wide prefix sum over the words' bit counts), grid roads
+// a 0 (a car at rest) on every chosen cell.
+__global__ void __launch_bounds__(256) batch_floyd_expand_kernel(const BatchRoadDev *roads, uint32_t n,
+                                                                 uint64_t *const *bitmaps)
+{
+    __shared__ uint32_t s_warp[8];
+    __shared__ uint32_t s_total;
+    const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+    for (uint32_t r = blockIdx.x; r < n; r += gridDim.x) {
+        const BatchRoadDev rd = roads[r];
+        const uint64_t *bm = bitmaps[r];
+        const uint32_t words = (rd.L + 63u) / 64u;
+        const bool grid = rd.type == kBatchGridTile || rd.type == kBatchGridRing;
+        if (grid) {
+            for (uint32_t w = tid; w < words; w += 256u)
+                for (uint64_t bits = bm[w]; bits; bits &= bits - 1) rd.cells[0][64u * w + (uint32_t)__ffsll(bits) - 1u] = 0;
+            continue;
+        }
+        uint32_t running = 0;
+        for (uint32_t base = 0; base < words; base += 256u) {
+            const uint32_t w = base + tid;
+            const uint64_t bits = w < words ? bm[w] : 0ull;
+            const uint32_t c = (uint32_t)__popcll(bits);
+            uint32_t incl = c;
+#pragma unroll
+            for (uint32_t d = 1; d < 32; d <<= 1) {
+                const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+                if (lane >= d) incl += t;
+            }
+            if (lane == 31) s_warp[warp] = incl;
+            __syncthreads();
+            if (tid == 0) {
+                uint32_t acc = 0;
+                for (int k = 0; k < 8; ++k) {
+                    const uint32_t t = s_warp[k];
+                    s_warp[k] = acc;
+                    acc += t;
+                }
+                s_total = acc;
+            }
+            __syncthreads();
+            uint32_t pos = running + s_warp[warp] + incl - c;
+            for (uint64_t b2 = bits; b2; b2 &= b2 - 1) rd.x[0][pos++] = (int32_t)(64u * w + (uint32_t)__ffsll(b2) - 1u);
+            running += s_total;
+            __syncthreads();
+        }
+    }
+}
+
+}  // namespace
+
+size_t batch_smem_bytes(uint32_t padded) { return 4u * (size_t)padded; }   // stage + three output buffers
+
+int batch_blocks_per_sm(uint32_t padded)
+{
+    const size_t smem = batch_smem_bytes(padded);
+    if (cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_kernel, kBatchThreads, smem) != cudaSuccess) return 1;
+    return n > 0 ? n : 1;
+}
+
+cudaError_t launch_batch_super_step(const BatchLaunch &bl, int blocks, cudaStream_t s)
+{
+    const size_t smem = batch_smem_bytes(bl.padded);
+    cudaError_t e = cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    batch_kernel<<<blocks, kBatchThreads, smem, s>>>(bl);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_floyd(const BatchRoadDev *roads, uint32_t n, uint64_t *const *bitmaps, int sms, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    batch_floyd_bits_kernel<<<(n + 63u) / 64u, 64, 0, s>>>(roads, n, bitmaps);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const uint32_t blocks = n < (uint32_t)sms * 8u ? n : (uint32_t)sms * 8u;
+    batch_floyd_expand_kernel<<<blocks, 256, 0, s>>>(roads, n, bitmaps);
+    return cudaGetLastError();
+}
+
+}  // namespace nasch

@@ -4,7 +4,7 @@
 // of the step; the benchmark reports the step kernels against it.
 #include <cuda_runtime.h>
 
-#include "../../include/nasch.h"
+#include "nasch.h"
 #include "kernels.h"
 #include "runtime_internal.h"
 

@@ -2,229 +2,47 @@
 // the car on it ("Concepts Covered": the grid representation; Handout,
 // model section rules 1-4).
 //
-// Tiled kernel.  A tile is kGridTileCells cells staged in shared memory with
-// a halo of H = round_up(k * vmax, 16) cells on each side: after one step a
-// cell depends on the cells within vmax of it (a car arriving from behind,
-// the gap of that car ahead), so after k fused steps the middle tile is
-// exact.  Persistent blocks walk the tiles; each tile (with its halos)
-// arrives by one bulk (TMA) copy issued while the previous tile computes,
-// completion counted on an mbarrier, and leaves by one bulk store.  Per step
-// a warp turns 16-cell chunks into occupancy bit masks (one bit per cell),
-// finds each car's gap with find-first-set on the mask of the cells ahead,
-// compacts the cars into a list so the draws are spread evenly over the
-// lanes, applies rules 1-3 and scatters each car into the next buffer,
-// which was cleared to -1 one step earlier (rotating buffers, one barrier
-// per step).  Rule 2 makes the scatter collision-free.  Statistics of the
-// cars that start the step in the tile's own cells are reduced per warp,
-// per block, and added to the per-step series once per block.  The first
-// and last tiles take their halo across the ring boundary (modular cell
-// index, plain loads).
+// Tiled kernel.  A span of kGridSpan = 8192 cells is staged in shared
+// memory: the tile's own C = 8192 - 2H cells and a halo of H =
+// round_up(k * vmax, 16) cells on each side.  After one step a cell depends
+// on the cells within vmax of it (a car arriving from behind, the gap of
+// that car ahead), so after k fused steps the middle C cells are exact.
+// Persistent blocks walk the tiles; each span arrives by one bulk (TMA)
+// copy issued while the previous tile computes, completion counted on an
+// mbarrier, and the tile leaves by one bulk store.  Per step each of the 8
+// warps takes one 1024-cell row: lanes turn their 32 cells into an
+// occupancy bit mask, the warp compacts the row's cars into a list so the
+// draws are spread evenly over the lanes, each car's gap comes from
+// find-first-set on the masks of the cells ahead, and the car is scattered
+// into the next buffer, which was cleared to -1 one step earlier (rotating
+// buffers, one barrier per step).  Rule 2 makes the scatter collision-free.
+// Statistics of the cars that start the step in the tile's own cells are
+// reduced per warp, per block, and added to the per-step series once per
+// block.  The first and last tiles take their halo across the ring boundary
+// (modular cell index, plain loads).
 //
 // Ring kernel.  For L <= kGridRingMaxCells one block holds the whole ring
 // in shared memory and runs any number of steps in one launch.
-#include "kernels.h"
+#include "tile_device.cuh"
 
 namespace nasch {
 namespace {
 
-// Occupancy bits of four cells packed in a 32-bit word (bit b = byte b has
-// its sign bit clear, i.e. holds a car).
-__device__ __forceinline__ uint32_t occupancy4(uint32_t w)
-{
-    const uint32_t m = (~w >> 7) & 0x01010101u;
-    return (m * 0x10204080u) >> 28;
-}
-
-__device__ __forceinline__ uint32_t occupancy16(const uint4 q)
-{
-    return occupancy4(q.x) | (occupancy4(q.y) << 4) | (occupancy4(q.z) << 8) | (occupancy4(q.w) << 12);
-}
-
-__device__ __forceinline__ uint32_t byte_of(const uint4 q, uint32_t j)
-{
-    const uint32_t w = j < 8u ? (j < 4u ? q.x : q.y) : (j < 12u ? q.z : q.w);
-    return (w >> (8u * (j & 3u))) & 0xFFu;
-}
-
-enum class Draw { kNever, kAlways, kPhilox };
-
-constexpr uint4 kEmpty4 = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu};
-constexpr int kGridWarps = kGridThreads / 32;
-constexpr uint32_t kRowCells = 32u * 16u;           // cells one warp scans per pass
-constexpr uint64_t kWaitLimitNs = 1000000000ull;    // bounded wait on an async copy: 1 s
-
-// ---- PTX wrappers: shared-memory mbarriers and 1-D bulk (TMA) copies ----
-__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ uint64_t global_ns()
-{
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
-
-// Orders this thread's generic-proxy shared-memory accesses before later
-// async-proxy (bulk copy) accesses.
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
-{
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(done)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return done != 0;
-}
-
-// Wait for the phase of `bar` with the given parity, for at most 1 s.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
-{
-    if (mbar_try_wait(bar, parity)) return true;
-    const uint64_t t0 = global_ns();
-    while (!mbar_try_wait(bar, parity))
-        if (global_ns() - t0 > kWaitLimitNs) return false;
-    return true;
-}
-
-// global -> shared, completion counted in bytes on `bar`
-__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
-{
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_u32(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
-                 : "memory");
-}
-
-// shared -> global, tracked by bulk groups
-__device__ __forceinline__ void bulk_store(void *dst, const void *src, uint32_t bytes)
-{
-    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_u32(src)),
-                 "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
-__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
-
-struct GridTileGeom {
-    uint32_t halo;      // H, multiple of 16
-    uint32_t width;     // W = tile + 2H cells processed per step
-    uint32_t padded;    // W + pad: buffer length (multiple of 16)
-    uint32_t n_tiles;
-    uint32_t lookahead; // chunks read beyond a car's own chunk for its gap
-    uint32_t nwork;     // rotating output buffers: 2 for k = 1, else 3
-};
-
-// One synchronous step over a staged buffer: read `cur`, scatter every car
-// into `nxt` (already all -1), and clear `clr` for the step after.  Each warp
-// scans rows of 512 cells; the cars of a row are compacted into the warp's
-// list (cell index, gap, velocity) so that every lane then applies rules 1-4
-// to the same number of cars (a lane's own cells hold 0..16 cars, which would
-// leave most lanes idle through the draws).
-template <Draw D>
-__device__ __forceinline__ void grid_step(const RoadConst &rc, const int8_t *__restrict__ cur, int8_t *nxt,
-                                          int8_t *clr, const GridTileGeom &geo, uint32_t own_cells, uint32_t base,
-                                          uint32_t step, uint32_t *list, uint32_t &tsum, uint32_t &tcross)
-{
-    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
-    const uint32_t chunks = geo.width / 16u;
-    const uint32_t H = geo.halo;
-    const uint32_t L = rc.L;
-    const uint4 *cur4 = reinterpret_cast<const uint4 *>(cur);
-    uint4 *clr4 = reinterpret_cast<uint4 *>(clr);
-    for (uint32_t c = threadIdx.x; c < geo.padded / 16u; c += kGridThreads) clr4[c] = kEmpty4;
-
-    for (uint32_t row = warp; row * 32u < chunks; row += kGridWarps) {
-        const uint32_t c = row * 32u + lane;
-        const uint4 q = c < chunks ? cur4[c] : kEmpty4;
-        uint32_t m = occupancy16(q);
-        uint32_t m_next = __shfl_down_sync(0xFFFFFFFFu, m, 1);
-        if (lane == 31 && c < chunks) m_next = occupancy16(cur4[c + 1]);
-        const uint32_t n = __popc(m);
-        uint32_t incl = n;
-#pragma unroll
-        for (uint32_t d = 1; d < 32; d <<= 1) {
-            const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, incl, d);
-            if (lane >= d) incl += t;
-        }
-        const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
-        if (total == 0) continue;
-        uint32_t pos = incl - n;
-        const uint32_t window = m | (m_next << 16);
-        while (m) {
-            const uint32_t j = (uint32_t)(__ffs(m) - 1);
-            m &= m - 1u;
-            const uint32_t after = window >> (j + 1u);
-            uint32_t gap = after ? (uint32_t)(__ffs(after) - 1) : 31u - j;
-            if (after == 0u && gap < rc.vmax) {
-                // vmax > 16: keep scanning whole chunks ahead
-                uint32_t cc = c + 2u;
-                for (uint32_t k = 1; k < geo.lookahead && gap < rc.vmax; ++k, ++cc) {
-                    const uint32_t m2 = occupancy16(cur4[cc]);
-                    if (m2) {
-                        gap += (uint32_t)(__ffs(m2) - 1);
-                        break;
-                    }
-                    gap += 16u;
-                }
-            }
-            list[pos++] = ((c * 16u + j) << 16) | (min(gap, 255u) << 8) | byte_of(q, j);
-        }
-        __syncwarp();
-        for (uint32_t i = lane; i < total; i += 32u) {
-            const uint32_t e = list[i];
-            const uint32_t idx = e >> 16;
-            uint32_t cell = base + idx;
-            if (cell >= L) cell -= L;
-            uint32_t vel = min(min((e & 0xFFu) + 1u, rc.vmax), (e >> 8) & 0xFFu);   // rules 1, 2
-            if (D == Draw::kAlways) {
-                vel -= vel > 0u ? 1u : 0u;                                          // rule 3, p = 1
-            } else if (D == Draw::kPhilox) {
-                const uint32_t u = philox_word0(cell, step, rc.road, kTagSlowdown, rc.key0, rc.key1);
-                vel -= (vel > 0u && u < (uint32_t)rc.thr) ? 1u : 0u;                // rule 3
-            }
-            nxt[idx + vel] = (int8_t)vel;                                           // rule 4
-            if (idx - H < own_cells) {
-                tsum += vel;
-                tcross += (cell + vel >= L) ? 1u : 0u;
-            }
-        }
-        __syncwarp();
-    }
-}
-
-template <Draw D>
+template <Draw D, bool kWide>
 __global__ void __launch_bounds__(kGridThreads) grid_tiled_kernel(const GridStep g, const GridTileGeom geo)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t s_full[2];
     __shared__ unsigned long long s_sum[kMaxFusedSteps];
     __shared__ unsigned long long s_cross[kMaxFusedSteps];
-    __shared__ uint32_t s_list[kGridWarps][kRowCells];
+    __shared__ uint16_t s_list[kGridWarps][kRowCells];
 
     const RoadConst rc = g.rc;
     const uint32_t L = rc.L;
     const uint32_t H = geo.halo;
-    const uint32_t W = geo.width;
+    const uint32_t C = geo.tile;
+    const uint32_t W = (uint32_t)kGridSpan;
     const uint32_t WP = geo.padded;
-    const uint32_t C = (uint32_t)kGridTileCells;
     const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
     int8_t *const pool = reinterpret_cast<int8_t *>(smem);
     // buffers: stage 0, stage 1 (bulk-load targets), then nwork output buffers
@@ -298,10 +116,12 @@ __global__ void __launch_bounds__(kGridThreads) grid_tiled_kernel(const GridStep
 
         const int8_t *cur = in;
         for (int s = 0; s < g.ksteps; ++s) {
-            int8_t *nxt = work((wa + (uint32_t)s) % geo.nwork);
-            int8_t *clr = work((wa + (uint32_t)s + 1u) % geo.nwork);
+            const uint32_t o = (wa + (uint32_t)s) % geo.nwork;
+            int8_t *nxt = work(o);
+            int8_t *clr = work(o + 1u == geo.nwork ? 0u : o + 1u);
             uint32_t tsum = 0, tcross = 0;
-            grid_step<D>(rc, cur, nxt, clr, geo, own_cells, base, g.step0 + (uint32_t)s, s_list[warp], tsum, tcross);
+            grid_step<D, kWide>(rc, cur, nxt, clr, geo, own_cells, base, g.step0 + (uint32_t)s, s_list[warp], tsum,
+                                tcross);
             tsum = __reduce_add_sync(0xFFFFFFFFu, tsum);
             tcross = __reduce_add_sync(0xFFFFFFFFu, tcross);
             if (lane == 0 && (tsum | tcross)) {
@@ -332,78 +152,26 @@ __global__ void __launch_bounds__(kGridThreads) grid_tiled_kernel(const GridStep
     }
 }
 
-// Whole ring in one block.  Cells [0, L) plus the successor grid in shared
-// memory; gaps and moves wrap modulo L.
+// Whole ring in one block (L <= kGridRingMaxCells).
 __global__ void __launch_bounds__(1024) grid_ring_kernel(const GridStep g)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ uint32_t s_psum[32];
     __shared__ uint32_t s_pcross[32];
-    const RoadConst rc = g.rc;
-    const uint32_t L = rc.L;
-    const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
-    const uint32_t nwarps = blockDim.x >> 5;
     int8_t *cur = reinterpret_cast<int8_t *>(smem);
-    int8_t *nxt = cur + ((L + 15u) / 16u) * 16u;
-
-    for (uint32_t i = tid; i < L; i += blockDim.x) cur[i] = g.c_in[i];
-    for (int s = 0; s < g.ksteps; ++s) {
-        const uint32_t step = g.step0 + (uint32_t)s;
-        for (uint32_t i = tid; i < L; i += blockDim.x) nxt[i] = -1;
-        __syncthreads();
-        uint32_t tsum = 0, tcross = 0;
-        for (uint32_t i = tid; i < L; i += blockDim.x) {
-            const int8_t here = cur[i];
-            if (here < 0) continue;
-            const uint32_t limit = min((uint32_t)here + 1u, rc.vmax);
-            uint32_t gap = 0;
-            uint32_t ahead = i + 1u == L ? 0u : i + 1u;
-            while (gap < limit && cur[ahead] < 0) {   // reaches the car itself after L-1 cells
-                ++gap;
-                ahead = ahead + 1u == L ? 0u : ahead + 1u;
-            }
-            const uint32_t vel = new_velocity(rc, (uint32_t)here, gap, i, step);
-            uint32_t dest = i + vel;
-            const bool wrap = dest >= L;
-            if (wrap) dest -= L;
-            nxt[dest] = (int8_t)vel;
-            tsum += vel;
-            tcross += wrap ? 1u : 0u;
-        }
-        tsum = __reduce_add_sync(0xFFFFFFFFu, tsum);
-        tcross = __reduce_add_sync(0xFFFFFFFFu, tcross);
-        if (lane == 0) {
-            s_psum[warp] = tsum;
-            s_pcross[warp] = tcross;
-        }
-        __syncthreads();
-        if (tid == 0) {
-            unsigned long long sv = 0, cr = 0;
-            for (uint32_t w = 0; w < nwarps; ++w) {
-                sv += s_psum[w];
-                cr += s_pcross[w];
-            }
-            g.sum_v[s] = sv;
-            g.crossings[s] = cr;
-        }
-        int8_t *t = cur;
-        cur = nxt;
-        nxt = t;
-        // the next step's clear of nxt (the old cur) must wait for this step's
-        // reads, and thread 0's reads of s_psum for the next step's writes
-        __syncthreads();
-    }
-    for (uint32_t i = tid; i < L; i += blockDim.x) g.c_out[i] = cur[i];
+    int8_t *nxt = cur + ((g.rc.L + 15u) / 16u) * 16u;
+    grid_ring_steps(g.c_in, g.c_out, g.rc, g.step0, g.ksteps, cur, nxt, g.sum_v, g.crossings, s_psum, s_pcross);
 }
 
 GridTileGeom make_geom(int ksteps, uint32_t vmax, uint32_t L)
 {
     GridTileGeom geo;
     geo.halo = grid_halo(ksteps, vmax);
-    geo.width = (uint32_t)kGridTileCells + 2u * geo.halo;
-    geo.lookahead = (vmax + 15u) / 16u + 1u;
-    geo.padded = geo.width + 16u * (geo.lookahead + 1u);
-    geo.n_tiles = (L + (uint32_t)kGridTileCells - 1u) / (uint32_t)kGridTileCells;
+    geo.tile = (uint32_t)kGridSpan - 2u * geo.halo;
+    // room past the span for the last lane's look-ahead, wide-vmax byte scans
+    // and cars scattered up to vmax cells beyond it
+    geo.padded = (uint32_t)kGridSpan + 16u * ((vmax + 15u) / 16u + 2u);
+    geo.n_tiles = (L + geo.tile - 1u) / geo.tile;
     geo.nwork = ksteps == 1 ? 2u : 3u;
     return geo;
 }
@@ -412,10 +180,22 @@ size_t grid_tiled_smem(const GridTileGeom &geo) { return (2u + geo.nwork) * (siz
 
 // Static plus dynamic shared memory exceeds the default 48 KB, so the
 // dynamic size is allowed explicitly (a per-device function attribute).
-template <Draw D>
-cudaError_t prepare_grid_kernel(size_t smem)
+template <Draw D, bool kWide>
+cudaError_t launch_grid_variant(const GridStep &g, const GridTileGeom &geo, int grid, size_t smem, cudaStream_t s)
 {
-    return cudaFuncSetAttribute(grid_tiled_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(grid_tiled_kernel<D, kWide>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    grid_tiled_kernel<D, kWide><<<grid, kGridThreads, smem, s>>>(g, geo);
+    return cudaGetLastError();
+}
+
+template <bool kWide>
+cudaError_t launch_grid_draw(const GridStep &g, const GridTileGeom &geo, int grid, size_t smem, cudaStream_t s)
+{
+    if (g.rc.thr == 0) return launch_grid_variant<Draw::kNever, kWide>(g, geo, grid, smem, s);
+    if (g.rc.thr > 0xFFFFFFFFull) return launch_grid_variant<Draw::kAlways, kWide>(g, geo, grid, smem, s);
+    return launch_grid_variant<Draw::kPhilox, kWide>(g, geo, grid, smem, s);
 }
 
 }  // namespace
@@ -425,10 +205,12 @@ int grid_tiled_blocks_per_sm()
     // the common case: k = 1, vmax = 5
     const GridTileGeom geo = make_geom(1, 5, 1u << 20);
     const size_t smem = grid_tiled_smem(geo);
-    if (prepare_grid_kernel<Draw::kPhilox>(smem) != cudaSuccess) return 1;
+    if (cudaFuncSetAttribute(grid_tiled_kernel<Draw::kPhilox, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+        return 1;
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, grid_tiled_kernel<Draw::kPhilox>, kGridThreads, smem) !=
-        cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, grid_tiled_kernel<Draw::kPhilox, false>, kGridThreads,
+                                                      smem) != cudaSuccess)
         return 1;
     return n > 0 ? n : 1;
 }
@@ -436,23 +218,14 @@ int grid_tiled_blocks_per_sm()
 cudaError_t launch_grid_tiled(const GridStep &g, int blocks, cudaStream_t s)
 {
     if (g.ksteps <= 0) return cudaSuccess;
-    if (g.ksteps > kMaxFusedSteps) return cudaErrorInvalidValue;
+    if (g.ksteps > kMaxFusedSteps || g.rc.vmax > 127u) return cudaErrorInvalidValue;
     const GridTileGeom geo = make_geom(g.ksteps, g.rc.vmax, g.rc.L);
-    if (g.rc.L < geo.width) return cudaErrorInvalidValue;   // the buffer must not wrap the ring twice
+    // the tile must own cells, and the staged span must not wrap the ring twice
+    if (2u * geo.halo >= (uint32_t)kGridSpan || g.rc.L < (uint32_t)kGridSpan) return cudaErrorInvalidValue;
     const size_t smem = grid_tiled_smem(geo);
     const int grid = (int)((uint32_t)blocks < geo.n_tiles ? (uint32_t)blocks : geo.n_tiles);
-    cudaError_t e;
-    if (g.rc.thr == 0) {
-        if ((e = prepare_grid_kernel<Draw::kNever>(smem)) != cudaSuccess) return e;
-        grid_tiled_kernel<Draw::kNever><<<grid, kGridThreads, smem, s>>>(g, geo);
-    } else if (g.rc.thr > 0xFFFFFFFFull) {
-        if ((e = prepare_grid_kernel<Draw::kAlways>(smem)) != cudaSuccess) return e;
-        grid_tiled_kernel<Draw::kAlways><<<grid, kGridThreads, smem, s>>>(g, geo);
-    } else {
-        if ((e = prepare_grid_kernel<Draw::kPhilox>(smem)) != cudaSuccess) return e;
-        grid_tiled_kernel<Draw::kPhilox><<<grid, kGridThreads, smem, s>>>(g, geo);
-    }
-    return cudaGetLastError();
+    return g.rc.vmax > 16u ? launch_grid_draw<true>(g, geo, grid, smem, s)
+                           : launch_grid_draw<false>(g, geo, grid, smem, s);
 }
 
 cudaError_t launch_grid_ring(const GridStep &g, cudaStream_t s)

@@ -24,10 +24,12 @@ constexpr int kAgentTileSpanSmall = 32 * 8;
 // Whole-ring agent kernel: one block of up to 1024 threads x 8 cars.
 constexpr int kAgentRingMaxCars = 1024 * 8;
 
-// Grid tiled kernel: tile of kGridTileCells cells plus a halo of
-// round_up(k * vmax, 16) cells on each side.
+// Grid tiled kernel: a span of kGridSpan cells staged per tile = the tile's
+// own kGridSpan - 2H cells plus a halo of H = round_up(k * vmax, 16) cells on
+// each side; 8 warps, one 1024-cell row each.
 constexpr int kGridThreads = 256;
-constexpr int kGridTileCells = 8192;
+constexpr int kGridSpan = 8192;
+constexpr int kGridTileCells = kGridSpan;   // the `tile` parameter value that selects the tiled kernel
 
 // Status word bits set by kernels (read by the host after a launch).
 constexpr unsigned int kStatusTimeout = 1u;   // a bounded wait on an async copy ran out

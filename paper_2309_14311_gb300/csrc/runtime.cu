@@ -13,7 +13,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/nasch.h"
+#include "nasch.h"
 #include "kernels.h"
 #include "runtime_internal.h"
 
@@ -378,11 +378,14 @@ int nasch_create_ex(const nasch_params *prm, nasch_handle *out)
         h->ring = prm->tile == 0 && h->L <= kGridRingMaxCells;
         h->tile = kGridTileCells;
         h->k = prm->k ? prm->k : 8;
-        // the tiled kernel's buffer (tile + two halos) must not wrap the ring twice
-        if (!h->ring && h->L < (int64_t)kGridTileCells + 2 * (int64_t)grid_halo(h->k, (uint32_t)h->vmax)) {
+        // the halo round_up(k * vmax, 16) on each side must leave the tile cells
+        // of its own: clamp k so that 2 * halo < the staged span
+        const int kfit = h->vmax > 0 ? std::max(1, ((kGridSpan / 2 - 16) / h->vmax)) : kMaxFusedSteps;
+        h->k = std::min(h->k, kfit);
+        if (!h->ring && h->L < (int64_t)kGridSpan) {
             free_road(h);
-            return fail(NASCH_EINVAL, "L=%lld too short for the tiled grid kernel with k=%d, vmax=%d",
-                        (long long)h->L, h->k, h->vmax);
+            return fail(NASCH_EINVAL, "L=%lld too short for the tiled grid kernel (needs L >= %d)",
+                        (long long)h->L, kGridSpan);
         }
         h->blocks = h->sms * grid_tiled_blocks_per_sm();
         e = cudaSuccess;

@@ -4,7 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "../../include/nasch.h"
+#include "nasch.h"
 
 namespace nasch {
 

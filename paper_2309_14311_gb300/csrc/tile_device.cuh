@@ -1,0 +1,474 @@
+// Device building blocks shared by the single-road and batched kernels:
+// the agent warp-tile step, the agent whole-ring step loop, the grid
+// span step, the grid whole-ring step loop, and the PTX wrappers for
+// mbarriers and 1-D bulk (TMA) copies.  Every routine applies the four rules
+// of the handout's model section ("The Nagel-Schreckenberg traffic model",
+// rules 1-4) with the rule-3 draw keyed by (cell, step, road).
+#pragma once
+
+#include "kernels.h"
+
+namespace nasch {
+namespace {
+
+// R consecutive cars starting at car g (g a multiple of 8): x by 16-byte
+// loads, v by 8-byte loads.
+template <int R>
+__device__ __forceinline__ void load_cars_vec(const int32_t *__restrict__ x_in,
+                                              const uint8_t *__restrict__ v_in, uint32_t g,
+                                              uint32_t (&x)[R], uint32_t (&v)[R])
+{
+    static_assert(R % 8 == 0, "vector path loads 8 cars at a time");
+#pragma unroll
+    for (int q = 0; q < R / 4; ++q) {
+        const int4 xq = __ldg(reinterpret_cast<const int4 *>(x_in + g) + q);
+        x[4 * q] = (uint32_t)xq.x;
+        x[4 * q + 1] = (uint32_t)xq.y;
+        x[4 * q + 2] = (uint32_t)xq.z;
+        x[4 * q + 3] = (uint32_t)xq.w;
+    }
+#pragma unroll
+    for (int q = 0; q < R / 8; ++q) {
+        const uint2 vv = __ldg(reinterpret_cast<const uint2 *>(v_in + g) + q);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            v[8 * q + r] = (vv.x >> (8 * r)) & 0xFFu;
+            v[8 * q + r + 4] = (vv.y >> (8 * r)) & 0xFFu;
+        }
+    }
+}
+
+template <int R>
+__device__ __forceinline__ void store_cars_vec(int32_t *__restrict__ x_out,
+                                               uint8_t *__restrict__ v_out, uint32_t g,
+                                               const uint32_t (&x)[R], const uint32_t (&v)[R])
+{
+    static_assert(R % 8 == 0, "vector path stores 8 cars at a time");
+#pragma unroll
+    for (int q = 0; q < R / 4; ++q)
+        reinterpret_cast<int4 *>(x_out + g)[q] =
+            make_int4((int)x[4 * q], (int)x[4 * q + 1], (int)x[4 * q + 2], (int)x[4 * q + 3]);
+#pragma unroll
+    for (int q = 0; q < R / 8; ++q) {
+        uint2 vv;
+        vv.x = v[8 * q] | (v[8 * q + 1] << 8) | (v[8 * q + 2] << 16) | (v[8 * q + 3] << 24);
+        vv.y = v[8 * q + 4] | (v[8 * q + 5] << 8) | (v[8 * q + 6] << 16) | (v[8 * q + 7] << 24);
+        reinterpret_cast<uint2 *>(v_out + g)[q] = vv;
+    }
+}
+
+// How rule 3 is decided for a whole launch: p = 0 never slows down, p = 1
+// always does (no draw needed), anything else draws.
+enum class Draw { kNever, kAlways, kPhilox };
+
+__host__ __device__ __forceinline__ Draw draw_mode(uint64_t thr) { return thr == 0 ? Draw::kNever : (thr > 0xFFFFFFFFull ? Draw::kAlways : Draw::kPhilox); }
+
+// One warp-tile: 32 lanes x R consecutive cars in registers.  kFull: the
+// tile lies inside [0, N) and every owned car of a lane is owned (lanes are
+// either all-owned or all-halo), so no per-car ownership test is needed.
+template <int R, Draw D, bool kFull>
+__device__ __forceinline__ void agent_warp_tile(const AgentStep &a, uint32_t t0, uint32_t owned,
+                                                unsigned long long *s_sum, unsigned long long *s_cross)
+{
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t e0 = lane * R;
+    const uint32_t N = a.N;
+    const uint32_t L = a.rc.L;
+    const uint32_t Lm1 = L - 1u;
+    const uint32_t vmax = a.rc.vmax;
+    const uint32_t thr = (uint32_t)a.rc.thr;
+    uint32_t x[R], v[R];
+    if (kFull) {
+        load_cars_vec<R>(a.x_in, a.v_in, t0 + e0, x, v);
+    } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const uint32_t g = (t0 + e0 + (uint32_t)r) % N;   // halo wraps round the ring
+            x[r] = (uint32_t)a.x_in[g];
+            v[r] = a.v_in[g];
+        }
+    }
+    // cars of this lane that the tile owns (statistics and write-back)
+    const uint32_t own_end = min(owned, N - t0);
+    const uint32_t n_own = e0 >= own_end ? 0u : min((uint32_t)R, own_end - e0);
+
+    for (int s = 0; s < a.ksteps; ++s) {
+        const uint32_t step = a.step0 + (uint32_t)s;
+        // leader of the lane's last car: the next lane's first car (start-of-step)
+        const uint32_t lead_last = __shfl_down_sync(0xFFFFFFFFu, x[0], 1);
+        uint32_t tsum = 0, tcross = 0;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const uint32_t xi = x[r];
+            const uint32_t lead = (r + 1 < R) ? x[r + 1] : lead_last;
+            // empty cells ahead on the ring: (lead - x - 1) mod L, or L - 1 if
+            // the car is its own leader; as the smaller of two unsigned values
+            const uint32_t d = lead - xi;
+            const uint32_t gap = min(d - 1u, d + Lm1);
+            uint32_t vel = min(min(v[r] + 1u, vmax), gap);            // rules 1, 2
+            if (D == Draw::kAlways) {
+                vel -= vel > 0u ? 1u : 0u;                              // rule 3, p = 1
+            } else if (D == Draw::kPhilox) {
+                const uint32_t u = philox_word0(xi, step, a.rc.road, kTagSlowdown, a.rc.key0, a.rc.key1);
+                vel -= (vel > 0u && u < thr) ? 1u : 0u;                 // rule 3
+            }
+            uint32_t nx = xi + vel;                                     // rule 4
+            const bool wrap = nx >= L;
+            nx = wrap ? nx - L : nx;
+            x[r] = nx;
+            v[r] = vel;
+            if (kFull || (uint32_t)r < n_own) {
+                tsum += vel;
+                tcross += wrap ? 1u : 0u;
+            }
+        }
+        if (kFull && n_own == 0u) tsum = tcross = 0u;   // halo lanes
+        tsum = __reduce_add_sync(0xFFFFFFFFu, tsum);
+        tcross = __reduce_add_sync(0xFFFFFFFFu, tcross);
+        if (lane == 0 && (tsum | tcross)) {
+            atomicAdd(&s_sum[s], (unsigned long long)tsum);
+            atomicAdd(&s_cross[s], (unsigned long long)tcross);
+        }
+    }
+
+    if (n_own == (uint32_t)R) {
+        store_cars_vec<R>(a.x_out, a.v_out, t0 + e0, x, v);
+    } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            if ((uint32_t)r < n_own) {
+                a.x_out[t0 + e0 + r] = (int32_t)x[r];
+                a.v_out[t0 + e0 + r] = (uint8_t)v[r];
+            }
+        }
+    }
+}
+
+// Occupancy bits of four cells packed in a 32-bit word (bit b = byte b has
+// its sign bit clear, i.e. holds a car).
+__device__ __forceinline__ uint32_t occupancy4(uint32_t w)
+{
+    const uint32_t m = (~w >> 7) & 0x01010101u;
+    return (m * 0x10204080u) >> 28;
+}
+
+__device__ __forceinline__ uint32_t occupancy16(const uint4 q)
+{
+    return occupancy4(q.x) | (occupancy4(q.y) << 4) | (occupancy4(q.z) << 8) | (occupancy4(q.w) << 12);
+}
+
+constexpr uint4 kEmpty4 = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu};
+constexpr int kGridWarps = kGridThreads / 32;
+constexpr uint32_t kRowCells = 1024u;               // one warp's row: 32 lanes x 32 cells
+static_assert(kGridWarps * kRowCells == (uint32_t)kGridSpan, "one row per warp");
+constexpr uint64_t kWaitLimitNs = 1000000000ull;    // bounded wait on an async copy: 1 s
+
+// ---- PTX wrappers: shared-memory mbarriers and 1-D bulk (TMA) copies ----
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+// Orders this thread's generic-proxy shared-memory accesses before later
+// async-proxy (bulk copy) accesses.
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+// Wait for the phase of `bar` with the given parity, for at most 1 s.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    while (!mbar_try_wait(bar, parity))
+        if (global_ns() - t0 > kWaitLimitNs) return false;
+    return true;
+}
+
+// global -> shared, completion counted in bytes on `bar`
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+// shared -> global, tracked by bulk groups
+__device__ __forceinline__ void bulk_store(void *dst, const void *src, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_u32(src)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+struct GridTileGeom {
+    uint32_t halo;      // H, multiple of 16
+    uint32_t tile;      // C = kGridSpan - 2H cells owned per tile
+    uint32_t padded;    // kGridSpan + pad: buffer length (multiple of 16)
+    uint32_t n_tiles;
+    uint32_t nwork;     // rotating output buffers: 2 for k = 1, else 3
+};
+
+// One synchronous step over a staged span: read `cur`, scatter every car
+// into `nxt` (already all -1), and clear `clr` for the step after.  Warp w
+// owns cells [1024w, 1024w + 1024): each lane turns its 32 cells into an
+// occupancy mask, the warp compacts the row's cars into a list of cell
+// indices, and the lanes then take the cars of the list in turn, so that
+// every lane applies rules 1-4 to the same number of cars (a lane's own
+// cells hold 0..32 cars).  A car's gap comes from its owner lane's mask and
+// the next lane's mask (shuffles) by one funnel shift and find-first-set.
+// kWide: vmax > 16, gaps may reach past the two masks.
+template <Draw D, bool kWide>
+__device__ __forceinline__ void grid_step(const RoadConst &rc, const int8_t *__restrict__ cur, int8_t *nxt,
+                                          int8_t *clr, const GridTileGeom &geo, uint32_t own_cells, uint32_t base,
+                                          uint32_t step, uint16_t *list, uint32_t &tsum, uint32_t &tcross)
+{
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    const uint32_t row0 = warp * kRowCells;
+    const uint32_t H = geo.halo;
+    const uint32_t L = rc.L;
+
+    uint4 *clr4 = reinterpret_cast<uint4 *>(clr + row0);
+    clr4[lane] = kEmpty4;
+    clr4[lane + 32] = kEmpty4;
+    if (warp == kGridWarps - 1)
+        for (uint32_t c = lane; c < (geo.padded - (uint32_t)kGridSpan) / 16u; c += 32u)
+            reinterpret_cast<uint4 *>(clr + kGridSpan)[c] = kEmpty4;
+
+    const uint4 *mine = reinterpret_cast<const uint4 *>(cur + row0 + 32u * lane);
+    const uint32_t m = occupancy16(mine[0]) | (occupancy16(mine[1]) << 16);
+    uint32_t m_next = __shfl_down_sync(0xFFFFFFFFu, m, 1);
+    if (lane == 31) m_next = occupancy16(mine[2]);   // first 16 cells of the next row (or the padding)
+    const uint32_t n = __popc(m);
+    uint32_t incl = n;
+#pragma unroll
+    for (uint32_t d = 1; d < 32; d <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+        if (lane >= d) incl += t;
+    }
+    const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+    if (total == 0) return;
+    uint32_t pos = incl - n;
+    for (uint32_t mm = m; mm; mm &= mm - 1u) list[pos++] = (uint16_t)(32u * lane + (uint32_t)(__ffs(mm) - 1));
+    __syncwarp();
+
+    for (uint32_t first = 0; first < total; first += 32u) {
+        const uint32_t i = first + lane;
+        const bool active = i < total;
+        const uint32_t r = active ? (uint32_t)list[i] : 0u;   // cell index within the row
+        const uint32_t src = r >> 5, bit = r & 31u;
+        const uint32_t wm = __shfl_sync(0xFFFFFFFFu, m, src);
+        const uint32_t wn = __shfl_sync(0xFFFFFFFFu, m_next, src);
+        if (!active) continue;
+        // occupancy of the 32 cells after the car
+        const uint32_t after = __funnelshift_rc(wm, wn, bit + 1u);
+        uint32_t gap = after ? (uint32_t)(__ffs(after) - 1) : 32u;
+        const uint32_t idx = row0 + r;
+        if (kWide) {
+            // the masks know 32 cells ahead (16 fewer for the row's last lane);
+            // past them, scan the bytes
+            uint32_t known = src == 31u ? 47u - bit : 32u;
+            if (gap > known) gap = known;
+            while (gap == known && gap < rc.vmax) {
+                if (cur[idx + 1u + gap] >= 0) break;
+                ++gap;
+                ++known;
+            }
+        }
+        uint32_t cell = base + idx;
+        if (cell >= L) cell -= L;
+        uint32_t vel = min(min((uint32_t)(uint8_t)cur[idx] + 1u, rc.vmax), gap);   // rules 1, 2
+        if (D == Draw::kAlways) {
+            vel -= vel > 0u ? 1u : 0u;                                              // rule 3, p = 1
+        } else if (D == Draw::kPhilox) {
+            const uint32_t u = philox_word0(cell, step, rc.road, kTagSlowdown, rc.key0, rc.key1);
+            vel -= (vel > 0u && u < (uint32_t)rc.thr) ? 1u : 0u;                    // rule 3
+        }
+        nxt[idx + vel] = (int8_t)vel;                                               // rule 4
+        if (idx - H < own_cells) {
+            tsum += vel;
+            tcross += (cell + vel >= L) ? 1u : 0u;
+        }
+    }
+    __syncwarp();
+}
+
+// Whole ring in one block, agent form: thread t holds cars [t*R, t*R + R)
+// of the N <= blockDim.x * R cars; the car after thread t's last car is
+// thread t+1's first, or car 0.  Runs ksteps steps; step s's totals go to
+// out_sum[s], out_cross[s] (written by thread 0).  Shared scratch:
+// s_first[2 * blockDim.x], s_psum[2 * 32], s_pcross[2 * 32].
+template <int R>
+__device__ __forceinline__ void agent_ring_steps(const int32_t *__restrict__ x_in, const uint8_t *__restrict__ v_in,
+                                                 int32_t *x_out, uint8_t *v_out, uint32_t N, const RoadConst &rc,
+                                                 uint32_t step0, int ksteps, unsigned long long *out_sum,
+                                                 unsigned long long *out_cross, uint32_t *s_first, uint32_t *s_psum,
+                                                 uint32_t *s_pcross)
+{
+    const uint32_t tid = threadIdx.x;
+    const uint32_t lane = tid & 31u, warp = tid >> 5;
+    const uint32_t nthreads = blockDim.x, nwarps = nthreads >> 5;
+    const uint32_t e0 = tid * R;
+    const int cnt = e0 < N ? (int)min((uint32_t)R, N - e0) : 0;
+    const uint32_t next_owner = (e0 + R < N) ? tid + 1 : 0u;
+
+    uint32_t x[R], v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        x[r] = r < cnt ? (uint32_t)x_in[e0 + r] : 0u;
+        v[r] = r < cnt ? (uint32_t)v_in[e0 + r] : 0u;
+    }
+    for (int s = 0; s < ksteps; ++s) {
+        const uint32_t ph = (uint32_t)s & 1u;
+        const uint32_t step = step0 + (uint32_t)s;
+        if (cnt > 0) s_first[ph * nthreads + tid] = x[0];
+        __syncthreads();
+        if (tid == 0 && s > 0) {
+            unsigned long long sv = 0, cr = 0;
+            for (uint32_t w = 0; w < nwarps; ++w) {
+                sv += s_psum[(ph ^ 1u) * 32u + w];
+                cr += s_pcross[(ph ^ 1u) * 32u + w];
+            }
+            out_sum[s - 1] = sv;
+            out_cross[s - 1] = cr;
+        }
+        const uint32_t lead_last = s_first[ph * nthreads + next_owner];
+        uint32_t tsum = 0, tcross = 0;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            if (r < cnt) {
+                const uint32_t xi = x[r];
+                const uint32_t lead = (r + 1 < cnt) ? x[r + 1] : lead_last;
+                const uint32_t vel = new_velocity(rc, v[r], agent_gap(xi, lead, rc.L), xi, step);
+                uint32_t nx = xi + vel;
+                const bool wrap = nx >= rc.L;
+                if (wrap) nx -= rc.L;
+                x[r] = nx;
+                v[r] = vel;
+                tsum += vel;
+                tcross += wrap ? 1u : 0u;
+            }
+        }
+        tsum = __reduce_add_sync(0xFFFFFFFFu, tsum);
+        tcross = __reduce_add_sync(0xFFFFFFFFu, tcross);
+        if (lane == 0) {
+            s_psum[ph * 32u + warp] = tsum;
+            s_pcross[ph * 32u + warp] = tcross;
+        }
+    }
+    __syncthreads();
+    if (tid == 0 && ksteps > 0) {
+        const uint32_t ph = (uint32_t)(ksteps - 1) & 1u;
+        unsigned long long sv = 0, cr = 0;
+        for (uint32_t w = 0; w < nwarps; ++w) {
+            sv += s_psum[ph * 32u + w];
+            cr += s_pcross[ph * 32u + w];
+        }
+        out_sum[ksteps - 1] = sv;
+        out_cross[ksteps - 1] = cr;
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        if (r < cnt) {
+            x_out[e0 + r] = (int32_t)x[r];
+            v_out[e0 + r] = (uint8_t)v[r];
+        }
+    }
+}
+
+// Whole ring in one block, grid form: the L cells and their successor in
+// shared memory (cur, nxt, each >= L bytes); gaps and moves wrap modulo L.
+// Step s's totals go to out_sum[s], out_cross[s] (thread 0).  Shared
+// scratch: s_psum[32], s_pcross[32].
+__device__ __forceinline__ void grid_ring_steps(const int8_t *__restrict__ c_in, int8_t *c_out, const RoadConst &rc,
+                                                uint32_t step0, int ksteps, int8_t *cur, int8_t *nxt,
+                                                unsigned long long *out_sum, unsigned long long *out_cross,
+                                                uint32_t *s_psum, uint32_t *s_pcross)
+{
+    const uint32_t L = rc.L;
+    const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+    const uint32_t nwarps = blockDim.x >> 5;
+    for (uint32_t i = tid; i < L; i += blockDim.x) cur[i] = c_in[i];
+    for (int s = 0; s < ksteps; ++s) {
+        const uint32_t step = step0 + (uint32_t)s;
+        for (uint32_t i = tid; i < L; i += blockDim.x) nxt[i] = -1;
+        __syncthreads();
+        uint32_t tsum = 0, tcross = 0;
+        for (uint32_t i = tid; i < L; i += blockDim.x) {
+            const int8_t here = cur[i];
+            if (here < 0) continue;
+            const uint32_t limit = min((uint32_t)here + 1u, rc.vmax);
+            uint32_t gap = 0;
+            uint32_t ahead = i + 1u == L ? 0u : i + 1u;
+            while (gap < limit && cur[ahead] < 0) {   // reaches the car itself after L-1 cells
+                ++gap;
+                ahead = ahead + 1u == L ? 0u : ahead + 1u;
+            }
+            const uint32_t vel = new_velocity(rc, (uint32_t)here, gap, i, step);
+            uint32_t dest = i + vel;
+            const bool wrap = dest >= L;
+            if (wrap) dest -= L;
+            nxt[dest] = (int8_t)vel;
+            tsum += vel;
+            tcross += wrap ? 1u : 0u;
+        }
+        tsum = __reduce_add_sync(0xFFFFFFFFu, tsum);
+        tcross = __reduce_add_sync(0xFFFFFFFFu, tcross);
+        if (lane == 0) {
+            s_psum[warp] = tsum;
+            s_pcross[warp] = tcross;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            unsigned long long sv = 0, cr = 0;
+            for (uint32_t w = 0; w < nwarps; ++w) {
+                sv += s_psum[w];
+                cr += s_pcross[w];
+            }
+            out_sum[s] = sv;
+            out_cross[s] = cr;
+        }
+        int8_t *t = cur;
+        cur = nxt;
+        nxt = t;
+        // the next step's clear of nxt (the old cur) must wait for this step's
+        // reads, and thread 0's reads of s_psum for the next step's writes
+        __syncthreads();
+    }
+    for (uint32_t i = tid; i < L; i += blockDim.x) c_out[i] = cur[i];
+}
+
+}  // namespace
+}  // namespace nasch

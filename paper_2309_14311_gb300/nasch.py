@@ -52,6 +52,12 @@ class Info(ctypes.Structure):
                 ("blocks", ctypes.c_int32)]
 
 
+class BatchInfo(ctypes.Structure):
+    _fields_ = [("n_roads", ctypes.c_int64), ("super_steps", ctypes.c_int64), ("items", ctypes.c_int64),
+                ("device_bytes", ctypes.c_int64), ("vehicle_steps", ctypes.c_int64),
+                ("cell_steps", ctypes.c_int64), ("blocks", ctypes.c_int32), ("graphs", ctypes.c_int32)]
+
+
 _lib = None
 _lock = threading.Lock()
 
@@ -98,6 +104,18 @@ def _declare(lib) -> None:
         "nasch_floyd_init": (ctypes.c_int, [i64, i64, u64, u32, P]),
         "nasch_philox_device": (ctypes.c_int, [i64, P, u64, P]),
         "nasch_calibrate_philox": (ctypes.c_int, [i64, P, P]),
+        "nasch_submit": (ctypes.c_int, [P, i64, P, P]),
+        "nasch_batch_wait": (ctypes.c_int, [H, i64]),
+        "nasch_batch_cancel": (ctypes.c_int, [H]),
+        "nasch_batch_read_state": (ctypes.c_int, [H, i64, P, P, i64]),
+        "nasch_batch_read_grid": (ctypes.c_int, [H, i64, P, i64]),
+        "nasch_batch_stats": (ctypes.c_int, [H, i64, u64, i64, P, P]),
+        "nasch_batch_stats_sum": (ctypes.c_int, [H, i64, u64, i64, P, P]),
+        "nasch_batch_get_info": (ctypes.c_int, [H, P]),
+        "nasch_batch_road_layout": (ctypes.c_int, [H, i64, P]),
+        "nasch_batch_destroy": (None, [H]),
+        "nasch_set_tuning": (ctypes.c_int, [dbl, i32, i32]),
+        "nasch_get_tuning": (ctypes.c_int, [P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -223,3 +241,99 @@ def _stream_handle(stream):
     if isinstance(stream, int):
         return stream
     return int(stream.cuda_stream)
+
+
+def set_tuning(rho_star: float, k_agent: int = 0, k_grid: int = 0) -> None:
+    """Density below which AUTO picks the agent layout, and default fusion depths."""
+    _check(load().nasch_set_tuning(float(rho_star), int(k_agent), int(k_grid)))
+
+
+def get_tuning():
+    r, ka, kg = ctypes.c_double(), ctypes.c_int32(), ctypes.c_int32()
+    _check(load().nasch_get_tuning(ctypes.byref(r), ctypes.byref(ka), ctypes.byref(kg)))
+    return r.value, ka.value, kg.value
+
+
+def make_params(L, N, vmax=5, p=0.0, seed=0, road_id=0, layout="auto", k=0, tile=0, stream=None) -> Params:
+    prm = Params()
+    load().nasch_params_init(ctypes.byref(prm))
+    prm.L, prm.N, prm.vmax, prm.p, prm.seed, prm.road_id = int(L), int(N), int(vmax), float(p), int(seed), int(road_id)
+    prm.layout = LAYOUTS[layout] if isinstance(layout, str) else int(layout)
+    prm.k, prm.tile = int(k), int(tile)
+    prm.stream = _stream_handle(stream)
+    return prm
+
+
+class Batch:
+    """Many roads run together (``nasch_submit``).  ``roads`` are dicts with
+    the keys of ``make_params``; ``steps[i]`` steps are run on road i."""
+
+    def __init__(self, roads, steps, stream=None):
+        lib = load()
+        n = len(roads)
+        arr = (Params * n)()
+        for i, r in enumerate(roads):
+            arr[i] = make_params(**r, stream=stream if i == 0 else None)
+        st = np.ascontiguousarray(np.asarray(steps, dtype=np.int64))
+        assert len(st) == n
+        self._stream_ref = stream
+        self._roads = [dict(r) for r in roads]
+        self._steps = st.copy()
+        h = ctypes.c_void_p()
+        _check(lib.nasch_submit(arr, n, _ptr(st), ctypes.byref(h)))
+        self._h = h
+        self.n = n
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            load().nasch_batch_destroy(self._h)
+            self._h = None
+
+    __del__ = close
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def wait(self, timeout_ms: int = -1) -> None:
+        _check(load().nasch_batch_wait(self._h, int(timeout_ms)))
+
+    def cancel(self) -> None:
+        _check(load().nasch_batch_cancel(self._h))
+
+    def info(self) -> BatchInfo:
+        inf = BatchInfo()
+        _check(load().nasch_batch_get_info(self._h, ctypes.byref(inf)))
+        return inf
+
+    def layout(self, i: int) -> int:
+        lay = ctypes.c_int32()
+        _check(load().nasch_batch_road_layout(self._h, i, ctypes.byref(lay)))
+        return lay.value
+
+    def read_state(self, i: int):
+        N = int(self._roads[i]["N"])
+        x = np.empty(max(N, 1), dtype=np.int32)
+        v = np.empty(max(N, 1), dtype=np.uint8)
+        _check(load().nasch_batch_read_state(self._h, i, _ptr(x), _ptr(v), len(x)))
+        return x[:N], v[:N]
+
+    def read_grid(self, i: int) -> np.ndarray:
+        L = int(self._roads[i]["L"])
+        c = np.empty(L, dtype=np.int8)
+        _check(load().nasch_batch_read_grid(self._h, i, _ptr(c), L))
+        return c
+
+    def stats(self, i: int, first: int = 0, count: int | None = None):
+        n = int(self._steps[i]) - first if count is None else count
+        sv = np.zeros(max(n, 1), dtype=np.uint64)
+        cr = np.zeros(max(n, 1), dtype=np.uint64)
+        _check(load().nasch_batch_stats(self._h, i, first, n, _ptr(sv), _ptr(cr)))
+        return sv[:n], cr[:n]
+
+    def stats_sum(self, i: int, first: int, count: int):
+        a, c = ctypes.c_uint64(), ctypes.c_uint64()
+        _check(load().nasch_batch_stats_sum(self._h, i, first, count, ctypes.byref(a), ctypes.byref(c)))
+        return a.value, c.value

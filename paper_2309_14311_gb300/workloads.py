@@ -32,3 +32,66 @@ EXAMPLE_PARAMS = RoadSpec("example-params L=500 N=300 vmax=2 p=0.2 T=500", 500, 
 # Launch configuration the benchmark times on LARGE_ROAD (fusion depth per
 # layout); the full-size parity tests run the same.
 LARGE_ROAD_K = {"agent": 4, "grid": 8}
+
+
+# --------------------------------------------------------------------------- batched workloads
+import csv as _csv  # noqa: E402
+import os as _os  # noqa: E402
+
+_DATA = _os.path.join(_os.path.dirname(_os.path.abspath(__file__)), "data")
+
+FD_DENSITIES = 64            # densities 0.02 .. 0.90, evenly spaced
+FD_PS = (0.0, 0.13, 0.25, 0.5)
+FD_L = 10**6
+FD_T = 12_000
+FD_WARMUP = 2_000
+
+
+def fd_cars(i: int, L: int = FD_L) -> int:
+    """Cars at density index i of the sweep: rho_i = 0.02 + 0.88 i / 63 =
+    (1260 + 880 i) / 63000, rounded half up in exact integers, in [1, L]."""
+    return max(1, min(L, (L * (1260 + 880 * i) + 31500) // 63000))
+
+
+def fundamental_diagram_roads(replicas: int = 128, L: int = FD_L, densities: int = FD_DENSITIES, ps=FD_PS):
+    """The density sweep: densities x ps x replicas roads of L cells, vmax 5.
+    Replica r uses seed r + 1; the road id is the flat index (density-major)."""
+    roads = []
+    for i in range(densities):
+        for j, p in enumerate(ps):
+            for r in range(replicas):
+                roads.append(dict(L=L, N=fd_cars(i, L), vmax=5, p=p, seed=r + 1,
+                                  road_id=(i * len(ps) + j) * replicas + r))
+    return roads
+
+
+def _load_table(name: str):
+    rows = []
+    with open(_os.path.join(_DATA, name)) as f:
+        for rec in _csv.DictReader(f):
+            thr = int(rec["threshold"])
+            row = dict(L=int(rec["L"]), N=int(rec["N"]), vmax=int(rec["vmax"]),
+                       p=thr / 2.0**32,   # exact: ceil(p * 2^32) gives back the threshold
+                       seed=7 if name.startswith("ensemble") else 11, road_id=int(rec["road_id"]),
+                       T=int(rec["T"]))
+            if "arrival_micro" in rec:
+                row["arrival"] = int(rec["arrival_micro"]) * 1e-6
+            rows.append(row)
+    return rows
+
+
+def uneven_ensemble():
+    """4096 roads of the seed-7 table: L log-uniform [1e3, 1e7], density
+    U[0.05, 0.6], vmax in {3, 5, 8}, p U[0, 0.5), T log-uniform [1e3, 1e5]."""
+    return _load_table("ensemble_seed7.csv")
+
+
+def request_stream():
+    """20000 requests of the seed-11 table (same distributions) with unit-rate
+    Poisson arrival times (`arrival`, seconds at rate 1)."""
+    return _load_table("requests_seed11.csv")
+
+
+def road_params(row: dict) -> dict:
+    """The nasch_params keys of a table row (drops T and arrival)."""
+    return {k: row[k] for k in ("L", "N", "vmax", "p", "seed", "road_id")}

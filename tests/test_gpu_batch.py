@@ -1,0 +1,168 @@
+"""GPU parity of batched runs (nasch_submit) against the oracle.
+
+A batch mixes every kind of work item (agent warp-tiles, grid spans,
+whole-ring agent and grid roads), uneven step counts (including 0), p = 0
+and p = 1, wide vmax, a lone car and a full ring.  Every road must equal the
+oracle bit for bit, and equal the same road run alone through the
+single-road API (the draws are keyed by road id, never by slot or order).
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2309_14311_gb300 import nasch as NS
+from paper_2309_14311_gb300 import workloads as WL
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2309_14311_gb300 import build
+    build.build()
+    NS.load()
+
+
+MIXED = [
+    dict(L=200000, N=9000, vmax=5, p=0.13, seed=3, road_id=11, T=57),            # agent tiles
+    dict(L=30000, N=1500, vmax=8, p=0.3, seed=4, road_id=12, T=101),             # agent ring
+    dict(L=50000, N=20000, vmax=5, p=0.25, seed=5, road_id=13, T=73),            # grid tiles
+    dict(L=5000, N=2500, vmax=3, p=0.5, seed=6, road_id=14, T=90),               # grid ring
+    dict(L=40000, N=9000, vmax=20, p=0.1, seed=7, road_id=15, T=33, layout="grid"),   # vmax > 16
+    dict(L=60000, N=7000, vmax=5, p=0.0, seed=8, road_id=16, T=40),              # p = 0
+    dict(L=60000, N=20000, vmax=5, p=1.0, seed=8, road_id=17, T=40),             # p = 1
+    dict(L=1000, N=10, vmax=5, p=0.1, seed=9, road_id=18, T=0),                  # no steps
+    dict(L=1000, N=1, vmax=5, p=0.1, seed=9, road_id=19, T=25),                  # a lone car
+    dict(L=3000, N=3000, vmax=5, p=0.5, seed=9, road_id=20, T=5),                # full ring
+    dict(L=2**31, N=5000, vmax=5, p=0.13, seed=10, road_id=21, T=16),           # wrap at 2^31
+    dict(L=9000, N=2100, vmax=127, p=0.2, seed=2, road_id=22, T=12, layout="agent", k=5),
+    dict(L=8192 * 3 + 5, N=3000, vmax=5, p=0.2, seed=2, road_id=23, T=30, layout="grid", k=3),
+]
+
+
+def _params(r):
+    return {k: r[k] for k in ("L", "N", "vmax", "p", "seed", "road_id", "layout", "k") if k in r}
+
+
+def oracle_road(r):
+    x0 = O.floyd_init(r["L"], r["N"], r["seed"], r["road_id"])
+    return O.agent_run(r["L"], x0, np.zeros(r["N"], np.uint8), r["vmax"], r["p"], r["seed"], r["road_id"], 0,
+                       r["T"], openmp=True)
+
+
+def check_road(b, i, r):
+    ox, ov, osv, ocr = oracle_road(r)
+    sv, cr = b.stats(i)
+    assert np.array_equal(sv, osv) and np.array_equal(cr, ocr), (i, "stats")
+    assert np.array_equal(b.read_grid(i), O.agent_to_grid(r["L"], ox, ov)), (i, "grid")
+    if b.layout(i) == NS.LAYOUT_AGENT:
+        x, v = b.read_state(i)
+        assert np.array_equal(x, ox) and np.array_equal(v, ov), (i, "agent state")
+
+
+def test_mixed_batch_matches_oracle():
+    with NS.Batch([_params(r) for r in MIXED], [r["T"] for r in MIXED]) as b:
+        b.wait()
+        inf = b.info()
+        assert inf.n_roads == len(MIXED) and inf.super_steps >= 1
+        for i, r in enumerate(MIXED):
+            check_road(b, i, r)
+
+
+def test_batch_equals_each_road_alone():
+    with NS.Batch([_params(r) for r in MIXED], [r["T"] for r in MIXED]) as b:
+        b.wait()
+        for i, r in enumerate(MIXED):
+            lay = "agent" if b.layout(i) == NS.LAYOUT_AGENT else "grid"
+            with NS.Road(r["L"], r["N"], r["vmax"], r["p"], r["seed"], r["road_id"], layout=lay) as alone:
+                alone.run(r["T"])
+                sv, cr = alone.stats()
+                assert np.array_equal(alone.read_grid(), b.read_grid(i)), i
+                bsv, bcr = b.stats(i)
+                assert np.array_equal(sv, bsv) and np.array_equal(cr, bcr), i
+
+
+def test_order_and_fusion_depth_do_not_matter():
+    rs = [_params(r) for r in MIXED]
+    steps = [r["T"] for r in MIXED]
+    with NS.Batch(rs, steps) as a:
+        a.wait()
+        want = [a.read_grid(i) for i in range(len(rs))]
+    perm = list(reversed(range(len(rs))))
+    rs2 = [dict(rs[i], k=k) for i, k in zip(perm, [1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13])]
+    with NS.Batch(rs2, [steps[i] for i in perm]) as b:
+        b.wait()
+        for j, i in enumerate(perm):
+            assert np.array_equal(b.read_grid(j), want[i]), i
+
+
+def test_uneven_ensemble_subset():
+    """The 160 smallest-work roads of the seed-7 ensemble, full length, against
+    the oracle, and 8 larger ones checked on light-cone windows of cars."""
+    rows = WL.uneven_ensemble()
+    order = sorted(range(len(rows)), key=lambda i: rows[i]["N"] * rows[i]["T"])
+    small = order[:160]
+    rng = np.random.default_rng(5)
+    mids = [i for i in order[160:] if rows[i]["T"] <= 3000 and rows[i]["N"] > 2048]
+    big = list(rng.choice(mids, 8, replace=False))
+    pick = small + big
+    roads = [WL.road_params(rows[i]) for i in pick]
+    steps = [rows[i]["T"] for i in pick]
+    with NS.Batch(roads, steps) as b:
+        b.wait()
+        for j in range(len(small)):
+            r = dict(roads[j], T=steps[j])
+            check_road(b, j, r)
+        for j in range(len(small), len(pick)):
+            r = dict(roads[j], T=steps[j])
+            x0 = O.floyd_init(r["L"], r["N"], r["seed"], r["road_id"])
+            lay = b.layout(j)
+            if lay == NS.LAYOUT_AGENT:
+                x, v = b.read_state(j)
+            else:
+                cells = b.read_grid(j)
+            for start in rng.integers(0, r["N"], 2):
+                M = r["T"] + 40
+                idx = (int(start) + np.arange(M)) % r["N"]
+                wx, wv = O.agent_segment(r["L"], x0[idx], np.zeros(M, np.uint8), r["vmax"], r["p"], r["seed"],
+                                         r["road_id"], 0, r["T"], openmp=True)
+                if lay == NS.LAYOUT_AGENT:
+                    assert np.array_equal(wx, x[idx[:40]]) and np.array_equal(wv, v[idx[:40]])
+                else:
+                    assert np.array_equal(cells[wx], wv.astype(np.int8))
+
+
+def test_fundamental_diagram_subset_matches_oracle():
+    """One replica per (density, p) of the sweep, on a shorter road and run."""
+    roads = WL.fundamental_diagram_roads(replicas=1, L=20000)
+    T = 60
+    with NS.Batch(roads, [T] * len(roads)) as b:
+        b.wait()
+        for i in range(0, len(roads), 5):
+            check_road(b, i, dict(roads[i], T=T))
+
+
+def test_wait_timeout_and_cancel():
+    roads = [dict(L=2_000_000, N=200_000, vmax=5, p=0.13, seed=1, road_id=i) for i in range(16)]
+    b = NS.Batch(roads, [20000] * len(roads))
+    try:
+        with pytest.raises(NS.NaschError) as e:
+            b.wait(0)
+        assert e.value.status == NS.ETIMEOUT
+        b.cancel()
+        with pytest.raises(NS.NaschError) as e:
+            b.wait(120000)
+        assert e.value.status == NS.ECANCELED
+    finally:
+        b.close()
+
+
+def test_submit_rejects_bad_roads():
+    with pytest.raises(NS.NaschError) as e:
+        NS.Batch([dict(L=100, N=200)], [10])
+    assert e.value.status == NS.EINVAL
+    with pytest.raises(NS.NaschError):
+        NS.Batch([dict(L=100, N=20)], [-1])
