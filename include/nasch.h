@@ -223,6 +223,27 @@ void nasch_batch_destroy(nasch_batch b);
 int nasch_set_tuning(double rho_star, int32_t k_agent, int32_t k_grid);
 int nasch_get_tuning(double *rho_star, int32_t *k_agent, int32_t *k_grid);
 
+/* Start positions of one road, computed on the GPU without allocating any
+ * device memory.  The paper has no counterpart: this entry point exists for
+ * callers that cannot allocate device memory - a process whose device memory
+ * is all owned by another allocator (a framework's caching pool, an arena set
+ * up at start), or one that forbids allocation after start-up.
+ * Writes the N sorted Floyd positions of (seed, road_id), the same as
+ * nasch_floyd_init, into the caller's device buffer x_dev[0..N-1],
+ * asynchronously on `stream` (a cudaStream_t, NULL for the default stream);
+ * the caller synchronises before reading x_dev.  It calls no allocating
+ * routine: its scratch bit map is a fixed 2 MiB array in the library's device
+ * memory, held by every GPU that loads the library until the process exits,
+ * so L is limited to 2^24 cells (a longer road is NASCH_EINVAL).  The first
+ * call on a device looks up that array's device address with the device
+ * current; make that first call before any stream capture.  All calls share
+ * the array and the bits of the previous call stay in it (each call clears
+ * the part it uses first), so calls whose work overlaps on the GPU race and
+ * give wrong positions: issue them on one stream, or synchronise between
+ * them. */
+int nasch_floyd_init_device_noalloc(int64_t L, int64_t N, uint64_t seed, uint32_t road_id, int32_t *x_dev,
+                                    void *stream);
+
 /* Calibration: the rate (draws per second) at which the GPU evaluates the
  * rule-3 draw, word 0 of Philox4x32-10, with nothing else to do - the
  * integer-pipe ceiling of the step, one draw per car-step.  Runs one

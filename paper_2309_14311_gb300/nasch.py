@@ -115,6 +115,7 @@ def _declare(lib) -> None:
         "nasch_batch_road_layout": (ctypes.c_int, [H, i64, P]),
         "nasch_batch_destroy": (None, [H]),
         "nasch_set_tuning": (ctypes.c_int, [dbl, i32, i32]),
+        "nasch_floyd_init_device_noalloc": (ctypes.c_int, [i64, i64, u64, u32, P, P]),
         "nasch_get_tuning": (ctypes.c_int, [P, P, P]),
     }
     for name, (res, args) in sig.items():
@@ -148,6 +149,14 @@ def philox_device(ctr: np.ndarray, seed: int) -> np.ndarray:
     out = np.zeros_like(c)
     _check(load().nasch_philox_device(len(c), _ptr(c), seed, _ptr(out)))
     return out
+
+
+def floyd_init_device_noalloc(L: int, N: int, seed: int, road: int, x_dev_ptr: int, stream=None) -> None:
+    """Floyd start positions written to a caller-owned device buffer (int32,
+    N entries) without any device allocation by the library; asynchronous on
+    `stream`.  Roads of at most 2^24 cells."""
+    _check(load().nasch_floyd_init_device_noalloc(int(L), int(N), int(seed), int(road), ctypes.c_void_p(x_dev_ptr),
+                                                  _stream_handle(stream)))
 
 
 def calibrate_philox(draws_per_thread: int = 1 << 14) -> float:
