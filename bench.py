@@ -221,6 +221,27 @@ def run_reference(args):
 
 
 # --------------------------------------------------------------------------- GPU arm
+# Algorithmic integer operations of one car-step on this instruction set:
+# Philox4x32-10 word 0 = 10 rounds of two 32x32->64 products and two 3-input
+# xors, less the first round's product of the per-launch constant counter
+# word and the last round's three unused outputs (37); rules 1-4 with the
+# per-step statistics: accelerate 1, gap 2, brake 1, slowdown 2, move 2,
+# statistics 2 (10).  Total 47.
+ALU_OPS_PER_CAR_STEP = 47
+
+
+def issue_peak_ops(props) -> tuple[float, str]:
+    """Integer issue ceiling: SMs x 4 schedulers x 32 lanes x max SM clock
+    (one instruction per lane per clock)."""
+    mhz = 2070.0
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            mhz = float(json.load(f).get("sm_max_mhz", mhz))
+    except Exception:
+        pass
+    return props.multi_processor_count * 128 * mhz * 1e6, f"{props.multi_processor_count} SMs x 128 lanes x {mhz:.0f} MHz"
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -235,6 +256,7 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group(backend="nccl")
     NS.load(build_if_missing=True)
+    props = torch.cuda.get_device_properties(local)
 
     spec = WL.LARGE_ROAD
     road_id = replica_road_ids(world)[rank]
@@ -269,7 +291,6 @@ def run_ours(args):
         barrier()
         return start.elapsed_time(end) / 1000.0
 
-    result = {}
     # ---------------------------------------------------------------- main (device-resident) measurement
     road = NS.Road(spec.L, spec.N, spec.vmax, spec.p, spec.seed, road_id, layout=layout, k=k, stream=stream)
     info = road.info()
@@ -285,43 +306,49 @@ def run_ours(args):
     value = total_units / t_max
     launches_per_run = -(-chunk // info.k) if not info.ring_kernel else 1
     gpu_launches = launches_per_run * args.steps
-    launch_s = secs / gpu_launches
-    if layout == "agent":
-        alg_bytes = AGENT_BYTES_PER_CAR * spec.N
-    else:
-        alg_bytes = GRID_BYTES_PER_CELL * spec.L
-    peak, peak_kind = measured_peaks()
-    achieved = alg_bytes / launch_s / 1e9
+    launch_s = secs / gpu_launches          # includes the two statistics memsets per run() call
+    hbm_peak, hbm_kind = measured_peaks()
     kernel_name = f"{layout}_tiled_k{info.k}"
+    car_steps_per_launch = spec.N * info.k
+    if layout == "agent":
+        ops_peak, ops_how = issue_peak_ops(props)
+        achieved_ops = ALU_OPS_PER_CAR_STEP * car_steps_per_launch / launch_s
+        roofline = {"bound": "alu", "achieved": achieved_ops / 1e12, "peak": ops_peak / 1e12, "unit": "Tops/s",
+                    "frac": achieved_ops / ops_peak, "traffic": traffic_for(kernel_name), "kernel": kernel_name,
+                    "peak_source": f"derived: {ops_how}, one integer instruction per lane per clock",
+                    "algorithmic_ops_per_car_step": ALU_OPS_PER_CAR_STEP,
+                    "algorithmic_bytes_per_launch": AGENT_BYTES_PER_CAR * spec.N,
+                    "hbm_gbs": AGENT_BYTES_PER_CAR * spec.N / launch_s / 1e9, "launch_ms": launch_s * 1e3}
+    else:
+        alg = GRID_BYTES_PER_CELL * spec.L
+        roofline = {"bound": "hbm", "achieved": alg / launch_s / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": alg / launch_s / 1e9 / hbm_peak, "traffic": traffic_for(kernel_name),
+                    "kernel": kernel_name, "peak_source": f"{hbm_kind} hbm_gbs",
+                    "algorithmic_bytes_per_launch": alg, "launch_ms": launch_s * 1e3}
+    philox_rate = NS.calibrate_philox(1 << 14)
 
-    # ---------------------------------------------------------------- other layout, same road (context)
-    other = "grid" if layout == "agent" else "agent"
-    other_k = WL.LARGE_ROAD_K[other]
-    other_road = NS.Road(spec.L, spec.N, spec.vmax, spec.p, spec.seed, road_id, layout=other, k=other_k,
-                         stream=stream)
-    other_steps = max(other_k, (args.other_steps // other_k) * other_k)
-    other_road.run(other_steps)
-    other_road.synchronize()
-    o_secs = timed_device_run(other_road, other_steps, 1)
-    o_launch_s = o_secs / (-(-other_steps // other_k))
-    o_bytes = AGENT_BYTES_PER_CAR * spec.N if other == "agent" else GRID_BYTES_PER_CELL * spec.L
-    other_res = {"layout": other, "k": other_k, "vehicle_updates_per_s": spec.N * other_steps / o_secs,
-                 "cell_updates_per_s": spec.L * other_steps / o_secs,
-                 "hbm_gbs": o_bytes / o_launch_s / 1e9, "hbm_frac": o_bytes / o_launch_s / 1e9 / peak,
-                 "steps_timed": other_steps}
-    other_road.close()
-
-    # k = 1 form of each layout: the HBM-bound configuration of the step
-    k1 = {}
-    for lay in ("agent", "grid"):
-        r1 = NS.Road(spec.L, spec.N, spec.vmax, spec.p, spec.seed, road_id, layout=lay, k=1, stream=stream)
-        r1.run(5)
-        r1.synchronize()
-        s1 = timed_device_run(r1, 1, args.k1_steps)
-        b1 = AGENT_BYTES_PER_CAR * spec.N if lay == "agent" else GRID_BYTES_PER_CELL * spec.L
-        k1[lay] = {"k": 1, "vehicle_updates_per_s": spec.N * args.k1_steps / s1,
-                   "hbm_gbs": b1 * args.k1_steps / s1 / 1e9, "hbm_frac": b1 * args.k1_steps / s1 / 1e9 / peak}
-        r1.close()
+    # ---------------------------------------------------------------- the HBM-bound form: grid at k = 1
+    g1 = NS.Road(spec.L, spec.N, spec.vmax, spec.p, spec.seed, road_id, layout="grid", k=1, stream=stream)
+    g1.run(5)
+    g1.synchronize()
+    s1 = timed_device_run(g1, 1, args.k1_steps)
+    b1 = GRID_BYTES_PER_CELL * spec.L
+    roofline_hbm = {"bound": "hbm", "kernel": "grid_tiled_k1", "achieved": b1 * args.k1_steps / s1 / 1e9,
+                    "peak": hbm_peak, "unit": "GB/s", "frac": b1 * args.k1_steps / s1 / 1e9 / hbm_peak,
+                    "traffic": traffic_for("grid_tiled_k1"), "peak_source": f"{hbm_kind} hbm_gbs",
+                    "algorithmic_bytes_per_launch": b1, "launch_ms": s1 / args.k1_steps * 1e3,
+                    "vehicle_updates_per_s": spec.N * args.k1_steps / s1,
+                    "cell_updates_per_s": spec.L * args.k1_steps / s1}
+    gk = WL.LARGE_ROAD_K["grid"]
+    g1.close()
+    gr = NS.Road(spec.L, spec.N, spec.vmax, spec.p, spec.seed, road_id, layout="grid", k=gk, stream=stream)
+    gr.run(gk)
+    gr.synchronize()
+    gsteps = max(gk, (args.other_steps // gk) * gk)
+    sg = timed_device_run(gr, gsteps, 1)
+    grid_res = {"layout": "grid", "k": gk, "vehicle_updates_per_s": spec.N * gsteps / sg,
+                "cell_updates_per_s": spec.L * gsteps / sg, "steps_timed": gsteps}
+    gr.close()
 
     # ---------------------------------------------------------------- end to end through the C ABI, host buffers
     x_host = torch.empty(spec.N, dtype=torch.int32, pin_memory=True).numpy()
@@ -331,18 +358,22 @@ def run_ours(args):
     road.read_state(x_host, v_host)
     step0 = road.step
     e2e_iters = max(1, args.e2e_steps)
+    lib = NS.load()
     barrier()
     t0 = time.perf_counter()
     for i in range(e2e_iters):
         road.set_state(x_host, v_host, step0 + i * chunk)        # host -> device
         road.run(chunk)
         road.read_state(x_host, v_host)                          # device -> host
-        lib = NS.load()
         NS._check(lib.nasch_stats(road.handle, step0 + i * chunk, chunk, NS._ptr(sv_host), NS._ptr(cr_host)))
     e2e_secs = max_over_ranks(time.perf_counter() - t0)
     barrier()
     e2e_units = sum_over_ranks(spec.N * chunk * e2e_iters)
     road.close()
+
+    # ---------------------------------------------------------------- batched vs plain, and served
+    batch_res = run_batch_vs_plain(args, NS, stream, torch) if not args.no_batch else None
+    serve_res = run_served(args, NS, batch_res) if (not args.no_serve and batch_res) else None
 
     # ---------------------------------------------------------------- oracle on the host cores (rank 0, N = 1)
     cpu = None
@@ -371,16 +402,16 @@ def run_ours(args):
                        "steps_per_bench_step": chunk, "nasch_steps_timed": chunk * args.steps,
                        "parallelism": f"replicas{world}",
                        "l2_flush": "not needed: state 640 MiB (agent) / 4 GiB (grid) > 129 MB L2"},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": traffic_for(kernel_name),
-                         "kernel": kernel_name, "peak_source": f"{peak_kind} hbm_gbs",
-                         "algorithmic_bytes_per_launch": alg_bytes,
-                         "launch_ms": launch_s * 1e3},
+            "roofline": roofline,
+            "roofline_hbm": roofline_hbm,
+            "philox_ceiling": {"draws_per_s": philox_rate, "frac": value / world / philox_rate,
+                               "note": "bare rule-3 draws per second (nasch_calibrate_philox); one per car-step"},
             "cell_updates_per_s": value * spec.L / spec.N,
-            "other_layout": other_res,
-            "k1": k1,
+            "grid_layout": grid_res,
             "e2e": {"value": e2e_units / e2e_secs, "unit": "vehicle-updates/s",
                     "h2d_bytes_per_step": spec.N * 5, "d2h_bytes_per_step": spec.N * 5 + chunk * 16},
+            "batched_vs_plain": batch_res,
+            "served": serve_res,
             "gpu_launches": gpu_launches,
             "clocks": clocks,
             "cpu_baseline": cpu,
@@ -391,12 +422,163 @@ def run_ours(args):
     return 0
 
 
+def run_batch_vs_plain(args, NS, stream, torch):
+    """A seeded sample of the uneven ensemble (L log-uniform 1e3..1e7, T
+    log-uniform 1e3..1e5): all roads in one batched job vs the same roads one
+    after another through the single-road API (plain per-road launches).
+    GPU time only (start states excluded on both sides)."""
+    import numpy as np
+    rows = WL.uneven_ensemble()
+    rng = np.random.default_rng(2309)
+    idx = sorted(rng.choice(len(rows), args.batch_roads, replace=False).tolist())
+    roads = [WL.road_params(rows[i]) for i in idx]
+    steps = [rows[i]["T"] for i in idx]
+    work = sum(r["N"] * t for r, t in zip(roads, steps))
+    with NS.Batch(roads, steps, stream=stream) as b:
+        b.wait()
+        inf = b.info()
+        batched_s = inf.run_seconds
+    plain_s = 0.0
+    launches = 0
+    for r, t in zip(roads, steps):
+        with NS.Road(r["L"], r["N"], r["vmax"], r["p"], r["seed"], r["road_id"], stream=stream) as road:
+            ri = road.info()
+            road.synchronize()
+            a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            road.run(t)
+            e.record(stream)
+            e.synchronize()
+            plain_s += a.elapsed_time(e) / 1e3
+            launches += 1 if ri.ring_kernel else -(-t // ri.k)
+    return {"roads": len(roads), "sample": f"{len(roads)} roads drawn (seed 2309) from the seed-7 ensemble table",
+            "vehicle_updates": work, "batched_vehicle_updates_per_s": work / batched_s,
+            "plain_vehicle_updates_per_s": work / plain_s, "speedup": plain_s / batched_s,
+            "batched_launches": int(inf.super_steps), "plain_launches": launches,
+            "batched_seconds": batched_s, "plain_seconds": plain_s}
+
+
+def run_served(args, NS, batch_res):
+    """The first requests of the seed-11 stream served by the continuous-batching
+    loop at an offered load of `serve_load` x the batched capacity."""
+    from paper_2309_14311_gb300 import serve as SV
+    rows = WL.request_stream()[: args.serve_requests]
+    mean_work = sum(r["N"] * r["T"] for r in rows) / len(rows)
+    capacity = batch_res["batched_vehicle_updates_per_s"] / mean_work     # requests per second
+    rate = args.serve_load * capacity
+    out = SV.run_poisson(rows, rate=rate, memory_budget=args.serve_budget_gb << 30, steps_per_tick=8,
+                         time_limit_s=args.serve_time_limit)
+    out["offered_load"] = args.serve_load
+    out["budget_bytes"] = args.serve_budget_gb << 30
+    return out
+
+
 class _Null:
     def __enter__(self):
         return self
 
     def __exit__(self, *exc):
         return False
+
+
+# --------------------------------------------------------------------------- other workloads (one JSON line each)
+def run_workload(args):
+    """The batched and served configurations, measured on their own:
+
+    ensemble             the seed-7 uneven ensemble (4096 roads, or the first
+                         --roads of a seeded sample), batched in one job vs
+                         plain per-road launches (--plain-roads of them);
+    fundamental-diagram  the density sweep: 64 densities x p in {0, 0.13, 0.25,
+                         0.5} x --replicas replicas, L = --fd-L, T = 12000 with
+                         the first 2000 steps discarded; time-averaged flux and
+                         velocity per (density, p), and for p = 0 the
+                         deterministic steady state min(vmax rho, 1 - rho);
+    serve                the seed-11 request stream (first --serve-requests),
+                         Poisson arrivals at --serve-load x capacity, 40 GB
+                         budget; p50/p99 latency and aggregate rate."""
+    import numpy as np
+    import torch
+
+    from paper_2309_14311_gb300 import nasch as NS
+    torch.cuda.set_device(0)
+    NS.load(build_if_missing=True)
+    stream = torch.cuda.Stream()
+    out = {"workload": args.workload}
+    if args.workload == "ensemble":
+        rows = WL.uneven_ensemble()
+        if args.roads < len(rows):
+            rng = np.random.default_rng(2309)
+            rows = [rows[i] for i in sorted(rng.choice(len(rows), args.roads, replace=False).tolist())]
+        roads = [WL.road_params(r) for r in rows]
+        steps = [r["T"] for r in rows]
+        work = sum(r["N"] * r["T"] for r in rows)
+        t0 = time.perf_counter()
+        with NS.Batch(roads, steps, stream=stream) as b:
+            b.wait()
+            inf = b.info()
+        wall = time.perf_counter() - t0
+        out.update(roads=len(rows), vehicle_updates=work, batched_gpu_seconds=inf.run_seconds,
+                   batched_wall_seconds=wall, batched_vehicle_updates_per_s=work / inf.run_seconds,
+                   super_steps=int(inf.super_steps), graphs=int(inf.graphs), device_bytes=int(inf.device_bytes))
+        # plain: the same roads one after another (a seeded subset if --plain-roads is smaller)
+        sub = list(range(len(rows)))
+        if args.plain_roads < len(rows):
+            rng = np.random.default_rng(7)
+            sub = sorted(rng.choice(len(rows), args.plain_roads, replace=False).tolist())
+        pwork = sum(rows[i]["N"] * rows[i]["T"] for i in sub)
+        plain = 0.0
+        for i in sub:
+            r = rows[i]
+            with NS.Road(r["L"], r["N"], r["vmax"], r["p"], r["seed"], r["road_id"], stream=stream) as road:
+                road.synchronize()
+                a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                road.run(r["T"])
+                e.record(stream)
+                e.synchronize()
+                plain += a.elapsed_time(e) / 1e3
+        out.update(plain_roads=len(sub), plain_vehicle_updates=pwork, plain_gpu_seconds=plain,
+                   plain_vehicle_updates_per_s=pwork / plain,
+                   speedup=(work / inf.run_seconds) / (pwork / plain))
+    elif args.workload == "fundamental-diagram":
+        roads = WL.fundamental_diagram_roads(replicas=args.replicas, L=args.fd_L)
+        T = WL.FD_T
+        t0 = time.perf_counter()
+        with NS.Batch(roads, [T] * len(roads), stream=stream) as b:
+            b.wait()
+            inf = b.info()
+            table = {}
+            for i, r in enumerate(roads):
+                sv, _ = b.stats_sum(i, WL.FD_WARMUP, T - WL.FD_WARMUP)
+                key = (r["N"], r["p"])
+                table.setdefault(key, []).append(sv)
+        wall = time.perf_counter() - t0
+        rows = []
+        L = args.fd_L
+        for (N, p), sums in sorted(table.items()):
+            steps = T - WL.FD_WARMUP
+            J = [s / (L * steps) for s in sums]            # time-averaged flux per replica
+            v = [s / (N * steps) for s in sums]            # time-averaged mean velocity
+            row = {"rho": N / L, "p": p, "J": float(np.mean(J)), "J_sd": float(np.std(J)),
+                   "v": float(np.mean(v)), "replicas": len(J)}
+            if p == 0.0:
+                row["J_p0_theory"] = min(5 * N / L, 1 - N / L)
+            rows.append(row)
+        work = sum(r["N"] for r in roads) * T
+        out.update(roads=len(roads), L=L, T=T, warmup=WL.FD_WARMUP, vehicle_updates=work,
+                   batched_gpu_seconds=inf.run_seconds, wall_seconds=wall,
+                   vehicle_updates_per_s=work / inf.run_seconds, table=rows)
+    elif args.workload == "serve":
+        from paper_2309_14311_gb300 import serve as SV
+        rows = WL.request_stream()[: args.serve_requests]
+        mean_work = sum(r["N"] * r["T"] for r in rows) / len(rows)
+        cap = args.serve_capacity or 3.5e11
+        rate = args.serve_load * cap / mean_work
+        res = SV.run_poisson(rows, rate=rate, memory_budget=args.serve_budget_gb << 30, steps_per_tick=8,
+                             time_limit_s=args.serve_time_limit)
+        out.update(res, assumed_capacity_vehicle_updates_per_s=cap, offered_load=args.serve_load)
+    print(json.dumps(out), flush=True)
+    return 0
 
 
 def run_profile_case(args):
@@ -433,16 +615,33 @@ def main(argv=None):
     ap.add_argument("--chunk", type=int, default=STEPS_PER_BENCH_STEP, help="NaSch steps per benchmark step")
     ap.add_argument("--other-steps", type=int, default=400)
     ap.add_argument("--k1-steps", type=int, default=100)
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--batch-roads", type=int, default=64)
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=300)
+    ap.add_argument("--serve-load", type=float, default=0.7)
+    ap.add_argument("--serve-budget-gb", type=int, default=40)
+    ap.add_argument("--serve-time-limit", type=float, default=120.0)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-steps", type=int, default=10)
     ap.add_argument("--ref-steps-per-step", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=["large-road", "ensemble", "fundamental-diagram", "serve"],
+                    default="large-road", help="large-road is the benchmark line; the others print their own line")
+    ap.add_argument("--roads", type=int, default=4096)
+    ap.add_argument("--plain-roads", type=int, default=256)
+    ap.add_argument("--replicas", type=int, default=128)
+    ap.add_argument("--fd-L", type=int, default=10**6)
+    ap.add_argument("--serve-capacity", type=float, default=0.0,
+                    help="vehicle-updates/s the offered load is scaled to (0: 3.5e11)")
     ap.add_argument("--profile", choices=["agent", "grid"], default=None,
                     help="run the small ncu profiling case of one layout and exit")
     ap.add_argument("--profile-launches", type=int, default=3)
     args = ap.parse_args(argv)
     if args.profile:
         return run_profile_case(args)
+    if args.workload != "large-road":
+        return run_workload(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -186,6 +186,8 @@ typedef struct nasch_batch_info {
     int64_t cell_steps;     /* sum over roads of L * steps */
     int32_t blocks;         /* persistent thread blocks per launch */
     int32_t graphs;         /* CUDA graphs the launches were captured in */
+    double run_seconds;     /* GPU time from the first launch to the last (after the start state is
+                               built); 0 until the batch has finished */
 } nasch_batch_info;
 
 int nasch_submit(const nasch_params *roads, int64_t n_roads, const int64_t *steps, nasch_batch *out);
@@ -223,6 +225,73 @@ void nasch_batch_destroy(nasch_batch b);
 int nasch_set_tuning(double rho_star, int32_t k_agent, int32_t k_grid);
 int nasch_get_tuning(double *rho_star, int32_t *k_agent, int32_t *k_grid);
 
+/* ------------------------------------------------------------------------
+ * Serving: a request loop with continuous batching.  Requests (one road
+ * each, the paper's parameter set plus a step count) queue in arrival order;
+ * each scheduling round admits queued requests, oldest first, while their
+ * state and statistics fit the device-memory budget, and enqueues one tick
+ * of launches over every resident road, each continuing from its own step -
+ * requests admitted later run in the same launches as earlier ones.
+ * Finished requests return their per-step statistics (and, with keep_state,
+ * their final state) to the host and their memory to the budget.  A
+ * request's result equals the same road run alone.
+ * ------------------------------------------------------------------------ */
+typedef struct nasch_server_s *nasch_server;
+
+typedef struct nasch_server_config {
+    int64_t memory_budget;   /* device bytes for resident roads (one slab, allocated at create) */
+    int32_t steps_per_tick;  /* super-step launches per scheduling round (default 8) */
+    int32_t max_resident;    /* most roads resident at once (default 4096) */
+    int32_t keep_state;      /* nonzero: also copy each request's final state back */
+    void *stream;            /* cudaStream_t; NULL = one owned by the server */
+} nasch_server_config;
+
+typedef struct nasch_request_result {
+    uint64_t request_id;
+    int32_t status;          /* NASCH_OK or NASCH_ECANCELED */
+    int32_t layout;
+    int64_t steps;
+    int64_t vehicles;
+    double submit_time;      /* seconds since the server was created (host clock) */
+    double admit_time;
+    double done_time;        /* when the host saw the last launch finish */
+} nasch_request_result;
+
+typedef struct nasch_server_info {
+    int64_t queued, resident, completed;
+    int64_t bytes_in_use;
+    int64_t ticks;
+    int64_t vehicle_steps_done;
+    int32_t blocks;
+    double now;              /* seconds since the server was created (host clock) */
+} nasch_server_info;
+
+/* Defaults: 40 GiB budget, 8 launches per tick, 4096 resident roads. */
+void nasch_server_config_init(nasch_server_config *cfg);
+int nasch_server_create(const nasch_server_config *cfg, nasch_server *out);
+/* Queue one request (thread-safe).  NASCH_ENOMEM if it could never fit the budget. */
+int nasch_server_submit(nasch_server s, const nasch_params *road, int64_t steps, uint64_t request_id);
+/* One scheduling round: retire finished requests, admit queued ones, enqueue
+ * a tick (blocks only while two ticks are already in flight).  *pending
+ * (may be NULL) receives the queued plus resident requests. */
+int nasch_server_step(nasch_server s, int64_t *pending);
+/* Rounds until every submitted request has finished (timeout_ms < 0: no limit). */
+int nasch_server_drain(nasch_server s, int64_t timeout_ms);
+/* Take up to cap finished requests' results (each is returned once). */
+int nasch_server_poll(nasch_server s, nasch_request_result *out, int64_t cap, int64_t *n_out);
+/* Copy a finished request's per-step statistics (cap_steps >= its steps) and,
+ * with keep_state, its final state in cell order (cap_cars >= N); any output
+ * may be NULL. */
+int nasch_server_result(nasch_server s, uint64_t request_id, uint64_t *sum_v_host, uint64_t *crossings_host,
+                        int64_t cap_steps, int32_t *x_host, uint8_t *v_host, int64_t cap_cars);
+/* Forget a finished, polled request (frees its host copies). */
+int nasch_server_release(nasch_server s, uint64_t request_id);
+/* Cancel a queued or running request; it finishes with NASCH_ECANCELED. */
+int nasch_server_cancel(nasch_server s, uint64_t request_id);
+int nasch_server_get_info(nasch_server s, nasch_server_info *info);
+/* Wait for all work, then free the server.  NULL is a no-op. */
+void nasch_server_destroy(nasch_server s);
+
 /* Start positions of one road, computed on the GPU without allocating any
  * device memory.  The paper has no counterpart: this entry point exists for
  * callers that cannot allocate device memory - a process whose device memory
@@ -250,6 +319,15 @@ int nasch_floyd_init_device_noalloc(int64_t L, int64_t N, uint64_t seed, uint32_
  * kernel of draws_per_thread draws per thread on a full grid and
  * synchronises; seconds (may be NULL) receives the kernel's duration. */
 int nasch_calibrate_philox(int64_t draws_per_thread, double *draws_per_second, double *seconds);
+
+/* Self-test of failure detection without a GPU fault: runs a kernel whose
+ * bounded wait (on an mbarrier that nothing completes) gives up after
+ * limit_ms (1..5000).  The kernel records the timeout in a status word and
+ * returns, leaving the context usable; the call returns NASCH_ETIMEOUT with
+ * that word in *status_out (may be NULL).  The same bounded waits guard the
+ * asynchronous copies of the tiled grid kernel, whose timeouts surface as
+ * NASCH_ETIMEOUT from the next call that synchronises the road. */
+int nasch_selftest_bounded_wait(int64_t limit_ms, uint32_t *status_out);
 
 #ifdef __cplusplus
 }

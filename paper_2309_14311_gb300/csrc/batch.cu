@@ -39,10 +39,65 @@ uint32_t round_up(uint32_t a, uint32_t m) { return (a + m - 1u) / m * m; }
 
 }  // namespace
 
-double tuning_rho_star()
+void get_tuning_values(double *rho_star, int *k_agent, int *k_grid)
 {
     std::lock_guard<std::mutex> g(g_tuning_mu);
-    return g_rho_star;
+    *rho_star = g_rho_star;
+    *k_agent = g_k_agent;
+    *k_grid = g_k_grid;
+}
+
+void plan_road(const nasch_params &p, int64_t T, double rho_star, int k_agent, int k_grid, BatchRoadDev *out,
+               int *layout_out, int64_t *n_items, int64_t *super)
+{
+    BatchRoadDev &rd = *out;
+    std::memset(&rd, 0, sizeof(rd));
+    int layout = p.layout;
+    if (layout == NASCH_LAYOUT_AUTO) layout = (double)p.N < rho_star * (double)p.L ? NASCH_LAYOUT_AGENT : NASCH_LAYOUT_GRID;
+    *layout_out = layout;
+    rd.L = (uint32_t)p.L;
+    rd.N = (uint32_t)p.N;
+    rd.vmax = (uint32_t)p.vmax;
+    rd.thr = slow_threshold(p.p);
+    rd.key0 = (uint32_t)p.seed;
+    rd.key1 = (uint32_t)(p.seed >> 32);
+    rd.road_id = p.road_id;
+    rd.T = (uint32_t)T;
+    int k;
+    if (layout == NASCH_LAYOUT_AGENT) {
+        if (p.N <= (int64_t)kBatchRingCars) {
+            rd.type = kBatchAgentRing;
+            k = p.k ? p.k : kRingK;
+            *n_items = 1;
+        } else {
+            rd.type = kBatchAgentTile;
+            k = p.k ? p.k : k_agent;
+            rd.halo = round_up((uint32_t)k, (uint32_t)kBatchAgentR);
+            rd.tile = kBatchAgentSpan - rd.halo;
+            const int64_t per_item = (int64_t)rd.tile * (kBatchThreads / 32);
+            *n_items = (p.N + per_item - 1) / per_item;
+        }
+    } else {
+        if (p.L <= (int64_t)kBatchRingCells) {
+            rd.type = kBatchGridRing;
+            k = p.k ? p.k : kRingK;
+            *n_items = 1;
+        } else {
+            rd.type = kBatchGridTile;
+            k = p.k ? p.k : k_grid;
+            const int kfit = p.vmax > 0 ? std::max(1, (kGridSpan / 2 - 16) / p.vmax) : kMaxFusedSteps;
+            k = std::min(k, kfit);
+            rd.halo = grid_halo(k, (uint32_t)p.vmax);
+            rd.tile = (uint32_t)kGridSpan - 2u * rd.halo;
+            *n_items = (p.L + rd.tile - 1) / rd.tile;
+        }
+    }
+    rd.k = (uint32_t)k;
+    *super = rd.T == 0 ? 0 : (rd.T + rd.k - 1) / rd.k;
+    if (rd.N == 0) {
+        *super = 0;
+        *n_items = 0;
+    }
 }
 
 }  // namespace nasch
@@ -70,6 +125,7 @@ struct nasch_batch_s {
     std::vector<cudaGraphExec_t> execs;
     std::vector<cudaGraph_t> graphs;
     cudaEvent_t done = nullptr;
+    cudaEvent_t started = nullptr;     // recorded after initialisation, before the first launch
     bool canceled = false;
     bool finished = false;
 };
@@ -83,6 +139,7 @@ void free_batch(nasch_batch b)
     for (auto e : b->execs) cudaGraphExecDestroy(e);
     for (auto g : b->graphs) cudaGraphDestroy(g);
     if (b->done) cudaEventDestroy(b->done);
+    if (b->started) cudaEventDestroy(b->started);
     cudaFree(b->pool);
     cudaFree(b->d_roads);
     cudaFree(b->d_items);
@@ -150,6 +207,7 @@ int nasch_get_tuning(double *rho_star, int32_t *k_agent, int32_t *k_grid)
 int nasch_submit(const nasch_params *roads, int64_t n_roads, const int64_t *steps, nasch_batch *out)
 {
     clear_error();
+    TraceRange trace("nasch_submit");
     if (!out) return fail(NASCH_EINVAL, "out is NULL");
     *out = nullptr;
     if (n_roads <= 0 || !roads || !steps) return fail(NASCH_EINVAL, "no roads");
@@ -195,57 +253,13 @@ int nasch_submit(const nasch_params *roads, int64_t n_roads, const int64_t *step
     std::vector<int64_t> n_items((size_t)n_roads);
     uint32_t max_vmax_grid = 0;
     for (int64_t i = 0; i < n_roads; ++i) {
-        const nasch_params &p = roads[i];
-        BatchRoadDev &rd = b->roads[(size_t)i];
-        std::memset(&rd, 0, sizeof(rd));
-        int layout = p.layout;
-        if (layout == NASCH_LAYOUT_AUTO)
-            layout = (double)p.N < rho_star * (double)p.L ? NASCH_LAYOUT_AGENT : NASCH_LAYOUT_GRID;
+        int layout = 0;
+        plan_road(roads[i], steps[i], rho_star, k_agent, k_grid, &b->roads[(size_t)i], &layout, &n_items[(size_t)i],
+                  &b->super[(size_t)i]);
         b->layout[(size_t)i] = layout;
-        rd.L = (uint32_t)p.L;
-        rd.N = (uint32_t)p.N;
-        rd.vmax = (uint32_t)p.vmax;
-        rd.thr = slow_threshold(p.p);
-        rd.key0 = (uint32_t)p.seed;
-        rd.key1 = (uint32_t)(p.seed >> 32);
-        rd.road_id = p.road_id;
-        rd.T = (uint32_t)steps[i];
-        rd.step0 = 0;
-        int k;
-        if (layout == NASCH_LAYOUT_AGENT) {
-            if (p.N <= (int64_t)kBatchRingCars) {
-                rd.type = kBatchAgentRing;
-                k = p.k ? p.k : kRingK;
-                n_items[(size_t)i] = 1;
-            } else {
-                rd.type = kBatchAgentTile;
-                k = p.k ? p.k : k_agent;
-                rd.halo = round_up((uint32_t)k, (uint32_t)kBatchAgentR);
-                rd.tile = kBatchAgentSpan - rd.halo;
-                const int64_t per_item = (int64_t)rd.tile * (kBatchThreads / 32);
-                n_items[(size_t)i] = (p.N + per_item - 1) / per_item;
-            }
-        } else {
-            if (p.L <= (int64_t)kBatchRingCells) {
-                rd.type = kBatchGridRing;
-                k = p.k ? p.k : kRingK;
-                n_items[(size_t)i] = 1;
-            } else {
-                rd.type = kBatchGridTile;
-                k = p.k ? p.k : k_grid;
-                const int kfit = p.vmax > 0 ? std::max(1, (kGridSpan / 2 - 16) / p.vmax) : kMaxFusedSteps;
-                k = std::min(k, kfit);
-                rd.halo = grid_halo(k, (uint32_t)p.vmax);
-                rd.tile = (uint32_t)kGridSpan - 2u * rd.halo;
-                n_items[(size_t)i] = (p.L + rd.tile - 1) / rd.tile;
-            }
-            max_vmax_grid = std::max(max_vmax_grid, (uint32_t)p.vmax);
-        }
-        rd.k = (uint32_t)k;
-        b->super[(size_t)i] = rd.T == 0 ? 0 : (rd.T + rd.k - 1) / rd.k;
-        if (rd.N == 0) b->super[(size_t)i] = 0, n_items[(size_t)i] = 0;
-        b->vehicle_steps += (int64_t)rd.N * (int64_t)rd.T;
-        b->cell_steps += (int64_t)rd.L * (int64_t)rd.T;
+        if (layout == NASCH_LAYOUT_GRID) max_vmax_grid = std::max(max_vmax_grid, (uint32_t)roads[i].vmax);
+        b->vehicle_steps += (int64_t)roads[i].N * steps[i];
+        b->cell_steps += roads[i].L * steps[i];
     }
     b->padded = (uint32_t)kGridSpan + 16u * ((max_vmax_grid + 15u) / 16u + 2u);
     std::vector<int64_t> order((size_t)n_roads);
@@ -385,7 +399,8 @@ int nasch_submit(const nasch_params *roads, int64_t n_roads, const int64_t *step
 
     // ---------------------------------------------------------------- launches, captured in graphs
     b->blocks = b->sms * batch_blocks_per_sm(b->padded);
-    e = cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming);
+    e = cudaEventCreate(&b->done);
+    if (e == cudaSuccess) e = cudaEventCreate(&b->started);
     std::vector<uint32_t> active((size_t)std::max<int64_t>(b->n_super, 1));
     {
         // roads with S > s are a prefix of `order`; its length only falls as s grows
@@ -424,6 +439,7 @@ int nasch_submit(const nasch_params *roads, int64_t n_roads, const int64_t *step
         e = cudaGraphInstantiate(&x, g, 0);
         if (e == cudaSuccess) b->execs.push_back(x);
     }
+    if (e == cudaSuccess) e = cudaEventRecord(b->started, b->stream);
     for (size_t gi = 0; e == cudaSuccess && gi < b->execs.size(); ++gi) e = cudaGraphLaunch(b->execs[gi], b->stream);
     if (e == cudaSuccess) e = cudaEventRecord(b->done, b->stream);
     if (e != cudaSuccess) {
@@ -549,6 +565,11 @@ int nasch_batch_get_info(nasch_batch b, nasch_batch_info *info)
     info->cell_steps = b->cell_steps;
     info->blocks = b->blocks;
     info->graphs = (int32_t)b->execs.size();
+    info->run_seconds = 0.0;
+    if (b->finished || cudaEventQuery(b->done) == cudaSuccess) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, b->started, b->done) == cudaSuccess) info->run_seconds = ms * 1e-3;
+    }
     return NASCH_OK;
 }
 

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include "kernels.h"
+#include "nasch.h"
 
 namespace nasch {
 
@@ -28,6 +29,8 @@ struct BatchRoadDev {
     uint32_t key0, key1, road_id, k;   // k: steps per super-step
     uint32_t T;                        // steps to run
     uint32_t step0;                    // global index of the first step
+    uint32_t sbase;                    // the road's super-step at launch super_step 0 (serving; 0 in batches)
+    uint32_t pad0;
     uint32_t halo;                     // grid: H cells per side; agent: halo cars per warp-tile
     uint32_t tile;                     // grid: owned cells per item; agent: owned cars per warp-tile
     int32_t *x[2];
@@ -46,11 +49,18 @@ struct BatchLaunch {
     const BatchRoadDev *roads;
     const BatchItem *items;
     uint32_t n_items;                  // active items this super-step (a prefix of the list)
-    uint32_t super_step;
+    uint32_t super_step;               // launch index; road r runs its super-step sbase_r + super_step
     uint32_t *counter;                 // work-list cursor of this super-step (starts at 0)
     const volatile uint32_t *cancel;   // host-mapped; nonzero: skip remaining work
     uint32_t padded;                   // grid buffer length (max over the batch's grid roads)
 };
+
+// Per-road plan shared by batches and the server: layout (AUTO by density),
+// item kind, fusion depth, halo/tile geometry, items per super-step and the
+// number of super-steps.  Pointers and sbase are left zero.
+void plan_road(const nasch_params &p, int64_t T, double rho_star, int k_agent, int k_grid, BatchRoadDev *rd,
+               int *layout, int64_t *n_items, int64_t *super);
+void get_tuning_values(double *rho_star, int *k_agent, int *k_grid);
 
 size_t batch_smem_bytes(uint32_t padded);
 int batch_blocks_per_sm(uint32_t padded);

@@ -94,7 +94,8 @@ __device__ __forceinline__ void batch_grid_tile(const BatchRoadDev &rd, const Ro
         int8_t *nxt = work(o);
         int8_t *clr = work(o == 2u ? 0u : o + 1u);
         uint32_t tsum = 0, tcross = 0;
-        grid_step<D, kWide>(rc, cur, nxt, clr, geo, own_cells, base, step0 + (uint32_t)s, s_list[warp], tsum, tcross);
+        grid_step<D, kWide, 32>(rc, cur, nxt, clr, geo, own_cells, base, step0 + (uint32_t)s, s_list[warp], tsum,
+                                    tcross);
         tsum = __reduce_add_sync(0xFFFFFFFFu, tsum);
         tcross = __reduce_add_sync(0xFFFFFFFFu, tcross);
         if (lane == 0 && (tsum | tcross)) {
@@ -165,9 +166,12 @@ __global__ void __launch_bounds__(kBatchThreads, 3) batch_kernel(const BatchLaun
         if (i >= bl.n_items) break;
         const BatchItem it = bl.items[i];
         const BatchRoadDev rd = bl.roads[it.road];
-        const uint32_t s0 = bl.super_step * rd.k;
-        const int kk = (int)min(rd.k, rd.T - s0);
-        const uint32_t par = bl.super_step & 1u;
+        const uint32_t sst = rd.sbase + bl.super_step;   // this road's super-step
+        const uint32_t s0 = sst * rd.k;
+        // an item past the road's last step has nothing to do (the host never
+        // lists one; this keeps a stale list from writing past the series)
+        const int kk = s0 < rd.T ? (int)min(rd.k, rd.T - s0) : 0;
+        const uint32_t par = sst & 1u;
         const uint32_t step0 = rd.step0 + s0;
         RoadConst rc;
         rc.L = rd.L;
@@ -181,6 +185,7 @@ __global__ void __launch_bounds__(kBatchThreads, 3) batch_kernel(const BatchLaun
             s_cross[j] = 0ull;
         }
         __syncthreads();
+        if (kk == 0) continue;   // uniform across the block; the loop head synchronises again
         switch (draw_mode(rd.thr)) {
         case Draw::kNever:
             batch_item<Draw::kNever>(rd, rc, it.tile, par, step0, kk, bl.padded, pool, s_list, s_first, s_psum,

@@ -5,8 +5,8 @@
 #include <cuda_runtime.h>
 
 #include "nasch.h"
-#include "kernels.h"
 #include "runtime_internal.h"
+#include "tile_device.cuh"
 
 namespace nasch {
 namespace {
@@ -25,10 +25,49 @@ __global__ void __launch_bounds__(256) philox_rate_kernel(uint32_t k0, uint32_t 
     if (acc == 0x9E3779B9u) sink[0] = acc;   // keeps the draws live; practically never taken
 }
 
+// A bounded wait that runs out on purpose: the mbarrier expects 16 bytes
+// that no copy will deliver, so every thread's wait gives up after limit_ns,
+// the kernel records the timeout in the status word and returns.  No copy
+// is in flight, so nothing outlives the kernel.
+__global__ void bounded_wait_selftest_kernel(uint64_t limit_ns, unsigned int *status)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) mbar_expect_tx(&bar, 16);
+    __syncthreads();
+    const bool ok = mbar_wait_bounded(&bar, 0u, limit_ns);
+    if (!__syncthreads_and(ok) && threadIdx.x == 0) atomicOr(status, kStatusTimeout);
+}
+
 }  // namespace
 }  // namespace nasch
 
 using namespace nasch;
+
+extern "C" int nasch_selftest_bounded_wait(int64_t limit_ms, uint32_t *status_out)
+{
+    clear_error();
+    if (limit_ms < 1 || limit_ms > 5000) return fail(NASCH_EINVAL, "limit_ms outside 1..5000");
+    unsigned int *d = nullptr;
+    unsigned int h = 0;
+    cudaError_t e = cudaMalloc(&d, sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMemset(d, 0, sizeof(unsigned int));
+    if (e == cudaSuccess) {
+        bounded_wait_selftest_kernel<<<1, 64>>>((uint64_t)limit_ms * 1000000ull, d);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(&h, d, sizeof(h), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return cuda_fail(e, "bounded-wait self-test");
+    if (status_out) *status_out = h;
+    return h ? fail(NASCH_ETIMEOUT, "the kernel's bounded wait ran out (status 0x%x), as the self-test intends", h)
+             : NASCH_OK;
+}
 
 extern "C" int nasch_calibrate_philox(int64_t draws_per_thread, double *draws_per_second, double *seconds)
 {

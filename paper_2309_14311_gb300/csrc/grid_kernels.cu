@@ -28,6 +28,10 @@
 namespace nasch {
 namespace {
 
+constexpr uint32_t kGridWarps = (uint32_t)kGridThreads / 32u;
+constexpr uint32_t kGridRow = 32u * kGridCellsPerLane;
+static_assert(kGridWarps * kGridRow == (uint32_t)kGridSpan, "one row per warp");
+
 template <Draw D, bool kWide>
 __global__ void __launch_bounds__(kGridThreads) grid_tiled_kernel(const GridStep g, const GridTileGeom geo)
 {
@@ -35,7 +39,7 @@ __global__ void __launch_bounds__(kGridThreads) grid_tiled_kernel(const GridStep
     __shared__ __align__(8) uint64_t s_full[2];
     __shared__ unsigned long long s_sum[kMaxFusedSteps];
     __shared__ unsigned long long s_cross[kMaxFusedSteps];
-    __shared__ uint16_t s_list[kGridWarps][kRowCells];
+    __shared__ uint16_t s_list[kGridWarps][kGridRow];
 
     const RoadConst rc = g.rc;
     const uint32_t L = rc.L;
@@ -45,9 +49,10 @@ __global__ void __launch_bounds__(kGridThreads) grid_tiled_kernel(const GridStep
     const uint32_t WP = geo.padded;
     const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
     int8_t *const pool = reinterpret_cast<int8_t *>(smem);
-    // buffers: stage 0, stage 1 (bulk-load targets), then nwork output buffers
-    auto stage = [&](uint32_t b) { return pool + b * WP; };
-    auto work = [&](uint32_t b) { return pool + (2u + b) * WP; };
+    // four buffers: stage 0, stage 1 (bulk-load targets), work 0, work 1.  A
+    // tile's steps rotate over (its stage, work a, work b): the stage is free
+    // once step 0 has read it.
+    auto buf = [&](uint32_t b) { return pool + b * WP; };
 
     for (int i = tid; i < g.ksteps; i += kGridThreads) {
         s_sum[i] = 0ull;
@@ -58,12 +63,12 @@ __global__ void __launch_bounds__(kGridThreads) grid_tiled_kernel(const GridStep
         mbar_init(&s_full[1], 1);
         fence_mbar_init();
     }
-    // stage padding (never written by the loads) and the output buffers start empty
+    // stage padding (never written by the loads) and both work buffers start empty
     for (uint32_t c = W / 16u + tid; c < WP / 16u; c += kGridThreads) {
-        reinterpret_cast<uint4 *>(stage(0))[c] = kEmpty4;
-        reinterpret_cast<uint4 *>(stage(1))[c] = kEmpty4;
+        reinterpret_cast<uint4 *>(buf(0))[c] = kEmpty4;
+        reinterpret_cast<uint4 *>(buf(1))[c] = kEmpty4;
     }
-    for (uint32_t c = tid; c < geo.nwork * WP / 16u; c += kGridThreads) reinterpret_cast<uint4 *>(work(0))[c] = kEmpty4;
+    for (uint32_t c = tid; c < 2u * WP / 16u; c += kGridThreads) reinterpret_cast<uint4 *>(buf(2))[c] = kEmpty4;
     __syncthreads();
 
     auto bulk_ok = [&](uint32_t tile) {
@@ -71,12 +76,12 @@ __global__ void __launch_bounds__(kGridThreads) grid_tiled_kernel(const GridStep
         return t0 >= H && t0 + C + H <= L;
     };
     uint32_t parity = 0;   // bit b: phase parity of s_full[b]
-    uint32_t wa = 0;       // output buffer of the next tile's first step (already empty)
+    int clean = 2;         // a work buffer known to be all -1, or -1 if none
     uint32_t tile = blockIdx.x;
     if (tid == 0 && tile < geo.n_tiles && bulk_ok(tile)) {
         fence_proxy_async();
         mbar_expect_tx(&s_full[0], W);
-        bulk_load(stage(0), g.c_in + (tile * C - H), W, &s_full[0]);
+        bulk_load(buf(0), g.c_in + (tile * C - H), W, &s_full[0]);
     }
     for (uint32_t it = 0; tile < geo.n_tiles; tile += gridDim.x, ++it) {
         const uint32_t sb = it & 1u;
@@ -90,10 +95,10 @@ __global__ void __launch_bounds__(kGridThreads) grid_tiled_kernel(const GridStep
             if (next < geo.n_tiles && bulk_ok(next)) {
                 fence_proxy_async();
                 mbar_expect_tx(&s_full[sb ^ 1u], W);
-                bulk_load(stage(sb ^ 1u), g.c_in + (next * C - H), W, &s_full[sb ^ 1u]);
+                bulk_load(buf(sb ^ 1u), g.c_in + (next * C - H), W, &s_full[sb ^ 1u]);
             }
         }
-        int8_t *in = stage(sb);
+        int8_t *in = buf(sb);
         bool ok = true;
         if (bulk_ok(tile)) {
             ok = mbar_wait_bounded(&s_full[sb], (parity >> sb) & 1u);
@@ -113,27 +118,37 @@ __global__ void __launch_bounds__(kGridThreads) grid_tiled_kernel(const GridStep
             }
             return;
         }
-
-        const int8_t *cur = in;
+        // rotation (stage, wa, wb); step 0 writes wa, which must be empty
+        const uint32_t wa = clean >= 0 ? (uint32_t)clean : 2u;
+        const uint32_t wb = wa == 2u ? 3u : 2u;
+        if (clean < 0) {
+            for (uint32_t c = tid; c < WP / 16u; c += kGridThreads) reinterpret_cast<uint4 *>(buf(wa))[c] = kEmpty4;
+            __syncthreads();
+        }
+        // buffer at rotation position i (selected arithmetically: no local array)
+        auto rot = [&](uint32_t i) { return i == 0u ? sb : (i == 1u ? wa : wb); };
         for (int s = 0; s < g.ksteps; ++s) {
-            const uint32_t o = (wa + (uint32_t)s) % geo.nwork;
-            int8_t *nxt = work(o);
-            int8_t *clr = work(o + 1u == geo.nwork ? 0u : o + 1u);
+            const uint32_t i0 = (uint32_t)s % 3u;
+            const uint32_t i1 = i0 == 2u ? 0u : i0 + 1u;
+            const uint32_t i2 = i1 == 2u ? 0u : i1 + 1u;
             uint32_t tsum = 0, tcross = 0;
-            grid_step<D, kWide>(rc, cur, nxt, clr, geo, own_cells, base, g.step0 + (uint32_t)s, s_list[warp], tsum,
-                                tcross);
+            grid_step<D, kWide, kGridCellsPerLane>(rc, buf(rot(i0)), buf(rot(i1)), buf(rot(i2)), geo, own_cells, base,
+                                                   g.step0 + (uint32_t)s, s_list[warp], tsum, tcross);
             tsum = __reduce_add_sync(0xFFFFFFFFu, tsum);
             tcross = __reduce_add_sync(0xFFFFFFFFu, tcross);
             if (lane == 0 && (tsum | tcross)) {
                 atomicAdd(&s_sum[s], (unsigned long long)tsum);
                 atomicAdd(&s_cross[s], (unsigned long long)tcross);
             }
-            if (s + 1 == g.ksteps) fence_proxy_async();   // the result may leave by bulk store
+            // the result may leave by bulk store, and a cleared stage may be
+            // refilled by a bulk load
+            if (s + 1 == g.ksteps) fence_proxy_async();
             __syncthreads();
-            cur = nxt;
         }
-        const int8_t *fin = cur;
-        wa = (wa + (uint32_t)g.ksteps) % geo.nwork;
+        const uint32_t k3 = (uint32_t)g.ksteps % 3u;
+        const int8_t *fin = buf(rot(k3));
+        const uint32_t cleared = rot(k3 == 2u ? 0u : k3 + 1u);   // cleared during the last step
+        clean = cleared >= 2u ? (int)cleared : -1;
 
         if (own_cells == C) {
             if (tid == 0) {
@@ -142,6 +157,8 @@ __global__ void __launch_bounds__(kGridThreads) grid_tiled_kernel(const GridStep
             }
         } else {
             for (uint32_t i = tid; i < own_cells; i += kGridThreads) g.c_out[t0 + i] = fin[H + i];
+            // the next tile may clear or scatter into this buffer
+            __syncthreads();
         }
     }
     if (tid == 0) bulk_wait_all();
@@ -172,11 +189,12 @@ GridTileGeom make_geom(int ksteps, uint32_t vmax, uint32_t L)
     // and cars scattered up to vmax cells beyond it
     geo.padded = (uint32_t)kGridSpan + 16u * ((vmax + 15u) / 16u + 2u);
     geo.n_tiles = (L + geo.tile - 1u) / geo.tile;
-    geo.nwork = ksteps == 1 ? 2u : 3u;
+    geo.nwork = 2;
     return geo;
 }
 
-size_t grid_tiled_smem(const GridTileGeom &geo) { return (2u + geo.nwork) * (size_t)geo.padded; }
+// two stage buffers and two work buffers
+size_t grid_tiled_smem(const GridTileGeom &geo) { return 4u * (size_t)geo.padded; }
 
 // Static plus dynamic shared memory exceeds the default 48 KB, so the
 // dynamic size is allowed explicitly (a per-device function attribute).

@@ -323,6 +323,7 @@ int nasch_floyd_init(int64_t L, int64_t N, uint64_t seed, uint32_t road_id, int3
 int nasch_create_ex(const nasch_params *prm, nasch_handle *out)
 {
     clear_error();
+    TraceRange trace("nasch_create");
     if (!out) return fail(NASCH_EINVAL, "out is NULL");
     *out = nullptr;
     int st = validate_params(prm);
@@ -451,6 +452,7 @@ int nasch_set_state(nasch_handle h, const int32_t *x_host, const uint8_t *v_host
 int nasch_run(nasch_handle h, int64_t steps)
 {
     clear_error();
+    TraceRange trace("nasch_run");
     if (!h) return fail(NASCH_EINVAL, "handle is NULL");
     if (steps < 0) return fail(NASCH_EINVAL, "steps=%lld < 0", (long long)steps);
     if (steps == 0) return NASCH_OK;

@@ -4,9 +4,20 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "nasch.h"
 
 namespace nasch {
+
+// Names a host phase in profiler timelines (NVTX range; free when no tool
+// is attached).
+struct TraceRange {
+    explicit TraceRange(const char *name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+    TraceRange(const TraceRange &) = delete;
+    TraceRange &operator=(const TraceRange &) = delete;
+};
 
 // Record a message for nasch_last_error() and return `code`.
 int fail(int code, const char *fmt, ...);

@@ -158,9 +158,6 @@ __device__ __forceinline__ uint32_t occupancy16(const uint4 q)
 }
 
 constexpr uint4 kEmpty4 = {0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu};
-constexpr int kGridWarps = kGridThreads / 32;
-constexpr uint32_t kRowCells = 1024u;               // one warp's row: 32 lanes x 32 cells
-static_assert(kGridWarps * kRowCells == (uint32_t)kGridSpan, "one row per warp");
 constexpr uint64_t kWaitLimitNs = 1000000000ull;    // bounded wait on an async copy: 1 s
 
 // ---- PTX wrappers: shared-memory mbarriers and 1-D bulk (TMA) copies ----
@@ -203,13 +200,14 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
     return done != 0;
 }
 
-// Wait for the phase of `bar` with the given parity, for at most 1 s.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
+// Wait for the phase of `bar` with the given parity, for at most limit_ns
+// (1 s by default); false if the wait ran out.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, uint64_t limit_ns = kWaitLimitNs)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_ns();
     while (!mbar_try_wait(bar, parity))
-        if (global_ns() - t0 > kWaitLimitNs) return false;
+        if (global_ns() - t0 > limit_ns) return false;
     return true;
 }
 
@@ -242,35 +240,46 @@ struct GridTileGeom {
 };
 
 // One synchronous step over a staged span: read `cur`, scatter every car
-// into `nxt` (already all -1), and clear `clr` for the step after.  Warp w
-// owns cells [1024w, 1024w + 1024): each lane turns its 32 cells into an
+// into `nxt` (already all -1), and clear `clr` for the step after.  The span
+// is cut into rows of 32 * CPL cells, one per warp (the block has
+// kGridSpan / (32 * CPL) warps): each lane turns its CPL cells into an
 // occupancy mask, the warp compacts the row's cars into a list of cell
 // indices, and the lanes then take the cars of the list in turn, so that
 // every lane applies rules 1-4 to the same number of cars (a lane's own
-// cells hold 0..32 cars).  A car's gap comes from its owner lane's mask and
-// the next lane's mask (shuffles) by one funnel shift and find-first-set.
+// cells hold 0..CPL cars).  A car's gap comes from its owner lane's mask and
+// the next lane's mask (shuffles) by a shift and find-first-set.
 // kWide: vmax > 16, gaps may reach past the two masks.
-template <Draw D, bool kWide>
+template <Draw D, bool kWide, int CPL>
 __device__ __forceinline__ void grid_step(const RoadConst &rc, const int8_t *__restrict__ cur, int8_t *nxt,
                                           int8_t *clr, const GridTileGeom &geo, uint32_t own_cells, uint32_t base,
                                           uint32_t step, uint16_t *list, uint32_t &tsum, uint32_t &tcross)
 {
+    static_assert(CPL == 16 || CPL == 32, "16 or 32 cells per lane");
+    constexpr uint32_t kRow = 32u * CPL;
+    constexpr uint32_t kWarps = (uint32_t)kGridSpan / kRow;
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
-    const uint32_t row0 = warp * kRowCells;
+    const uint32_t row0 = warp * kRow;
     const uint32_t H = geo.halo;
     const uint32_t L = rc.L;
 
     uint4 *clr4 = reinterpret_cast<uint4 *>(clr + row0);
     clr4[lane] = kEmpty4;
-    clr4[lane + 32] = kEmpty4;
-    if (warp == kGridWarps - 1)
+    if (CPL == 32) clr4[lane + 32] = kEmpty4;
+    if (warp == kWarps - 1)
         for (uint32_t c = lane; c < (geo.padded - (uint32_t)kGridSpan) / 16u; c += 32u)
             reinterpret_cast<uint4 *>(clr + kGridSpan)[c] = kEmpty4;
 
-    const uint4 *mine = reinterpret_cast<const uint4 *>(cur + row0 + 32u * lane);
-    const uint32_t m = occupancy16(mine[0]) | (occupancy16(mine[1]) << 16);
-    uint32_t m_next = __shfl_down_sync(0xFFFFFFFFu, m, 1);
-    if (lane == 31) m_next = occupancy16(mine[2]);   // first 16 cells of the next row (or the padding)
+    const uint4 *mine = reinterpret_cast<const uint4 *>(cur + row0 + CPL * lane);
+    uint32_t m, m_next;
+    if (CPL == 32) {
+        m = occupancy16(mine[0]) | (occupancy16(mine[1]) << 16);
+        m_next = __shfl_down_sync(0xFFFFFFFFu, m, 1);
+        if (lane == 31) m_next = occupancy16(mine[2]);   // first 16 cells of the next row (or the padding)
+    } else {
+        m = occupancy16(mine[0]);
+        m_next = __shfl_down_sync(0xFFFFFFFFu, m, 1);
+        if (lane == 31) m_next = occupancy16(mine[1]);
+    }
     const uint32_t n = __popc(m);
     uint32_t incl = n;
 #pragma unroll
@@ -281,25 +290,27 @@ __device__ __forceinline__ void grid_step(const RoadConst &rc, const int8_t *__r
     const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
     if (total == 0) return;
     uint32_t pos = incl - n;
-    for (uint32_t mm = m; mm; mm &= mm - 1u) list[pos++] = (uint16_t)(32u * lane + (uint32_t)(__ffs(mm) - 1));
+    for (uint32_t mm = m; mm; mm &= mm - 1u) list[pos++] = (uint16_t)(CPL * lane + (uint32_t)(__ffs(mm) - 1));
     __syncwarp();
 
-    for (uint32_t first = 0; first < total; first += 32u) {
-        const uint32_t i = first + lane;
-        const bool active = i < total;
-        const uint32_t r = active ? (uint32_t)list[i] : 0u;   // cell index within the row
-        const uint32_t src = r >> 5, bit = r & 31u;
-        const uint32_t wm = __shfl_sync(0xFFFFFFFFu, m, src);
-        const uint32_t wn = __shfl_sync(0xFFFFFFFFu, m_next, src);
-        if (!active) continue;
-        // occupancy of the 32 cells after the car
-        const uint32_t after = __funnelshift_rc(wm, wn, bit + 1u);
-        uint32_t gap = after ? (uint32_t)(__ffs(after) - 1) : 32u;
+    // one car: rules 1-4 from its row index r and its owner lane's masks;
+    // computed without branches (an idle lane computes a dummy car and does
+    // not store), so two cars per lane interleave
+    auto car = [&](bool active, uint32_t r, uint32_t wm, uint32_t wn) {
+        const uint32_t bit = r & (CPL - 1u);
+        const uint32_t src = CPL == 32 ? r >> 5 : r >> 4;
+        uint32_t after, known;
+        if (CPL == 32) {
+            after = __funnelshift_rc(wm, wn, bit + 1u);
+            known = src == 31u ? 47u - bit : 32u;
+        } else {
+            after = (wm | (wn << 16)) >> (bit + 1u);
+            known = 31u - bit;
+        }
+        uint32_t gap = after ? (uint32_t)(__ffs(after) - 1) : known;
         const uint32_t idx = row0 + r;
-        if (kWide) {
-            // the masks know 32 cells ahead (16 fewer for the row's last lane);
-            // past them, scan the bytes
-            uint32_t known = src == 31u ? 47u - bit : 32u;
+        if (kWide && active) {
+            // past the cells the masks know, scan the bytes
             if (gap > known) gap = known;
             while (gap == known && gap < rc.vmax) {
                 if (cur[idx + 1u + gap] >= 0) break;
@@ -316,10 +327,29 @@ __device__ __forceinline__ void grid_step(const RoadConst &rc, const int8_t *__r
             const uint32_t u = philox_word0(cell, step, rc.road, kTagSlowdown, rc.key0, rc.key1);
             vel -= (vel > 0u && u < (uint32_t)rc.thr) ? 1u : 0u;                    // rule 3
         }
-        nxt[idx + vel] = (int8_t)vel;                                               // rule 4
-        if (idx - H < own_cells) {
-            tsum += vel;
-            tcross += (cell + vel >= L) ? 1u : 0u;
+        if (active) {
+            nxt[idx + vel] = (int8_t)vel;                                           // rule 4
+            if (idx - H < own_cells) {
+                tsum += vel;
+                tcross += (cell + vel >= L) ? 1u : 0u;
+            }
+        }
+    };
+    constexpr uint32_t kShift = CPL == 32 ? 5u : 4u;
+    for (uint32_t first = 0; first < total; first += 64u) {
+        const uint32_t i0 = first + lane, i1 = i0 + 32u;
+        const bool a0 = i0 < total, a1 = i1 < total;
+        const uint32_t r0 = a0 ? (uint32_t)list[i0] : 0u;
+        const uint32_t wm0 = __shfl_sync(0xFFFFFFFFu, m, r0 >> kShift);
+        const uint32_t wn0 = __shfl_sync(0xFFFFFFFFu, m_next, r0 >> kShift);
+        if (first + 32u < total) {   // warp-uniform: a second car for (some) lanes
+            const uint32_t r1 = a1 ? (uint32_t)list[i1] : 0u;
+            const uint32_t wm1 = __shfl_sync(0xFFFFFFFFu, m, r1 >> kShift);
+            const uint32_t wn1 = __shfl_sync(0xFFFFFFFFu, m_next, r1 >> kShift);
+            car(a0, r0, wm0, wn0);
+            car(a1, r1, wm1, wn1);
+        } else {
+            car(a0, r0, wm0, wn0);
         }
     }
     __syncwarp();

@@ -55,7 +55,8 @@ class Info(ctypes.Structure):
 class BatchInfo(ctypes.Structure):
     _fields_ = [("n_roads", ctypes.c_int64), ("super_steps", ctypes.c_int64), ("items", ctypes.c_int64),
                 ("device_bytes", ctypes.c_int64), ("vehicle_steps", ctypes.c_int64),
-                ("cell_steps", ctypes.c_int64), ("blocks", ctypes.c_int32), ("graphs", ctypes.c_int32)]
+                ("cell_steps", ctypes.c_int64), ("blocks", ctypes.c_int32), ("graphs", ctypes.c_int32),
+                ("run_seconds", ctypes.c_double)]
 
 
 _lib = None
@@ -116,6 +117,18 @@ def _declare(lib) -> None:
         "nasch_batch_destroy": (None, [H]),
         "nasch_set_tuning": (ctypes.c_int, [dbl, i32, i32]),
         "nasch_floyd_init_device_noalloc": (ctypes.c_int, [i64, i64, u64, u32, P, P]),
+        "nasch_selftest_bounded_wait": (ctypes.c_int, [i64, P]),
+        "nasch_server_config_init": (None, [P]),
+        "nasch_server_create": (ctypes.c_int, [P, P]),
+        "nasch_server_submit": (ctypes.c_int, [H, P, i64, u64]),
+        "nasch_server_step": (ctypes.c_int, [H, P]),
+        "nasch_server_drain": (ctypes.c_int, [H, i64]),
+        "nasch_server_poll": (ctypes.c_int, [H, P, i64, P]),
+        "nasch_server_result": (ctypes.c_int, [H, u64, P, P, i64, P, P, i64]),
+        "nasch_server_release": (ctypes.c_int, [H, u64]),
+        "nasch_server_cancel": (ctypes.c_int, [H, u64]),
+        "nasch_server_get_info": (ctypes.c_int, [H, P]),
+        "nasch_server_destroy": (None, [H]),
         "nasch_get_tuning": (ctypes.c_int, [P, P, P]),
     }
     for name, (res, args) in sig.items():
@@ -157,6 +170,13 @@ def floyd_init_device_noalloc(L: int, N: int, seed: int, road: int, x_dev_ptr: i
     `stream`.  Roads of at most 2^24 cells."""
     _check(load().nasch_floyd_init_device_noalloc(int(L), int(N), int(seed), int(road), ctypes.c_void_p(x_dev_ptr),
                                                   _stream_handle(stream)))
+
+
+def selftest_bounded_wait(limit_ms: int = 50):
+    """Run the bounded-wait self-test kernel; returns (status code, status word)."""
+    w = ctypes.c_uint32()
+    st = load().nasch_selftest_bounded_wait(int(limit_ms), ctypes.byref(w))
+    return st, w.value
 
 
 def calibrate_philox(draws_per_thread: int = 1 << 14) -> float:
@@ -346,3 +366,97 @@ class Batch:
         a, c = ctypes.c_uint64(), ctypes.c_uint64()
         _check(load().nasch_batch_stats_sum(self._h, i, first, count, ctypes.byref(a), ctypes.byref(c)))
         return a.value, c.value
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("memory_budget", ctypes.c_int64), ("steps_per_tick", ctypes.c_int32),
+                ("max_resident", ctypes.c_int32), ("keep_state", ctypes.c_int32), ("stream", ctypes.c_void_p)]
+
+
+class RequestResult(ctypes.Structure):
+    _fields_ = [("request_id", ctypes.c_uint64), ("status", ctypes.c_int32), ("layout", ctypes.c_int32),
+                ("steps", ctypes.c_int64), ("vehicles", ctypes.c_int64), ("submit_time", ctypes.c_double),
+                ("admit_time", ctypes.c_double), ("done_time", ctypes.c_double)]
+
+
+class ServerInfo(ctypes.Structure):
+    _fields_ = [("queued", ctypes.c_int64), ("resident", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("bytes_in_use", ctypes.c_int64), ("ticks", ctypes.c_int64), ("vehicle_steps_done", ctypes.c_int64),
+                ("blocks", ctypes.c_int32), ("now", ctypes.c_double)]
+
+
+class Server:
+    """Continuous-batching request loop (``nasch_server_*``)."""
+
+    def __init__(self, memory_budget: int = 40 << 30, steps_per_tick: int = 8, max_resident: int = 4096,
+                 keep_state: bool = False, stream=None):
+        lib = load()
+        cfg = ServerConfig()
+        lib.nasch_server_config_init(ctypes.byref(cfg))
+        cfg.memory_budget, cfg.steps_per_tick, cfg.max_resident = int(memory_budget), int(steps_per_tick), int(max_resident)
+        cfg.keep_state = 1 if keep_state else 0
+        cfg.stream = _stream_handle(stream)
+        self._stream_ref = stream
+        h = ctypes.c_void_p()
+        _check(lib.nasch_server_create(ctypes.byref(cfg), ctypes.byref(h)))
+        self._h = h
+        self._roads = {}
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            load().nasch_server_destroy(self._h)
+            self._h = None
+
+    __del__ = close
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def submit(self, road: dict, steps: int, request_id: int) -> None:
+        prm = make_params(**road)
+        _check(load().nasch_server_submit(self._h, ctypes.byref(prm), int(steps), int(request_id)))
+        self._roads[int(request_id)] = (int(road["N"]), int(steps))
+
+    def step(self) -> int:
+        pending = ctypes.c_int64()
+        _check(load().nasch_server_step(self._h, ctypes.byref(pending)))
+        return pending.value
+
+    def drain(self, timeout_ms: int = -1) -> None:
+        _check(load().nasch_server_drain(self._h, int(timeout_ms)))
+
+    def poll(self, cap: int = 4096):
+        out = (RequestResult * cap)()
+        n = ctypes.c_int64()
+        _check(load().nasch_server_poll(self._h, out, cap, ctypes.byref(n)))
+        return [dict(request_id=r.request_id, status=r.status, layout=r.layout, steps=r.steps, vehicles=r.vehicles,
+                     submit_time=r.submit_time, admit_time=r.admit_time, done_time=r.done_time)
+                for r in out[: n.value]]
+
+    def result(self, request_id: int, with_state: bool = False):
+        N, T = self._roads[int(request_id)]
+        sv = np.zeros(max(T, 1), dtype=np.uint64)
+        cr = np.zeros(max(T, 1), dtype=np.uint64)
+        if with_state:
+            x = np.zeros(max(N, 1), dtype=np.int32)
+            v = np.zeros(max(N, 1), dtype=np.uint8)
+            _check(load().nasch_server_result(self._h, int(request_id), _ptr(sv), _ptr(cr), len(sv), _ptr(x), _ptr(v),
+                                              len(x)))
+            return sv[:T], cr[:T], x[:N], v[:N]
+        _check(load().nasch_server_result(self._h, int(request_id), _ptr(sv), _ptr(cr), len(sv), None, None, 0))
+        return sv[:T], cr[:T]
+
+    def release(self, request_id: int) -> None:
+        _check(load().nasch_server_release(self._h, int(request_id)))
+        self._roads.pop(int(request_id), None)
+
+    def cancel(self, request_id: int) -> None:
+        _check(load().nasch_server_cancel(self._h, int(request_id)))
+
+    def info(self) -> ServerInfo:
+        inf = ServerInfo()
+        _check(load().nasch_server_get_info(self._h, ctypes.byref(inf)))
+        return inf

@@ -31,7 +31,7 @@ EXAMPLE_PARAMS = RoadSpec("example-params L=500 N=300 vmax=2 p=0.2 T=500", 500, 
 
 # Launch configuration the benchmark times on LARGE_ROAD (fusion depth per
 # layout); the full-size parity tests run the same.
-LARGE_ROAD_K = {"agent": 4, "grid": 8}
+LARGE_ROAD_K = {"agent": 16, "grid": 8}
 
 
 # --------------------------------------------------------------------------- batched workloads

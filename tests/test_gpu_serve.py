@@ -1,0 +1,106 @@
+"""GPU tests of the serving loop (continuous batching under a memory budget).
+
+Requests arriving while others run are admitted into the same launches; each
+request's per-step statistics and final state must equal the same road run
+alone through the single-road API (bit-exact; its draws are keyed by its
+own seed and road id).  The budget bounds what is resident; requests that
+can never fit are refused; cancelled requests report so.
+"""
+import numpy as np
+import pytest
+
+from paper_2309_14311_gb300 import nasch as NS
+from paper_2309_14311_gb300 import serve as SV
+from paper_2309_14311_gb300 import workloads as WL
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2309_14311_gb300 import build
+    build.build()
+    NS.load()
+
+
+def mixed_requests(n, seed=0):
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for i in range(n):
+        L = int(rng.choice([900, 5000, 20000, 70000, 300000]))
+        rho = float(rng.uniform(0.03, 0.7))
+        N = max(1, min(L, int(rho * L)))
+        reqs.append(dict(L=L, N=N, vmax=int(rng.choice([3, 5, 8, 20])), p=float(rng.choice([0.0, 0.13, 0.4, 1.0])),
+                         seed=int(rng.integers(1, 1000)), road_id=1000 + i, T=int(rng.integers(0, 120))))
+    return reqs
+
+
+def alone(r):
+    lay = "agent" if r["N"] < 0.2 * r["L"] else "grid"
+    with NS.Road(r["L"], r["N"], r["vmax"], r["p"], r["seed"], r["road_id"], layout=lay) as road:
+        road.run(r["T"])
+        sv, cr = road.stats()
+        x, v = road.read_state()   # agent: car order; grid: cell order (the server returns the same)
+        return sv.copy(), cr.copy(), x.copy(), v.copy()
+
+
+def test_requests_in_the_mix_equal_alone():
+    reqs = mixed_requests(48)
+    with NS.Server(memory_budget=1 << 30, steps_per_tick=4, max_resident=16, keep_state=True) as srv:
+        # submit in waves while earlier requests are running
+        for wave in range(4):
+            for i in range(wave * 12, wave * 12 + 12):
+                srv.submit(WL.road_params(reqs[i]), reqs[i]["T"], i)
+            for _ in range(3):
+                srv.step()
+        srv.drain(600000)
+        results = {r["request_id"]: r for r in srv.poll()}
+        assert sorted(results) == list(range(len(reqs)))
+        for i, r in enumerate(reqs):
+            assert results[i]["status"] == NS.OK
+            sv, cr, x, v = srv.result(i, with_state=True)
+            asv, acr, ax, av = alone(r)
+            assert np.array_equal(sv, asv) and np.array_equal(cr, acr), i
+            assert np.array_equal(x, ax) and np.array_equal(v, av), i
+        inf = srv.info()
+        assert inf.resident == 0 and inf.queued == 0 and inf.bytes_in_use == 0
+
+
+def test_budget_bounds_residency_and_oversize_is_refused():
+    # each request: agent N=400k -> 2*(1.6 MB + 0.4 MB) + stats, about 4 MB; budget 10 MB
+    road = dict(L=4_000_000, N=400_000, vmax=5, p=0.13, seed=1)
+    with NS.Server(memory_budget=10 << 20, steps_per_tick=2, max_resident=64) as srv:
+        for i in range(6):
+            srv.submit(dict(road, road_id=i), 20, i)
+        peak = 0
+        while srv.step() > 0:
+            peak = max(peak, srv.info().resident)
+        srv.drain(600000)
+        assert 1 <= peak <= 2
+        assert len(srv.poll()) == 6
+        with pytest.raises(NS.NaschError) as e:
+            srv.submit(dict(L=2**31, N=2**20, vmax=5, p=0.1, seed=1, road_id=99), 10, 99)
+        assert e.value.status == NS.ENOMEM
+
+
+def test_cancel_queued_and_running():
+    road = dict(L=2_000_000, N=100_000, vmax=5, p=0.13, seed=3)
+    with NS.Server(memory_budget=1 << 30, steps_per_tick=2, max_resident=1) as srv:
+        srv.submit(dict(road, road_id=1), 200_000, 1)   # long, occupies the only slot
+        srv.submit(dict(road, road_id=2), 50, 2)        # waits in the queue
+        srv.step()
+        srv.cancel(2)
+        srv.cancel(1)
+        srv.drain(600000)
+        res = {r["request_id"]: r for r in srv.poll()}
+        assert res[1]["status"] == NS.ECANCELED and res[2]["status"] == NS.ECANCELED
+
+
+def test_poisson_driver_small_stream():
+    rows = [r for r in WL.request_stream() if r["N"] * r["T"] < 3e7][:40]
+    out = SV.run_poisson(rows, rate=200.0, memory_budget=2 << 30, steps_per_tick=8)
+    assert out["completed"] == len(rows)
+    assert out["latency_p99_s"] >= out["latency_p50_s"] > 0
