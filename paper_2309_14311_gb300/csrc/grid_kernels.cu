@@ -31,15 +31,17 @@ namespace {
 constexpr uint32_t kGridWarps = (uint32_t)kGridThreads / 32u;
 constexpr uint32_t kGridRow = 32u * kGridCellsPerLane;
 static_assert(kGridWarps * kGridRow == (uint32_t)kGridSpan, "one row per warp");
+constexpr uint32_t kGridStages = 2;      // spans in flight per block: the current one and one prefetched
+constexpr uint32_t kGridListCap = 512;   // cars per list pass (a row holds up to 1024)
 
 template <Draw D, bool kWide>
 __global__ void __launch_bounds__(kGridThreads) grid_tiled_kernel(const GridStep g, const GridTileGeom geo)
 {
     extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ __align__(8) uint64_t s_full[2];
+    __shared__ __align__(8) uint64_t s_full[kGridStages];
     __shared__ unsigned long long s_sum[kMaxFusedSteps];
     __shared__ unsigned long long s_cross[kMaxFusedSteps];
-    __shared__ uint16_t s_list[kGridWarps][kGridRow];
+    __shared__ uint16_t s_list[kGridWarps][kGridListCap];
 
     const RoadConst rc = g.rc;
     const uint32_t L = rc.L;
@@ -49,9 +51,9 @@ __global__ void __launch_bounds__(kGridThreads) grid_tiled_kernel(const GridStep
     const uint32_t WP = geo.padded;
     const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
     int8_t *const pool = reinterpret_cast<int8_t *>(smem);
-    // four buffers: stage 0, stage 1 (bulk-load targets), work 0, work 1.  A
-    // tile's steps rotate over (its stage, work a, work b): the stage is free
-    // once step 0 has read it.
+    // five buffers: stages 0..2 (bulk-load targets), work 3, work 4.  A tile's
+    // steps rotate over (its stage, work a, work b): the stage is free once
+    // step 0 has read it, until it is refilled for the tile three ahead.
     auto buf = [&](uint32_t b) { return pool + b * WP; };
 
     for (int i = tid; i < g.ksteps; i += kGridThreads) {
@@ -59,49 +61,56 @@ __global__ void __launch_bounds__(kGridThreads) grid_tiled_kernel(const GridStep
         s_cross[i] = 0ull;
     }
     if (tid == 0) {
-        mbar_init(&s_full[0], 1);
-        mbar_init(&s_full[1], 1);
+        for (uint32_t b = 0; b < kGridStages; ++b) mbar_init(&s_full[b], 1);
         fence_mbar_init();
     }
     // stage padding (never written by the loads) and both work buffers start empty
-    for (uint32_t c = W / 16u + tid; c < WP / 16u; c += kGridThreads) {
-        reinterpret_cast<uint4 *>(buf(0))[c] = kEmpty4;
-        reinterpret_cast<uint4 *>(buf(1))[c] = kEmpty4;
-    }
-    for (uint32_t c = tid; c < 2u * WP / 16u; c += kGridThreads) reinterpret_cast<uint4 *>(buf(2))[c] = kEmpty4;
+    for (uint32_t b = 0; b < kGridStages; ++b)
+        for (uint32_t c = W / 16u + tid; c < WP / 16u; c += kGridThreads) reinterpret_cast<uint4 *>(buf(b))[c] = kEmpty4;
+    for (uint32_t c = tid; c < 2u * WP / 16u; c += kGridThreads)
+        reinterpret_cast<uint4 *>(buf(kGridStages))[c] = kEmpty4;
     __syncthreads();
 
     auto bulk_ok = [&](uint32_t tile) {
         const uint32_t t0 = tile * C;
         return t0 >= H && t0 + C + H <= L;
     };
-    uint32_t parity = 0;   // bit b: phase parity of s_full[b]
-    int clean = 2;         // a work buffer known to be all -1, or -1 if none
+    uint32_t parity = 0;                  // bit b: phase parity of s_full[b]
+    int clean = (int)kGridStages;         // a work buffer known to be all -1, or -1 if none
     uint32_t tile = blockIdx.x;
-    if (tid == 0 && tile < geo.n_tiles && bulk_ok(tile)) {
-        fence_proxy_async();
-        mbar_expect_tx(&s_full[0], W);
-        bulk_load(buf(0), g.c_in + (tile * C - H), W, &s_full[0]);
+    if (tid == 0) {
+        // the first two spans of this block
+        for (uint32_t b = 0; b + 1 < kGridStages; ++b) {
+            const uint32_t t = tile + b * gridDim.x;
+            if (t < geo.n_tiles && bulk_ok(t)) {
+                fence_proxy_async();
+                mbar_expect_tx(&s_full[b], W);
+                bulk_load(buf(b), g.c_in + (t * C - H), W, &s_full[b]);
+            }
+        }
     }
     for (uint32_t it = 0; tile < geo.n_tiles; tile += gridDim.x, ++it) {
-        const uint32_t sb = it & 1u;
+        const uint32_t sb = it % kGridStages;
         const uint32_t t0 = tile * C;
         const uint32_t own_cells = min(C, L - t0);
         const uint32_t base = t0 >= H ? t0 - H : t0 + L - H;   // road cell of buffer index 0
-        const uint32_t next = tile + gridDim.x;
+        const uint32_t ahead = tile + (kGridStages - 1u) * gridDim.x;
+        const uint32_t ab = (it + kGridStages - 1u) % kGridStages;   // its stage: the one tile it-1 used
         if (tid == 0) {
             // earlier bulk stores must have read their source before buffers are reused
             bulk_wait_read_all();
-            if (next < geo.n_tiles && bulk_ok(next)) {
+            if (ahead < geo.n_tiles && bulk_ok(ahead)) {
                 fence_proxy_async();
-                mbar_expect_tx(&s_full[sb ^ 1u], W);
-                bulk_load(buf(sb ^ 1u), g.c_in + (next * C - H), W, &s_full[sb ^ 1u]);
+                mbar_expect_tx(&s_full[ab], W);
+                bulk_load(buf(ab), g.c_in + (ahead * C - H), W, &s_full[ab]);
             }
         }
         int8_t *in = buf(sb);
         bool ok = true;
         if (bulk_ok(tile)) {
-            ok = mbar_wait_bounded(&s_full[sb], (parity >> sb) & 1u);
+            // one thread waits for the span; the barrier below releases the
+            // others (waiting warps would otherwise take issue slots)
+            if (tid == 0) ok = mbar_wait_bounded(&s_full[sb], (parity >> sb) & 1u);
             parity ^= 1u << sb;
         } else {
             for (uint32_t i = tid; i < W; i += kGridThreads) {
@@ -113,14 +122,18 @@ __global__ void __launch_bounds__(kGridThreads) grid_tiled_kernel(const GridStep
         if (!__syncthreads_and(ok)) {
             if (tid == 0) {
                 atomicOr(g.status, kStatusTimeout);
-                if (next < geo.n_tiles && bulk_ok(next)) mbar_wait_bounded(&s_full[sb ^ 1u], (parity >> (sb ^ 1u)) & 1u);
+                // let the loads still in flight land before the block's memory goes
+                for (uint32_t d = 1; d < kGridStages; ++d) {
+                    const uint32_t t = tile + d * gridDim.x, b = (it + d) % kGridStages;
+                    if (t < geo.n_tiles && bulk_ok(t)) mbar_wait_bounded(&s_full[b], (parity >> b) & 1u);
+                }
                 bulk_wait_all();
             }
             return;
         }
         // rotation (stage, wa, wb); step 0 writes wa, which must be empty
-        const uint32_t wa = clean >= 0 ? (uint32_t)clean : 2u;
-        const uint32_t wb = wa == 2u ? 3u : 2u;
+        const uint32_t wa = clean >= 0 ? (uint32_t)clean : kGridStages;
+        const uint32_t wb = wa == kGridStages ? kGridStages + 1u : kGridStages;
         if (clean < 0) {
             for (uint32_t c = tid; c < WP / 16u; c += kGridThreads) reinterpret_cast<uint4 *>(buf(wa))[c] = kEmpty4;
             __syncthreads();
@@ -132,8 +145,9 @@ __global__ void __launch_bounds__(kGridThreads) grid_tiled_kernel(const GridStep
             const uint32_t i1 = i0 == 2u ? 0u : i0 + 1u;
             const uint32_t i2 = i1 == 2u ? 0u : i1 + 1u;
             uint32_t tsum = 0, tcross = 0;
-            grid_step<D, kWide, kGridCellsPerLane>(rc, buf(rot(i0)), buf(rot(i1)), buf(rot(i2)), geo, own_cells, base,
-                                                   g.step0 + (uint32_t)s, s_list[warp], tsum, tcross);
+            grid_step<D, kWide, kGridCellsPerLane, kGridListCap>(rc, buf(rot(i0)), buf(rot(i1)), buf(rot(i2)), geo,
+                                                                 own_cells, base, g.step0 + (uint32_t)s, s_list[warp],
+                                                                 tsum, tcross);
             tsum = __reduce_add_sync(0xFFFFFFFFu, tsum);
             tcross = __reduce_add_sync(0xFFFFFFFFu, tcross);
             if (lane == 0 && (tsum | tcross)) {
@@ -148,7 +162,7 @@ __global__ void __launch_bounds__(kGridThreads) grid_tiled_kernel(const GridStep
         const uint32_t k3 = (uint32_t)g.ksteps % 3u;
         const int8_t *fin = buf(rot(k3));
         const uint32_t cleared = rot(k3 == 2u ? 0u : k3 + 1u);   // cleared during the last step
-        clean = cleared >= 2u ? (int)cleared : -1;
+        clean = cleared >= kGridStages ? (int)cleared : -1;
 
         if (own_cells == C) {
             if (tid == 0) {
@@ -193,8 +207,8 @@ GridTileGeom make_geom(int ksteps, uint32_t vmax, uint32_t L)
     return geo;
 }
 
-// two stage buffers and two work buffers
-size_t grid_tiled_smem(const GridTileGeom &geo) { return 4u * (size_t)geo.padded; }
+// three stage buffers and two work buffers
+size_t grid_tiled_smem(const GridTileGeom &geo) { return (kGridStages + 2u) * (size_t)geo.padded; }
 
 // Static plus dynamic shared memory exceeds the default 48 KB, so the
 // dynamic size is allowed explicitly (a per-device function attribute).

@@ -148,8 +148,10 @@ __device__ __forceinline__ void agent_warp_tile(const AgentStep &a, uint32_t t0,
 // its sign bit clear, i.e. holds a car).
 __device__ __forceinline__ uint32_t occupancy4(uint32_t w)
 {
-    const uint32_t m = (~w >> 7) & 0x01010101u;
-    return (m * 0x10204080u) >> 28;
+    // sign bits of the bytes, inverted, at bits 7, 15, 23, 31; the multiply
+    // gathers them into bits 28..31 (the partial products below bit 28 add
+    // up to less than 2^24, so nothing carries into them)
+    return ((~w & 0x80808080u) * 0x00204081u) >> 28;
 }
 
 __device__ __forceinline__ uint32_t occupancy16(const uint4 q)
@@ -249,7 +251,9 @@ struct GridTileGeom {
 // cells hold 0..CPL cars).  A car's gap comes from its owner lane's mask and
 // the next lane's mask (shuffles) by a shift and find-first-set.
 // kWide: vmax > 16, gaps may reach past the two masks.
-template <Draw D, bool kWide, int CPL>
+// kListCap: entries of the warp's car list; a row with more cars is done in
+// several passes over its masks.
+template <Draw D, bool kWide, int CPL, uint32_t kListCap = 32u * CPL>
 __device__ __forceinline__ void grid_step(const RoadConst &rc, const int8_t *__restrict__ cur, int8_t *nxt,
                                           int8_t *clr, const GridTileGeom &geo, uint32_t own_cells, uint32_t base,
                                           uint32_t step, uint16_t *list, uint32_t &tsum, uint32_t &tcross)
@@ -270,15 +274,19 @@ __device__ __forceinline__ void grid_step(const RoadConst &rc, const int8_t *__r
             reinterpret_cast<uint4 *>(clr + kGridSpan)[c] = kEmpty4;
 
     const uint4 *mine = reinterpret_cast<const uint4 *>(cur + row0 + CPL * lane);
+    // every lane also reads the chunk after its own cells: cheaper than a
+    // branch for the one lane (31) whose next cells belong to the next row
     uint32_t m, m_next;
     if (CPL == 32) {
         m = occupancy16(mine[0]) | (occupancy16(mine[1]) << 16);
+        const uint32_t beyond = occupancy16(mine[2]);   // first 16 cells after (the next row, or padding)
         m_next = __shfl_down_sync(0xFFFFFFFFu, m, 1);
-        if (lane == 31) m_next = occupancy16(mine[2]);   // first 16 cells of the next row (or the padding)
+        if (lane == 31) m_next = beyond;
     } else {
         m = occupancy16(mine[0]);
+        const uint32_t beyond = occupancy16(mine[1]);
         m_next = __shfl_down_sync(0xFFFFFFFFu, m, 1);
-        if (lane == 31) m_next = occupancy16(mine[1]);
+        if (lane == 31) m_next = beyond;
     }
     const uint32_t n = __popc(m);
     uint32_t incl = n;
@@ -289,9 +297,6 @@ __device__ __forceinline__ void grid_step(const RoadConst &rc, const int8_t *__r
     }
     const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
     if (total == 0) return;
-    uint32_t pos = incl - n;
-    for (uint32_t mm = m; mm; mm &= mm - 1u) list[pos++] = (uint16_t)(CPL * lane + (uint32_t)(__ffs(mm) - 1));
-    __syncwarp();
 
     // one car: rules 1-4 from its row index r and its owner lane's masks;
     // computed without branches (an idle lane computes a dummy car and does
@@ -299,18 +304,14 @@ __device__ __forceinline__ void grid_step(const RoadConst &rc, const int8_t *__r
     auto car = [&](bool active, uint32_t r, uint32_t wm, uint32_t wn) {
         const uint32_t bit = r & (CPL - 1u);
         const uint32_t src = CPL == 32 ? r >> 5 : r >> 4;
-        uint32_t after, known;
-        if (CPL == 32) {
-            after = __funnelshift_rc(wm, wn, bit + 1u);
-            known = src == 31u ? 47u - bit : 32u;
-        } else {
-            after = (wm | (wn << 16)) >> (bit + 1u);
-            known = 31u - bit;
-        }
-        uint32_t gap = after ? (uint32_t)(__ffs(after) - 1) : known;
+        const uint32_t after = CPL == 32 ? __funnelshift_rc(wm, wn, bit + 1u) : (wm | (wn << 16)) >> (bit + 1u);
+        // with vmax <= 16 the masks always cover the cells a gap can need
+        uint32_t gap = after ? (uint32_t)(__ffs(after) - 1) : 32u;
         const uint32_t idx = row0 + r;
         if (kWide && active) {
-            // past the cells the masks know, scan the bytes
+            // the masks know the next 32 cells (16 fewer for the row's last
+            // lane; 31 - bit with 16 cells per lane); past them, scan the bytes
+            uint32_t known = CPL == 32 ? (src == 31u ? 47u - bit : 32u) : 31u - bit;
             if (gap > known) gap = known;
             while (gap == known && gap < rc.vmax) {
                 if (cur[idx + 1u + gap] >= 0) break;
@@ -336,23 +337,36 @@ __device__ __forceinline__ void grid_step(const RoadConst &rc, const int8_t *__r
         }
     };
     constexpr uint32_t kShift = CPL == 32 ? 5u : 4u;
-    for (uint32_t first = 0; first < total; first += 64u) {
-        const uint32_t i0 = first + lane, i1 = i0 + 32u;
-        const bool a0 = i0 < total, a1 = i1 < total;
-        const uint32_t r0 = a0 ? (uint32_t)list[i0] : 0u;
-        const uint32_t wm0 = __shfl_sync(0xFFFFFFFFu, m, r0 >> kShift);
-        const uint32_t wn0 = __shfl_sync(0xFFFFFFFFu, m_next, r0 >> kShift);
-        if (first + 32u < total) {   // warp-uniform: a second car for (some) lanes
-            const uint32_t r1 = a1 ? (uint32_t)list[i1] : 0u;
-            const uint32_t wm1 = __shfl_sync(0xFFFFFFFFu, m, r1 >> kShift);
-            const uint32_t wn1 = __shfl_sync(0xFFFFFFFFu, m_next, r1 >> kShift);
-            car(a0, r0, wm0, wn0);
-            car(a1, r1, wm1, wn1);
-        } else {
-            car(a0, r0, wm0, wn0);
+    for (uint32_t chunk = 0; chunk < total; chunk += kListCap) {
+        // list the cars of ranks [chunk, chunk + kListCap) of the row
+        uint32_t pos = incl - n;
+        if (total <= kListCap) {   // warp-uniform: the whole row in one pass
+            for (uint32_t mm = m; mm; mm &= mm - 1u) list[pos++] = (uint16_t)(CPL * lane + (uint32_t)(__ffs(mm) - 1));
+        } else if (pos < chunk + kListCap && pos + n > chunk) {
+            for (uint32_t mm = m; mm; mm &= mm - 1u, ++pos)
+                if (pos >= chunk && pos < chunk + kListCap)
+                    list[pos - chunk] = (uint16_t)(CPL * lane + (uint32_t)(__ffs(mm) - 1));
         }
+        __syncwarp();
+        const uint32_t count = min(kListCap, total - chunk);
+        for (uint32_t first = 0; first < count; first += 64u) {
+            const uint32_t i0 = first + lane, i1 = i0 + 32u;
+            const bool a0 = i0 < count, a1 = i1 < count;
+            const uint32_t r0 = a0 ? (uint32_t)list[i0] : 0u;
+            const uint32_t wm0 = __shfl_sync(0xFFFFFFFFu, m, r0 >> kShift);
+            const uint32_t wn0 = __shfl_sync(0xFFFFFFFFu, m_next, r0 >> kShift);
+            if (first + 32u < count) {   // warp-uniform: a second car for (some) lanes
+                const uint32_t r1 = a1 ? (uint32_t)list[i1] : 0u;
+                const uint32_t wm1 = __shfl_sync(0xFFFFFFFFu, m, r1 >> kShift);
+                const uint32_t wn1 = __shfl_sync(0xFFFFFFFFu, m_next, r1 >> kShift);
+                car(a0, r0, wm0, wn0);
+                car(a1, r1, wm1, wn1);
+            } else {
+                car(a0, r0, wm0, wn0);
+            }
+        }
+        __syncwarp();   // the list is rewritten by the next pass or step
     }
-    __syncwarp();
 }
 
 // Whole ring in one block, agent form: thread t holds cars [t*R, t*R + R)
