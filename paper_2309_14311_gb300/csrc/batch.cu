@@ -74,7 +74,7 @@ void plan_road(const nasch_params &p, int64_t T, double rho_star, int k_agent, i
             k = p.k ? p.k : k_agent;
             rd.halo = round_up((uint32_t)k, (uint32_t)kBatchAgentR);
             rd.tile = kBatchAgentSpan - rd.halo;
-            const int64_t per_item = (int64_t)rd.tile * (kBatchThreads / 32);
+            const int64_t per_item = (int64_t)rd.tile * (kBatchThreads / 32) * kBatchWarpTilesPerWarp;
             *n_items = (p.N + per_item - 1) / per_item;
         }
     } else {
@@ -261,7 +261,7 @@ int nasch_submit(const nasch_params *roads, int64_t n_roads, const int64_t *step
         b->vehicle_steps += (int64_t)roads[i].N * steps[i];
         b->cell_steps += roads[i].L * steps[i];
     }
-    b->padded = (uint32_t)kGridSpan + 16u * ((max_vmax_grid + 15u) / 16u + 2u);
+    b->padded = (uint32_t)kGridSpan;   // ring buffers; grid tiles use the span-list method
     std::vector<int64_t> order((size_t)n_roads);
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(),

@@ -11,7 +11,7 @@ namespace nasch {
 
 // How one road of a batch is stepped.
 enum BatchType : uint32_t {
-    kBatchAgentTile = 0,   // agent layout, warp-tiles of 256 cars, 8 per item
+    kBatchAgentTile = 0,   // agent layout, warp-tiles of 256 cars, 16 per item (2 per warp)
     kBatchGridTile = 1,    // grid layout, one staged 8192-cell span per item
     kBatchAgentRing = 2,   // agent layout, N <= 2048: the whole ring in one item
     kBatchGridRing = 3,    // grid layout, L <= 8192: the whole ring in one item
@@ -22,6 +22,7 @@ constexpr int kBatchAgentR = 8;                                       // cars pe
 constexpr uint32_t kBatchAgentSpan = 32u * kBatchAgentR;              // cars per warp-tile
 constexpr uint32_t kBatchRingCars = kBatchThreads * kBatchAgentR;     // 2048
 constexpr uint32_t kBatchRingCells = (uint32_t)kGridSpan;             // 8192
+constexpr uint32_t kBatchWarpTilesPerWarp = 2;                        // agent warp-tiles per warp per item
 
 struct BatchRoadDev {
     uint32_t L, N, vmax, type;

@@ -4,9 +4,11 @@
 // One launch per super-step.  A persistent grid of 256-thread blocks pulls
 // items from the super-step's work-list with an atomic cursor; an item is a
 // piece of one road and runs that road's k fused steps:
-//   agent tile: 8 warp-tiles of 256 consecutive cars (32 lanes x 8 cars in
-//               registers, leader by warp shuffle, halo of round_up(k, 8));
-//   grid tile:  one staged 8192-cell span (tile + halos of round_up(k*vmax,16));
+//   agent tile: 16 warp-tiles of 256 consecutive cars, two per warp (32 lanes
+//               x 8 cars in registers, leader by warp shuffle, halo of
+//               round_up(k, 8));
+//   grid tile:  one staged 8192-cell span (tile + halos of round_up(k*vmax,16)),
+//               stepped as a list of its cars (the span-list method);
 //   agent ring: a whole ring of N <= 2048 cars in one block;
 //   grid ring:  a whole ring of L <= 8192 cells in shared memory.
 // The step code is the single-road kernels' (tile_device.cuh), so a road in
@@ -30,8 +32,6 @@ __device__ __forceinline__ void batch_agent_tile(const BatchRoadDev &rd, const R
 {
     const uint32_t warp = threadIdx.x >> 5;
     const uint32_t owned = rd.tile;
-    const uint32_t t0 = (item_tile * (uint32_t)(kBatchThreads / 32) + warp) * owned;
-    if (t0 >= rd.N) return;
     AgentStep a;
     a.status = nullptr;
     // select by branch, not by index, so the descriptor stays in registers
@@ -45,29 +45,30 @@ __device__ __forceinline__ void batch_agent_tile(const BatchRoadDev &rd, const R
     a.ksteps = kk;
     a.sum_v = nullptr;
     a.crossings = nullptr;
-    if (t0 + kBatchAgentSpan <= rd.N)
-        agent_warp_tile<kBatchAgentR, D, true>(a, t0, owned, s_sum, s_cross);
-    else
-        agent_warp_tile<kBatchAgentR, D, false>(a, t0, owned, s_sum, s_cross);
+    // this warp's consecutive warp-tiles of the item
+    for (uint32_t w2 = 0; w2 < kBatchWarpTilesPerWarp; ++w2) {
+        const uint32_t t0 = ((item_tile * (uint32_t)(kBatchThreads / 32) + warp) * kBatchWarpTilesPerWarp + w2) * owned;
+        if (t0 >= rd.N) return;
+        if (t0 + kBatchAgentSpan <= rd.N)
+            agent_warp_tile<kBatchAgentR, D, true>(a, t0, owned, s_sum, s_cross);
+        else
+            agent_warp_tile<kBatchAgentR, D, false>(a, t0, owned, s_sum, s_cross);
+    }
 }
 
-template <Draw D, bool kWide>
+template <Draw D>
 __device__ __forceinline__ void batch_grid_tile(const BatchRoadDev &rd, const RoadConst &rc, uint32_t item_tile,
-                                                uint32_t par, uint32_t step0, int kk, uint32_t padded, int8_t *pool,
-                                                uint16_t (*s_list)[1024], unsigned long long *s_sum,
+                                                uint32_t par, uint32_t step0, int kk, int8_t *pool, uint32_t *s_first,
+                                                uint32_t *s_count, unsigned long long *s_sum,
                                                 unsigned long long *s_cross)
 {
-    const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+    const uint32_t tid = threadIdx.x;
     const uint32_t L = rd.L, H = rd.halo, C = rd.tile;
     const uint32_t W = (uint32_t)kGridSpan;
-    GridTileGeom geo;
-    geo.halo = H;
-    geo.tile = C;
-    geo.padded = padded;
-    geo.n_tiles = 0;
-    geo.nwork = 3;
     int8_t *stage = pool;
-    auto work = [&](uint32_t b) { return pool + (1u + b) * padded; };
+    int8_t *out = pool + W;
+    uint16_t *s_pos = reinterpret_cast<uint16_t *>(pool + 2u * W);
+    uint8_t *s_vel = reinterpret_cast<uint8_t *>(s_pos + W);
     const int8_t *c_in = par ? rd.cells[1] : rd.cells[0];
     int8_t *c_out = par ? rd.cells[0] : rd.cells[1];
     const uint32_t t0 = item_tile * C;
@@ -84,51 +85,31 @@ __device__ __forceinline__ void batch_grid_tile(const BatchRoadDev &rd, const Ro
             stage[i] = c_in[cell];
         }
     }
-    for (uint32_t c = W / 16u + tid; c < padded / 16u; c += kBatchThreads) reinterpret_cast<uint4 *>(stage)[c] = kEmpty4;
-    for (uint32_t c = tid; c < padded / 16u; c += kBatchThreads) reinterpret_cast<uint4 *>(work(0))[c] = kEmpty4;
     __syncthreads();
-
-    const int8_t *cur = stage;
-    for (int s = 0; s < kk; ++s) {
-        const uint32_t o = (uint32_t)s % 3u;
-        int8_t *nxt = work(o);
-        int8_t *clr = work(o == 2u ? 0u : o + 1u);
-        uint32_t tsum = 0, tcross = 0;
-        grid_step<D, kWide, 32>(rc, cur, nxt, clr, geo, own_cells, base, step0 + (uint32_t)s, s_list[warp], tsum,
-                                    tcross);
-        tsum = __reduce_add_sync(0xFFFFFFFFu, tsum);
-        tcross = __reduce_add_sync(0xFFFFFFFFu, tcross);
-        if (lane == 0 && (tsum | tcross)) {
-            atomicAdd(&s_sum[s], (unsigned long long)tsum);
-            atomicAdd(&s_cross[s], (unsigned long long)tcross);
-        }
-        __syncthreads();
-        cur = nxt;
-    }
+    grid_span_steps<D>(rc, stage, out, H, own_cells, base, step0, kk, s_pos, s_vel, W, s_first, s_count, s_sum,
+                       s_cross);
+    __syncthreads();
     if (own_cells == C) {
-        const uint4 *f4 = reinterpret_cast<const uint4 *>(cur + H);
+        const uint4 *f4 = reinterpret_cast<const uint4 *>(out + H);
         uint4 *dst = reinterpret_cast<uint4 *>(c_out + t0);
         for (uint32_t c = tid; c < C / 16u; c += kBatchThreads) dst[c] = f4[c];
     } else {
-        for (uint32_t i = tid; i < own_cells; i += kBatchThreads) c_out[t0 + i] = cur[H + i];
+        for (uint32_t i = tid; i < own_cells; i += kBatchThreads) c_out[t0 + i] = out[H + i];
     }
 }
 
 template <Draw D>
 __device__ __forceinline__ void batch_item(const BatchRoadDev &rd, const RoadConst &rc, uint32_t item_tile,
                                            uint32_t par, uint32_t step0, int kk, uint32_t padded, int8_t *pool,
-                                           uint16_t (*s_list)[1024], uint32_t *s_first, uint32_t *s_psum,
-                                           uint32_t *s_pcross, unsigned long long *s_sum, unsigned long long *s_cross)
+                                           uint32_t *s_first, uint32_t *s_count, uint32_t *s_psum, uint32_t *s_pcross,
+                                           unsigned long long *s_sum, unsigned long long *s_cross)
 {
     switch (rd.type) {
     case kBatchAgentTile:
         batch_agent_tile<D>(rd, rc, item_tile, par, step0, kk, s_sum, s_cross);
         break;
     case kBatchGridTile:
-        if (rd.vmax > 16u)
-            batch_grid_tile<D, true>(rd, rc, item_tile, par, step0, kk, padded, pool, s_list, s_sum, s_cross);
-        else
-            batch_grid_tile<D, false>(rd, rc, item_tile, par, step0, kk, padded, pool, s_list, s_sum, s_cross);
+        batch_grid_tile<D>(rd, rc, item_tile, par, step0, kk, pool, s_first, s_count, s_sum, s_cross);
         break;
     case kBatchAgentRing:
         agent_ring_steps<kBatchAgentR>(par ? rd.x[1] : rd.x[0], par ? rd.v[1] : rd.v[0], par ? rd.x[0] : rd.x[1],
@@ -145,8 +126,8 @@ __device__ __forceinline__ void batch_item(const BatchRoadDev &rd, const RoadCon
 __global__ void __launch_bounds__(kBatchThreads, 3) batch_kernel(const BatchLaunch bl)
 {
     extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ uint16_t s_list[kBatchThreads / 32][1024];
     __shared__ uint32_t s_first[2 * kBatchThreads];
+    __shared__ uint32_t s_count[kBatchThreads / 32 + 1];
     __shared__ uint32_t s_psum[2 * 32];
     __shared__ uint32_t s_pcross[2 * 32];
     __shared__ unsigned long long s_sum[kMaxFusedSteps];
@@ -188,15 +169,15 @@ __global__ void __launch_bounds__(kBatchThreads, 3) batch_kernel(const BatchLaun
         if (kk == 0) continue;   // uniform across the block; the loop head synchronises again
         switch (draw_mode(rd.thr)) {
         case Draw::kNever:
-            batch_item<Draw::kNever>(rd, rc, it.tile, par, step0, kk, bl.padded, pool, s_list, s_first, s_psum,
+            batch_item<Draw::kNever>(rd, rc, it.tile, par, step0, kk, bl.padded, pool, s_first, s_count, s_psum,
                                      s_pcross, s_sum, s_cross);
             break;
         case Draw::kAlways:
-            batch_item<Draw::kAlways>(rd, rc, it.tile, par, step0, kk, bl.padded, pool, s_list, s_first, s_psum,
+            batch_item<Draw::kAlways>(rd, rc, it.tile, par, step0, kk, bl.padded, pool, s_first, s_count, s_psum,
                                       s_pcross, s_sum, s_cross);
             break;
         default:
-            batch_item<Draw::kPhilox>(rd, rc, it.tile, par, step0, kk, bl.padded, pool, s_list, s_first, s_psum,
+            batch_item<Draw::kPhilox>(rd, rc, it.tile, par, step0, kk, bl.padded, pool, s_first, s_count, s_psum,
                                       s_pcross, s_sum, s_cross);
             break;
         }
@@ -306,7 +287,13 @@ __global__ void __launch_bounds__(256) batch_floyd_expand_kernel(const BatchRoad
 
 }  // namespace
 
-size_t batch_smem_bytes(uint32_t padded) { return 4u * (size_t)padded; }   // stage + three output buffers
+// grid tiles: staged span, output span, car list (uint16 position + uint8
+// velocity per cell of the span); grid rings: two ring buffers of <= 8192
+size_t batch_smem_bytes(uint32_t padded)
+{
+    (void)padded;
+    return 5u * (size_t)kGridSpan;
+}
 
 int batch_blocks_per_sm(uint32_t padded)
 {

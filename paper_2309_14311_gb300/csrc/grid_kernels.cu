@@ -29,19 +29,128 @@ namespace nasch {
 namespace {
 
 constexpr uint32_t kGridWarps = (uint32_t)kGridThreads / 32u;
-constexpr uint32_t kGridRow = 32u * kGridCellsPerLane;
-static_assert(kGridWarps * kGridRow == (uint32_t)kGridSpan, "one row per warp");
-constexpr uint32_t kGridStages = 2;      // spans in flight per block: the current one and one prefetched
-constexpr uint32_t kGridListCap = 512;   // cars per list pass (a row holds up to 1024)
+constexpr uint32_t kGridStages = 2;   // spans in flight per block: the current one and one prefetched
+constexpr uint32_t kGridListCap = (uint32_t)kGridSpan;   // every span's cars fit the list
 
-template <Draw D, bool kWide>
+template <Draw D>
 __global__ void __launch_bounds__(kGridThreads) grid_tiled_kernel(const GridStep g, const GridTileGeom geo)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t s_full[kGridStages];
     __shared__ unsigned long long s_sum[kMaxFusedSteps];
     __shared__ unsigned long long s_cross[kMaxFusedSteps];
-    __shared__ uint16_t s_list[kGridWarps][kGridListCap];
+    __shared__ uint32_t s_first[2 * kGridThreads];
+    __shared__ uint32_t s_count[kGridWarps + 1];
+
+    const RoadConst rc = g.rc;
+    const uint32_t L = rc.L;
+    const uint32_t H = geo.halo;
+    const uint32_t C = geo.tile;
+    const uint32_t W = (uint32_t)kGridSpan;
+    const uint32_t WP = geo.padded;
+    const uint32_t tid = threadIdx.x;
+    int8_t *const pool = reinterpret_cast<int8_t *>(smem);
+    // stages 0, 1 (bulk-load targets), outputs 2, 3 (alternating by tile),
+    // then the car list: positions (uint16) and velocities
+    auto buf = [&](uint32_t b) { return pool + b * WP; };
+    uint16_t *const s_pos = reinterpret_cast<uint16_t *>(pool + 4u * WP);
+    uint8_t *const s_vel = reinterpret_cast<uint8_t *>(s_pos + kGridListCap);
+
+    for (int i = tid; i < g.ksteps; i += kGridThreads) {
+        s_sum[i] = 0ull;
+        s_cross[i] = 0ull;
+    }
+    if (tid == 0) {
+        for (uint32_t b = 0; b < kGridStages; ++b) mbar_init(&s_full[b], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    auto bulk_ok = [&](uint32_t tile) {
+        const uint32_t t0 = tile * C;
+        return t0 >= H && t0 + C + H <= L;
+    };
+    uint32_t parity = 0;   // bit b: phase parity of s_full[b]
+    uint32_t tile = blockIdx.x;
+    if (tid == 0 && tile < geo.n_tiles && bulk_ok(tile)) {
+        fence_proxy_async();
+        mbar_expect_tx(&s_full[0], W);
+        bulk_load(buf(0), g.c_in + (tile * C - H), W, &s_full[0]);
+    }
+    for (uint32_t it = 0; tile < geo.n_tiles; tile += gridDim.x, ++it) {
+        const uint32_t sb = it & 1u;
+        const uint32_t t0 = tile * C;
+        const uint32_t own_cells = min(C, L - t0);
+        const uint32_t base = t0 >= H ? t0 - H : t0 + L - H;   // road cell of buffer index 0
+        const uint32_t next = tile + gridDim.x;
+        if (tid == 0) {
+            // earlier bulk stores must have read their source before buffers are reused
+            bulk_wait_read_all();
+            if (next < geo.n_tiles && bulk_ok(next)) {
+                fence_proxy_async();
+                mbar_expect_tx(&s_full[sb ^ 1u], W);
+                bulk_load(buf(sb ^ 1u), g.c_in + (next * C - H), W, &s_full[sb ^ 1u]);
+            }
+        }
+        int8_t *in = buf(sb);
+        bool ok = true;
+        if (bulk_ok(tile)) {
+            // one thread waits for the span; the barrier below releases the
+            // others (waiting warps would otherwise take issue slots)
+            if (tid == 0) ok = mbar_wait_bounded(&s_full[sb], (parity >> sb) & 1u);
+            parity ^= 1u << sb;
+        } else {
+            for (uint32_t i = tid; i < W; i += kGridThreads) {
+                uint32_t cell = base + i;
+                if (cell >= L) cell -= L;
+                in[i] = g.c_in[cell];
+            }
+        }
+        if (!__syncthreads_and(ok)) {
+            if (tid == 0) {
+                atomicOr(g.status, kStatusTimeout);
+                if (next < geo.n_tiles && bulk_ok(next)) mbar_wait_bounded(&s_full[sb ^ 1u], (parity >> (sb ^ 1u)) & 1u);
+                bulk_wait_all();
+            }
+            return;
+        }
+        int8_t *out = buf(2u + sb);
+        grid_span_steps<D>(rc, in, out, H, own_cells, base, g.step0, g.ksteps, s_pos, s_vel, kGridListCap, s_first,
+                           s_count, s_sum, s_cross);
+        fence_proxy_async();   // the result leaves by bulk store
+        __syncthreads();
+        if (own_cells == C) {
+            if (tid == 0) {
+                bulk_store(g.c_out + t0, out + H, C);
+                bulk_commit();
+            }
+        } else {
+            for (uint32_t i = tid; i < own_cells; i += kGridThreads) g.c_out[t0 + i] = out[H + i];
+        }
+    }
+    if (tid == 0) bulk_wait_all();
+    __syncthreads();
+    for (int i = tid; i < g.ksteps; i += kGridThreads) {
+        if (s_sum[i]) atomicAdd(&g.sum_v[i], s_sum[i]);
+        if (s_cross[i]) atomicAdd(&g.crossings[i], s_cross[i]);
+    }
+}
+
+// k = 1: the mask-step kernel.  One step per tile does not repay turning the
+// span into a list, so each warp steps its 1024-cell row directly from the
+// occupancy masks (grid_step): two staged spans, two work buffers rotating
+// with the stage, car lists of up to 512 entries per warp.
+constexpr uint32_t kMaskStages = 2;
+constexpr uint32_t kMaskListCap = 512;
+
+template <Draw D, bool kWide>
+__global__ void __launch_bounds__(kGridThreads) grid_mask_kernel(const GridStep g, const GridTileGeom geo)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t s_full[kMaskStages];
+    __shared__ unsigned long long s_sum[kMaxFusedSteps];
+    __shared__ unsigned long long s_cross[kMaxFusedSteps];
+    __shared__ uint16_t s_list[kGridWarps][kMaskListCap];
 
     const RoadConst rc = g.rc;
     const uint32_t L = rc.L;
@@ -61,14 +170,14 @@ __global__ void __launch_bounds__(kGridThreads) grid_tiled_kernel(const GridStep
         s_cross[i] = 0ull;
     }
     if (tid == 0) {
-        for (uint32_t b = 0; b < kGridStages; ++b) mbar_init(&s_full[b], 1);
+        for (uint32_t b = 0; b < kMaskStages; ++b) mbar_init(&s_full[b], 1);
         fence_mbar_init();
     }
     // stage padding (never written by the loads) and both work buffers start empty
-    for (uint32_t b = 0; b < kGridStages; ++b)
+    for (uint32_t b = 0; b < kMaskStages; ++b)
         for (uint32_t c = W / 16u + tid; c < WP / 16u; c += kGridThreads) reinterpret_cast<uint4 *>(buf(b))[c] = kEmpty4;
     for (uint32_t c = tid; c < 2u * WP / 16u; c += kGridThreads)
-        reinterpret_cast<uint4 *>(buf(kGridStages))[c] = kEmpty4;
+        reinterpret_cast<uint4 *>(buf(kMaskStages))[c] = kEmpty4;
     __syncthreads();
 
     auto bulk_ok = [&](uint32_t tile) {
@@ -76,11 +185,11 @@ __global__ void __launch_bounds__(kGridThreads) grid_tiled_kernel(const GridStep
         return t0 >= H && t0 + C + H <= L;
     };
     uint32_t parity = 0;                  // bit b: phase parity of s_full[b]
-    int clean = (int)kGridStages;         // a work buffer known to be all -1, or -1 if none
+    int clean = (int)kMaskStages;         // a work buffer known to be all -1, or -1 if none
     uint32_t tile = blockIdx.x;
     if (tid == 0) {
         // the first two spans of this block
-        for (uint32_t b = 0; b + 1 < kGridStages; ++b) {
+        for (uint32_t b = 0; b + 1 < kMaskStages; ++b) {
             const uint32_t t = tile + b * gridDim.x;
             if (t < geo.n_tiles && bulk_ok(t)) {
                 fence_proxy_async();
@@ -90,12 +199,12 @@ __global__ void __launch_bounds__(kGridThreads) grid_tiled_kernel(const GridStep
         }
     }
     for (uint32_t it = 0; tile < geo.n_tiles; tile += gridDim.x, ++it) {
-        const uint32_t sb = it % kGridStages;
+        const uint32_t sb = it % kMaskStages;
         const uint32_t t0 = tile * C;
         const uint32_t own_cells = min(C, L - t0);
         const uint32_t base = t0 >= H ? t0 - H : t0 + L - H;   // road cell of buffer index 0
-        const uint32_t ahead = tile + (kGridStages - 1u) * gridDim.x;
-        const uint32_t ab = (it + kGridStages - 1u) % kGridStages;   // its stage: the one tile it-1 used
+        const uint32_t ahead = tile + (kMaskStages - 1u) * gridDim.x;
+        const uint32_t ab = (it + kMaskStages - 1u) % kMaskStages;   // its stage: the one tile it-1 used
         if (tid == 0) {
             // earlier bulk stores must have read their source before buffers are reused
             bulk_wait_read_all();
@@ -123,8 +232,8 @@ __global__ void __launch_bounds__(kGridThreads) grid_tiled_kernel(const GridStep
             if (tid == 0) {
                 atomicOr(g.status, kStatusTimeout);
                 // let the loads still in flight land before the block's memory goes
-                for (uint32_t d = 1; d < kGridStages; ++d) {
-                    const uint32_t t = tile + d * gridDim.x, b = (it + d) % kGridStages;
+                for (uint32_t d = 1; d < kMaskStages; ++d) {
+                    const uint32_t t = tile + d * gridDim.x, b = (it + d) % kMaskStages;
                     if (t < geo.n_tiles && bulk_ok(t)) mbar_wait_bounded(&s_full[b], (parity >> b) & 1u);
                 }
                 bulk_wait_all();
@@ -132,8 +241,8 @@ __global__ void __launch_bounds__(kGridThreads) grid_tiled_kernel(const GridStep
             return;
         }
         // rotation (stage, wa, wb); step 0 writes wa, which must be empty
-        const uint32_t wa = clean >= 0 ? (uint32_t)clean : kGridStages;
-        const uint32_t wb = wa == kGridStages ? kGridStages + 1u : kGridStages;
+        const uint32_t wa = clean >= 0 ? (uint32_t)clean : kMaskStages;
+        const uint32_t wb = wa == kMaskStages ? kMaskStages + 1u : kMaskStages;
         if (clean < 0) {
             for (uint32_t c = tid; c < WP / 16u; c += kGridThreads) reinterpret_cast<uint4 *>(buf(wa))[c] = kEmpty4;
             __syncthreads();
@@ -145,7 +254,7 @@ __global__ void __launch_bounds__(kGridThreads) grid_tiled_kernel(const GridStep
             const uint32_t i1 = i0 == 2u ? 0u : i0 + 1u;
             const uint32_t i2 = i1 == 2u ? 0u : i1 + 1u;
             uint32_t tsum = 0, tcross = 0;
-            grid_step<D, kWide, kGridCellsPerLane, kGridListCap>(rc, buf(rot(i0)), buf(rot(i1)), buf(rot(i2)), geo,
+            grid_step<D, kWide, kGridCellsPerLane, kMaskListCap>(rc, buf(rot(i0)), buf(rot(i1)), buf(rot(i2)), geo,
                                                                  own_cells, base, g.step0 + (uint32_t)s, s_list[warp],
                                                                  tsum, tcross);
             tsum = __reduce_add_sync(0xFFFFFFFFu, tsum);
@@ -162,7 +271,7 @@ __global__ void __launch_bounds__(kGridThreads) grid_tiled_kernel(const GridStep
         const uint32_t k3 = (uint32_t)g.ksteps % 3u;
         const int8_t *fin = buf(rot(k3));
         const uint32_t cleared = rot(k3 == 2u ? 0u : k3 + 1u);   // cleared during the last step
-        clean = cleared >= kGridStages ? (int)cleared : -1;
+        clean = cleared >= kMaskStages ? (int)cleared : -1;
 
         if (own_cells == C) {
             if (tid == 0) {
@@ -199,50 +308,66 @@ GridTileGeom make_geom(int ksteps, uint32_t vmax, uint32_t L)
     GridTileGeom geo;
     geo.halo = grid_halo(ksteps, vmax);
     geo.tile = (uint32_t)kGridSpan - 2u * geo.halo;
-    // room past the span for the last lane's look-ahead, wide-vmax byte scans
-    // and cars scattered up to vmax cells beyond it
-    geo.padded = (uint32_t)kGridSpan + 16u * ((vmax + 15u) / 16u + 2u);
+    geo.padded = (uint32_t)kGridSpan;   // the span method never reads or writes past the span
     geo.n_tiles = (L + geo.tile - 1u) / geo.tile;
     geo.nwork = 2;
     return geo;
 }
 
-// three stage buffers and two work buffers
-size_t grid_tiled_smem(const GridTileGeom &geo) { return (kGridStages + 2u) * (size_t)geo.padded; }
+// two stages, two outputs, and the car list (uint16 position + uint8 velocity)
+size_t grid_tiled_smem(const GridTileGeom &geo) { return 4u * (size_t)geo.padded + 3u * (size_t)kGridListCap; }
 
-// Static plus dynamic shared memory exceeds the default 48 KB, so the
-// dynamic size is allowed explicitly (a per-device function attribute).
-template <Draw D, bool kWide>
-cudaError_t launch_grid_variant(const GridStep &g, const GridTileGeom &geo, int grid, size_t smem, cudaStream_t s)
+// the mask-step kernel reads past the span (look-ahead) and scatters up to
+// vmax cells past it: padded buffers, two stages and two work buffers
+GridTileGeom make_mask_geom(uint32_t vmax, uint32_t L)
 {
-    cudaError_t e = cudaFuncSetAttribute(grid_tiled_kernel<D, kWide>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    GridTileGeom geo = make_geom(1, vmax, L);
+    geo.padded = (uint32_t)kGridSpan + 16u * ((vmax + 15u) / 16u + 2u);
+    return geo;
+}
+size_t grid_mask_smem(const GridTileGeom &geo) { return 4u * (size_t)geo.padded; }
+
+template <Draw D, bool kWide>
+cudaError_t launch_mask_variant(const GridStep &g, const GridTileGeom &geo, int grid, size_t smem, cudaStream_t s)
+{
+    cudaError_t e = cudaFuncSetAttribute(grid_mask_kernel<D, kWide>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    grid_tiled_kernel<D, kWide><<<grid, kGridThreads, smem, s>>>(g, geo);
+    grid_mask_kernel<D, kWide><<<grid, kGridThreads, smem, s>>>(g, geo);
     return cudaGetLastError();
 }
 
 template <bool kWide>
-cudaError_t launch_grid_draw(const GridStep &g, const GridTileGeom &geo, int grid, size_t smem, cudaStream_t s)
+cudaError_t launch_mask_draw(const GridStep &g, const GridTileGeom &geo, int grid, size_t smem, cudaStream_t s)
 {
-    if (g.rc.thr == 0) return launch_grid_variant<Draw::kNever, kWide>(g, geo, grid, smem, s);
-    if (g.rc.thr > 0xFFFFFFFFull) return launch_grid_variant<Draw::kAlways, kWide>(g, geo, grid, smem, s);
-    return launch_grid_variant<Draw::kPhilox, kWide>(g, geo, grid, smem, s);
+    if (g.rc.thr == 0) return launch_mask_variant<Draw::kNever, kWide>(g, geo, grid, smem, s);
+    if (g.rc.thr > 0xFFFFFFFFull) return launch_mask_variant<Draw::kAlways, kWide>(g, geo, grid, smem, s);
+    return launch_mask_variant<Draw::kPhilox, kWide>(g, geo, grid, smem, s);
+}
+
+// Static plus dynamic shared memory exceeds the default 48 KB, so the
+// dynamic size is allowed explicitly (a per-device function attribute).
+template <Draw D>
+cudaError_t launch_grid_variant(const GridStep &g, const GridTileGeom &geo, int grid, size_t smem, cudaStream_t s)
+{
+    cudaError_t e = cudaFuncSetAttribute(grid_tiled_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    grid_tiled_kernel<D><<<grid, kGridThreads, smem, s>>>(g, geo);
+    return cudaGetLastError();
 }
 
 }  // namespace
 
 int grid_tiled_blocks_per_sm()
 {
-    // the common case: k = 1, vmax = 5
     const GridTileGeom geo = make_geom(1, 5, 1u << 20);
     const size_t smem = grid_tiled_smem(geo);
-    if (cudaFuncSetAttribute(grid_tiled_kernel<Draw::kPhilox, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess)
+    if (cudaFuncSetAttribute(grid_tiled_kernel<Draw::kPhilox>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
         return 1;
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, grid_tiled_kernel<Draw::kPhilox, false>, kGridThreads,
-                                                      smem) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, grid_tiled_kernel<Draw::kPhilox>, kGridThreads, smem) !=
+        cudaSuccess)
         return 1;
     return n > 0 ? n : 1;
 }
@@ -254,10 +379,19 @@ cudaError_t launch_grid_tiled(const GridStep &g, int blocks, cudaStream_t s)
     const GridTileGeom geo = make_geom(g.ksteps, g.rc.vmax, g.rc.L);
     // the tile must own cells, and the staged span must not wrap the ring twice
     if (2u * geo.halo >= (uint32_t)kGridSpan || g.rc.L < (uint32_t)kGridSpan) return cudaErrorInvalidValue;
+    if (g.ksteps == 1) {
+        const GridTileGeom mg = make_mask_geom(g.rc.vmax, g.rc.L);
+        const size_t msmem = grid_mask_smem(mg);
+        const int mblocks = blocks * 5 / 3;   // the mask kernel fits 5 blocks per SM where the list kernel fits 3
+        const int grid = (int)((uint32_t)mblocks < mg.n_tiles ? (uint32_t)mblocks : mg.n_tiles);
+        return g.rc.vmax > 16u ? launch_mask_draw<true>(g, mg, grid, msmem, s)
+                               : launch_mask_draw<false>(g, mg, grid, msmem, s);
+    }
     const size_t smem = grid_tiled_smem(geo);
     const int grid = (int)((uint32_t)blocks < geo.n_tiles ? (uint32_t)blocks : geo.n_tiles);
-    return g.rc.vmax > 16u ? launch_grid_draw<true>(g, geo, grid, smem, s)
-                           : launch_grid_draw<false>(g, geo, grid, smem, s);
+    if (g.rc.thr == 0) return launch_grid_variant<Draw::kNever>(g, geo, grid, smem, s);
+    if (g.rc.thr > 0xFFFFFFFFull) return launch_grid_variant<Draw::kAlways>(g, geo, grid, smem, s);
+    return launch_grid_variant<Draw::kPhilox>(g, geo, grid, smem, s);
 }
 
 cudaError_t launch_grid_ring(const GridStep &g, cudaStream_t s)

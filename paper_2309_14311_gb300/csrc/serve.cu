@@ -497,7 +497,7 @@ int nasch_server_create(const nasch_server_config *cfg, nasch_server *out)
         s->own_stream = true;
     }
     s->max_slots = cfg->max_resident;
-    s->padded = (uint32_t)kGridSpan + 16u * ((127u + 15u) / 16u + 2u);   // any vmax
+    s->padded = (uint32_t)kGridSpan;
     e = cudaMalloc(&s->slab, (size_t)cfg->memory_budget);
     if (e == cudaSuccess) e = cudaMalloc(&s->d_slots, sizeof(BatchRoadDev) * (size_t)s->max_slots);
     for (int i = 0; i < 2 && e == cudaSuccess; ++i)

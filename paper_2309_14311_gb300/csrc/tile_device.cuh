@@ -319,8 +319,8 @@ __device__ __forceinline__ void grid_step(const RoadConst &rc, const int8_t *__r
                 ++known;
             }
         }
-        uint32_t cell = base + idx;
-        if (cell >= L) cell -= L;
+        const uint32_t c = base + idx;
+        const uint32_t cell = min(c, c - L);   // c mod L, as c < 2L (c - L wraps above c when c < L)
         uint32_t vel = min(min((uint32_t)(uint8_t)cur[idx] + 1u, rc.vmax), gap);   // rules 1, 2
         if (D == Draw::kAlways) {
             vel -= vel > 0u ? 1u : 0u;                                              // rule 3, p = 1
@@ -328,13 +328,12 @@ __device__ __forceinline__ void grid_step(const RoadConst &rc, const int8_t *__r
             const uint32_t u = philox_word0(cell, step, rc.road, kTagSlowdown, rc.key0, rc.key1);
             vel -= (vel > 0u && u < (uint32_t)rc.thr) ? 1u : 0u;                    // rule 3
         }
-        if (active) {
-            nxt[idx + vel] = (int8_t)vel;                                           // rule 4
-            if (idx - H < own_cells) {
-                tsum += vel;
-                tcross += (cell + vel >= L) ? 1u : 0u;
-            }
-        }
+        // predicated, not branched: nested divergent branches cost more than
+        // the few instructions they guard
+        if (active) nxt[idx + vel] = (int8_t)vel;                                   // rule 4
+        const bool own = active && idx - H < own_cells;
+        tsum += own ? vel : 0u;
+        tcross += (own && cell + vel >= L) ? 1u : 0u;
     };
     constexpr uint32_t kShift = CPL == 32 ? 5u : 4u;
     for (uint32_t chunk = 0; chunk < total; chunk += kListCap) {
@@ -367,6 +366,117 @@ __device__ __forceinline__ void grid_step(const RoadConst &rc, const int8_t *__r
         }
         __syncwarp();   // the list is rewritten by the next pass or step
     }
+}
+
+// The span-list method of a grid tile (used when the staged span's cars fit
+// the list): the cars of the staged span `in` become a list sorted by
+// position (cell index within the span, velocity); k synchronous steps are
+// applied to the list as in the agent form - a car's leader is the next
+// entry, and the last car, whose leader is beyond the span, sees at least
+// vmax empty cells; then the list is scattered into `out`, which must be all
+// -1.  Only cars within k*vmax cells of the span's ends can be wrong (the
+// same light cone as the cell-by-cell step), so the middle C cells are
+// exact.  Threads own consecutive runs of the list; each step a thread
+// publishes its first car's position, and after one barrier updates its cars
+// in ascending order in place (car j reads car j+1 before car j+1 moves).
+// Shared scratch: s_pos[cap], s_vel[cap], s_first[2 * blockDim.x],
+// s_count[warps + 1].  Returns false (doing nothing) if the cars exceed cap.
+template <Draw D>
+__device__ __forceinline__ bool grid_span_steps(const RoadConst &rc, const int8_t *__restrict__ in, int8_t *out,
+                                                uint32_t H, uint32_t own_cells, uint32_t base, uint32_t step0,
+                                                int ksteps, uint16_t *s_pos, uint8_t *s_vel, uint32_t cap,
+                                                uint32_t *s_first, uint32_t *s_count, unsigned long long *s_sum,
+                                                unsigned long long *s_cross)
+{
+    const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+    const uint32_t nthreads = blockDim.x, nwarps = nthreads >> 5;
+    const uint32_t L = rc.L;
+    const uint32_t W = (uint32_t)kGridSpan;
+    const uint32_t cells_per_thread = W / nthreads;   // 32 (256 threads)
+    // 1. cars of this thread's cells -> list ranks
+    const uint32_t c0 = tid * cells_per_thread;
+    uint32_t m = 0;
+    for (uint32_t q = 0; q < cells_per_thread / 16u; ++q)
+        m |= occupancy16(reinterpret_cast<const uint4 *>(in + c0)[q]) << (16u * q);
+    const uint32_t n = __popc(m);
+    uint32_t incl = n;
+#pragma unroll
+    for (uint32_t d = 1; d < 32; d <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+        if (lane >= d) incl += t;
+    }
+    if (lane == 31) s_count[warp] = incl;
+    __syncthreads();
+    if (tid == 0) {
+        uint32_t acc = 0;
+        for (uint32_t w = 0; w < nwarps; ++w) {
+            const uint32_t t = s_count[w];
+            s_count[w] = acc;
+            acc += t;
+        }
+        s_count[nwarps] = acc;
+    }
+    __syncthreads();
+    const uint32_t count = s_count[nwarps];
+    if (count > cap) return false;   // uniform: every thread reads the same total
+    uint32_t pos = s_count[warp] + incl - n;
+    for (uint32_t mm = m; mm; mm &= mm - 1u, ++pos) {
+        const uint32_t cell = c0 + (uint32_t)(__ffs(mm) - 1);
+        s_pos[pos] = (uint16_t)cell;
+        s_vel[pos] = (uint8_t)in[cell];
+    }
+    // the output starts empty (its previous contents were stored before this
+    // tile's first barrier)
+    for (uint32_t c = tid; c < W / 16u; c += nthreads) reinterpret_cast<uint4 *>(out)[c] = kEmpty4;
+    // 2. k steps on the list; thread t owns list entries [t*per, (t+1)*per)
+    const uint32_t per = (count + nthreads - 1u) / nthreads;
+    const uint32_t j0 = min(tid * per, count), j1 = min(j0 + per, count);
+    const uint32_t far = 0xFFFFu + 1u + rc.vmax;   // no leader within reach
+    __syncthreads();   // the list is complete
+    for (int s = 0; s < ksteps; ++s) {
+        const uint32_t ph = (uint32_t)s & 1u;
+        // publish this thread's first car (start of step); two slots by step
+        // parity, so a fast thread cannot overwrite one still being read
+        s_first[ph * nthreads + tid] = j0 < j1 ? (uint32_t)s_pos[j0] : far;
+        __syncthreads();
+        // leader of this thread's last car: the next thread's first car
+        const uint32_t lead_last = j1 < count ? s_first[ph * nthreads + tid + 1u] : far;
+        const uint32_t step = step0 + (uint32_t)s;
+        uint32_t tsum = 0, tcross = 0;
+        for (uint32_t j = j0; j < j1; ++j) {
+            const uint32_t x = s_pos[j];
+            const uint32_t lead = j + 1u < j1 ? (uint32_t)s_pos[j + 1u] : lead_last;
+            const uint32_t gap = lead - x - 1u;                           // >= vmax when far
+            uint32_t vel = min(min((uint32_t)s_vel[j] + 1u, rc.vmax), gap);   // rules 1, 2
+            const uint32_t c = base + x;
+            uint32_t cell = c >= L ? c - L : c;
+            cell = cell >= L ? cell - L : cell;
+            if (D == Draw::kAlways) {
+                vel -= vel > 0u ? 1u : 0u;                                   // rule 3, p = 1
+            } else if (D == Draw::kPhilox) {
+                const uint32_t u = philox_word0(cell, step, rc.road, kTagSlowdown, rc.key0, rc.key1);
+                vel -= (vel > 0u && u < (uint32_t)rc.thr) ? 1u : 0u;         // rule 3
+            }
+            s_pos[j] = (uint16_t)(x + vel);                                  // rule 4
+            s_vel[j] = (uint8_t)vel;
+            const bool own = x - H < own_cells;
+            tsum += own ? vel : 0u;
+            tcross += (own && cell + vel >= L) ? 1u : 0u;
+        }
+        tsum = __reduce_add_sync(0xFFFFFFFFu, tsum);
+        tcross = __reduce_add_sync(0xFFFFFFFFu, tcross);
+        if (lane == 0 && (tsum | tcross)) {
+            atomicAdd(&s_sum[s], (unsigned long long)tsum);
+            atomicAdd(&s_cross[s], (unsigned long long)tcross);
+        }
+    }
+    // 3. scatter into the empty output (cars that left the span are dropped);
+    // a thread's own entries need no barrier, the output's clear had one
+    for (uint32_t j = j0; j < j1; ++j) {
+        const uint32_t x = s_pos[j];
+        if (x < W) out[x] = (int8_t)s_vel[j];
+    }
+    return true;
 }
 
 // Whole ring in one block, agent form: thread t holds cars [t*R, t*R + R)
