@@ -319,8 +319,8 @@ __device__ __forceinline__ void grid_step(const RoadConst &rc, const int8_t *__r
                 ++known;
             }
         }
-        const uint32_t c = base + idx;
-        const uint32_t cell = min(c, c - L);   // c mod L, as c < 2L (c - L wraps above c when c < L)
+        uint32_t cell = base + idx;
+        if (cell >= L) cell -= L;
         uint32_t vel = min(min((uint32_t)(uint8_t)cur[idx] + 1u, rc.vmax), gap);   // rules 1, 2
         if (D == Draw::kAlways) {
             vel -= vel > 0u ? 1u : 0u;                                              // rule 3, p = 1
@@ -328,12 +328,13 @@ __device__ __forceinline__ void grid_step(const RoadConst &rc, const int8_t *__r
             const uint32_t u = philox_word0(cell, step, rc.road, kTagSlowdown, rc.key0, rc.key1);
             vel -= (vel > 0u && u < (uint32_t)rc.thr) ? 1u : 0u;                    // rule 3
         }
-        // predicated, not branched: nested divergent branches cost more than
-        // the few instructions they guard
-        if (active) nxt[idx + vel] = (int8_t)vel;                                   // rule 4
-        const bool own = active && idx - H < own_cells;
-        tsum += own ? vel : 0u;
-        tcross += (own && cell + vel >= L) ? 1u : 0u;
+        if (active) {
+            nxt[idx + vel] = (int8_t)vel;                                           // rule 4
+            if (idx - H < own_cells) {
+                tsum += vel;
+                tcross += (cell + vel >= L) ? 1u : 0u;
+            }
+        }
     };
     constexpr uint32_t kShift = CPL == 32 ? 5u : 4u;
     for (uint32_t chunk = 0; chunk < total; chunk += kListCap) {
