@@ -149,9 +149,18 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-# DRAM traffic per launch from an ncu capture of the dominant kernel, keyed by
-# the kernel source hash it was taken on (None until a capture exists).
-NCU_TRAFFIC: dict[str, dict] = {}
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
+# one ncu --set full capture of the small profiling case (bench.py --profile),
+# scaled to a launch of the large road by the units it processes (x4 cars for
+# the agent kernel, x8 cells for the grid kernel; the traffic of these
+# streaming kernels grows in proportion).  Keyed by the kernel source hash the
+# capture was taken on: a changed kernel reports null until it is re-captured.
+NCU_TRAFFIC: dict[str, dict] = {
+    "agent_tiled_k16": {"source_hash": "4dffaea02c8beb22", "captured_bytes": 167851776 + 122708736,
+                        "scale": 4, "bytes_per_launch": 4 * (167851776 + 122708736)},
+    "grid_tiled_k1": {"source_hash": "4dffaea02c8beb22", "captured_bytes": 268537088 + 221754624,
+                      "scale": 8, "bytes_per_launch": 8 * (268537088 + 221754624)},
+}
 
 
 def traffic_for(kernel: str):
@@ -495,7 +504,10 @@ def run_workload(args):
                          deterministic steady state min(vmax rho, 1 - rho);
     serve                the seed-11 request stream (first --serve-requests),
                          Poisson arrivals at --serve-load x capacity, 40 GB
-                         budget; p50/p99 latency and aggregate rate."""
+                         budget; p50/p99 latency and aggregate rate;
+    k-sweep              the large road (2^31 cells, 2^27 cars) in each
+                         layout at each fusion depth k of --sweep-k: rates
+                         over --other-steps steps after 2k warm-up steps."""
     import numpy as np
     import torch
 
@@ -504,7 +516,27 @@ def run_workload(args):
     NS.load(build_if_missing=True)
     stream = torch.cuda.Stream()
     out = {"workload": args.workload}
-    if args.workload == "ensemble":
+    if args.workload == "k-sweep":
+        s = WL.LARGE_ROAD
+        rows = []
+        for layout in ("agent", "grid"):
+            for k in [int(t) for t in args.sweep_k.split(",")]:
+                steps = max(args.other_steps // k, 1) * k
+                with NS.Road(s.L, s.N, s.vmax, s.p, s.seed, s.road_id, layout=layout, k=k, stream=stream) as r:
+                    r.run(2 * k)
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    r.run(steps)
+                    b.record(stream)
+                    b.synchronize()
+                    sec = a.elapsed_time(b) / 1e3
+                    k_used = r.info().k
+                rows.append({"layout": layout, "k": k, "k_used": int(k_used), "steps": steps,
+                             "vehicle_updates_per_s": s.N * steps / sec, "cell_updates_per_s": s.L * steps / sec,
+                             "algorithmic_gbs": (10 * s.N if layout == "agent" else 2 * s.L) * steps / k_used / sec
+                             / 1e9})
+        out.update(L=s.L, N=s.N, vmax=s.vmax, p=s.p, rows=rows)
+    elif args.workload == "ensemble":
         rows = WL.uneven_ensemble()
         if args.roads < len(rows):
             rng = np.random.default_rng(2309)
@@ -626,8 +658,9 @@ def main(argv=None):
     ap.add_argument("--cpu-steps", type=int, default=10)
     ap.add_argument("--ref-steps-per-step", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["large-road", "ensemble", "fundamental-diagram", "serve"],
+    ap.add_argument("--workload", choices=["large-road", "ensemble", "fundamental-diagram", "serve", "k-sweep"],
                     default="large-road", help="large-road is the benchmark line; the others print their own line")
+    ap.add_argument("--sweep-k", default="1,2,4,8,16,32", help="fusion depths of the k-sweep workload")
     ap.add_argument("--roads", type=int, default=4096)
     ap.add_argument("--plain-roads", type=int, default=256)
     ap.add_argument("--replicas", type=int, default=128)

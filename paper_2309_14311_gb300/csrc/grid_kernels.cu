@@ -292,6 +292,221 @@ __global__ void __launch_bounds__(kGridThreads) grid_mask_kernel(const GridStep 
     }
 }
 
+// k = 1 and vmax <= 16: the one-step kernel.  A span is the tile's C =
+// 8192 - 2H owned cells with H = 16 halo cells on each side (H = 0 when
+// vmax = 0).  Each warp steps one 1024-cell row: its lanes turn 32 cells
+// each into an occupancy mask, the cars of the row are listed (a prefix sum
+// of the lanes' car counts gives each lane its first slot), and the lanes
+// take the listed cars 32 or 64 at a time, so every lane draws for the same
+// number of cars.  A car's gap is the count of trailing zeros of the masks
+// after its cell (vmax <= 16 < 32 cells in view).  Cars in the right halo
+// are not stepped: they can only move further right, out of the tile.
+// Cars in the left halo are stepped (they may move into the tile) but not
+// counted in the statistics.  Results are scattered into an all -1 buffer,
+// which leaves by one bulk store; three result buffers rotate, so the one
+// being cleared was stored two tiles earlier.  The rule-3 draw uses the
+// counter-independent parts of Philox computed on the host (SlowdownKey).
+constexpr uint32_t kK1Stages = 2;       // staged spans: the tile being stepped and the next one loading
+constexpr uint32_t kK1Outs = 3;         // result buffers: scattered into, being stored, being cleared
+constexpr uint32_t kK1ListCap = 128;    // car-list entries per warp; a denser row is listed in several passes
+constexpr uint32_t kK1Row = 1024;       // cells per warp
+static_assert(kK1Row * kGridWarps == (uint32_t)kGridSpan, "one row per warp");
+
+// One car of a row: rules 1-4.  r: its cell within the row; occ / occ_next
+// of every lane are exchanged by shuffles, so all 32 lanes call this
+// together (an inactive lane computes a dummy car and stores nothing).
+template <Draw D>
+__device__ __forceinline__ void k1_car(bool active, uint32_t r, uint32_t occ, uint32_t occ_next,
+                                       const int8_t *__restrict__ in, int8_t *__restrict__ out, uint32_t wcell,
+                                       uint32_t L, uint32_t vmax, uint32_t thr, const SlowdownKey &sk,
+                                       uint32_t count_from, bool may_wrap, uint32_t &tsum, uint32_t &tcross)
+{
+    const uint32_t wm = __shfl_sync(0xFFFFFFFFu, occ, r >> 5);
+    const uint32_t wn = __shfl_sync(0xFFFFFFFFu, occ_next, r >> 5);
+    const uint32_t gap = __clz(__brev(__funnelshift_rc(wm, wn, (r & 31u) + 1u)));   // empty cells ahead
+    uint32_t vel = min(min((uint32_t)(uint8_t)in[r] + 1u, vmax), gap);               // rules 1, 2
+    uint32_t cell = wcell + r;
+    if (cell >= L) cell -= L;
+    if (D == Draw::kAlways) {
+        vel -= vel != 0u ? 1u : 0u;                                                    // rule 3, p = 1
+    } else if (D == Draw::kPhilox) {
+        const uint32_t u = slowdown_word0(cell, sk);
+        vel -= (vel != 0u && u < thr) ? 1u : 0u;                                       // rule 3
+    }
+    if (active) {
+        out[r + vel] = (int8_t)vel;                                                    // rule 4
+        if (r >= count_from) {
+            tsum += vel;
+            if (may_wrap) tcross += cell + vel >= L ? 1u : 0u;
+        }
+    }
+}
+
+// One step of one row.  in / out / clr: the row in the staged span, the
+// result buffer and the buffer to clear for a later tile.  own_end: span
+// index where the cars not to step begin; count_from: cells of this row
+// before it belong to the left halo (not counted); wcell: road cell of the
+// row's first cell.
+template <Draw D>
+__device__ __forceinline__ void k1_row(const int8_t *__restrict__ in, int8_t *__restrict__ out, int8_t *clr,
+                                       uint16_t *list, uint32_t row0, bool last_row, uint32_t own_end,
+                                       uint32_t count_from, uint32_t wcell, uint32_t L, uint32_t vmax, uint32_t thr,
+                                       const SlowdownKey &sk, uint32_t &tsum, uint32_t &tcross)
+{
+    const uint32_t lane = threadIdx.x & 31u;
+    reinterpret_cast<uint4 *>(clr)[lane] = kEmpty4;
+    reinterpret_cast<uint4 *>(clr)[lane + 32u] = kEmpty4;
+
+    const uint4 *q = reinterpret_cast<const uint4 *>(in + 32u * lane);
+    const uint32_t occ = occupancy16(q[0]) | (occupancy16(q[1]) << 16);
+    uint32_t occ_next = __shfl_down_sync(0xFFFFFFFFu, occ, 1);
+    if (lane == 31u) occ_next = last_row ? 0u : occupancy16(reinterpret_cast<const uint4 *>(in + kK1Row)[0]);
+    uint32_t mine = occ;
+    const uint32_t c0 = row0 + 32u * lane;
+    if (c0 + 32u > own_end) mine = c0 >= own_end ? 0u : mine & ((1u << (own_end - c0)) - 1u);
+
+    const uint32_t n = __popc(mine);
+    uint32_t incl = n;
+#pragma unroll
+    for (uint32_t d = 1; d < 32; d <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+        if (lane >= d) incl += t;
+    }
+    const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+    const bool may_wrap = wcell + kK1Row + 16u >= L;   // a car of this row can pass cell L - 1
+    for (uint32_t chunk = 0; chunk < total; chunk += kK1ListCap) {
+        uint32_t pos = incl - n;
+        if (total <= kK1ListCap) {   // warp-uniform: the whole row at once
+            for (uint32_t mm = mine; mm; mm &= mm - 1u) list[pos++] = (uint16_t)(32u * lane + __clz(__brev(mm)));
+        } else {
+            for (uint32_t mm = mine; mm; mm &= mm - 1u, ++pos)
+                if (pos - chunk < kK1ListCap) list[pos - chunk] = (uint16_t)(32u * lane + __clz(__brev(mm)));
+        }
+        __syncwarp();
+        const uint32_t count = min(kK1ListCap, total - chunk);
+        for (uint32_t first = 0; first < count; first += 64u) {
+            const uint32_t i0 = first + lane, i1 = i0 + 32u;
+            const bool a0 = i0 < count, a1 = i1 < count;
+            const uint32_t r0 = list[a0 ? i0 : 0u];
+            if (first + 32u < count) {   // warp-uniform: a second car for (some) lanes
+                const uint32_t r1 = list[a1 ? i1 : 0u];
+                k1_car<D>(a0, r0, occ, occ_next, in, out, wcell, L, vmax, thr, sk, count_from, may_wrap, tsum, tcross);
+                k1_car<D>(a1, r1, occ, occ_next, in, out, wcell, L, vmax, thr, sk, count_from, may_wrap, tsum, tcross);
+            } else {
+                k1_car<D>(a0, r0, occ, occ_next, in, out, wcell, L, vmax, thr, sk, count_from, may_wrap, tsum, tcross);
+            }
+        }
+        __syncwarp();   // the list is rewritten by the next pass or tile
+    }
+}
+
+template <Draw D>
+__global__ void __launch_bounds__(kGridThreads, 5) grid_k1_kernel(const GridStep g, const GridTileGeom geo,
+                                                               const SlowdownKey sk)
+{
+    __shared__ __align__(128) int8_t s_in[kK1Stages][kGridSpan];
+    __shared__ __align__(128) int8_t s_out[kK1Outs][kGridSpan];
+    __shared__ __align__(8) uint64_t s_full[kK1Stages];
+    __shared__ uint16_t s_list[kGridWarps][kK1ListCap];
+
+    const uint32_t L = g.rc.L, vmax = g.rc.vmax, thr = (uint32_t)g.rc.thr;
+    const uint32_t H = geo.halo, C = geo.tile, W = (uint32_t)kGridSpan;
+    const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+    const uint32_t row0 = warp * kK1Row;
+    // the thread that issues the copies and waits for them; its warp varies
+    // with the block, so the waits of the blocks on one SM spread over its
+    // schedulers
+    const uint32_t leader = (blockIdx.x % kGridWarps) * 32u;
+
+    if (tid == leader) {
+        for (uint32_t b = 0; b < kK1Stages; ++b) mbar_init(&s_full[b], 1);
+        fence_mbar_init();
+    }
+    for (uint32_t c = tid; c < W / 16u; c += kGridThreads) reinterpret_cast<uint4 *>(s_out[0])[c] = kEmpty4;
+    __syncthreads();
+
+    auto bulk_ok = [&](uint32_t tile) {
+        const uint32_t t0 = tile * C;
+        return t0 >= H && t0 + C + H <= L;
+    };
+    uint32_t tile = blockIdx.x;
+    if (tid == leader && tile < geo.n_tiles && bulk_ok(tile)) {
+        mbar_expect_tx(&s_full[0], W);
+        bulk_load(s_in[0], g.c_in + (tile * C - H), W, &s_full[0]);
+    }
+    uint32_t parity = 0;
+    bool prev_stored = false;             // the previous tile left by a bulk store (leader only)
+    unsigned long long acc_sum = 0, acc_cross = 0;
+    for (uint32_t it = 0; tile < geo.n_tiles; tile += gridDim.x, ++it) {
+        const uint32_t sb = it & 1u;
+        const uint32_t ob = it % kK1Outs;
+        const uint32_t cb = ob + 1u == kK1Outs ? 0u : ob + 1u;   // cleared now, scattered into by the next tile
+        const uint32_t t0 = tile * C;
+        const uint32_t own_cells = min(C, L - t0);
+        const uint32_t base = t0 >= H ? t0 - H : t0 + L - H;     // road cell of span index 0
+        int8_t *in = s_in[sb];
+        if (tid == leader) {
+            // the other stage was read by the previous tile, which every thread has finished
+            const uint32_t ahead = tile + gridDim.x;
+            if (ahead < geo.n_tiles && bulk_ok(ahead)) {
+                fence_proxy_async();
+                mbar_expect_tx(&s_full[sb ^ 1u], W);
+                bulk_load(s_in[sb ^ 1u], g.c_in + (ahead * C - H), W, &s_full[sb ^ 1u]);
+            }
+            // buffer cb was last stored two tiles ago: that store must have read it
+            if (prev_stored) bulk_wait_read_1();
+            else bulk_wait_read_all();
+        }
+        bool ok = true;
+        if (bulk_ok(tile)) {
+            if (tid == leader) ok = mbar_wait_bounded(&s_full[sb], (parity >> sb) & 1u);
+            parity ^= 1u << sb;
+        } else {
+            for (uint32_t i = tid; i < W; i += kGridThreads) {
+                uint32_t cell = base + i;
+                if (cell >= L) cell -= L;
+                in[i] = g.c_in[cell];
+            }
+        }
+        if (!__syncthreads_and(ok)) {
+            if (tid == leader) {
+                atomicOr(g.status, kStatusTimeout);
+                const uint32_t ahead = tile + gridDim.x;   // its load may still be in flight
+                if (ahead < geo.n_tiles && bulk_ok(ahead))
+                    mbar_wait_bounded(&s_full[sb ^ 1u], (parity >> (sb ^ 1u)) & 1u);
+                bulk_wait_all();
+            }
+            return;
+        }
+        uint32_t wcell = base + row0;
+        if (wcell >= L) wcell -= L;
+        uint32_t tsum = 0, tcross = 0;
+        k1_row<D>(in + row0, s_out[ob] + row0, s_out[cb] + row0, s_list[warp], row0, warp + 1u == kGridWarps,
+                  H + own_cells, row0 >= H ? 0u : H - row0, wcell, L, vmax, thr, sk, tsum, tcross);
+        tsum = __reduce_add_sync(0xFFFFFFFFu, tsum);
+        tcross = __reduce_add_sync(0xFFFFFFFFu, tcross);
+        acc_sum += tsum;
+        acc_cross += tcross;
+        fence_proxy_async();   // the scattered result leaves by bulk store; the stage is refilled by bulk load
+        __syncthreads();
+        if (own_cells == C) {
+            if (tid == leader) {
+                bulk_store(g.c_out + t0, s_out[ob] + H, C);
+                bulk_commit();
+                prev_stored = true;
+            }
+        } else {
+            for (uint32_t i = tid; i < own_cells; i += kGridThreads) g.c_out[t0 + i] = s_out[ob][H + i];
+            prev_stored = false;
+        }
+    }
+    if (tid == leader) bulk_wait_all();
+    if (lane == 0) {
+        if (acc_sum) atomicAdd(&g.sum_v[0], acc_sum);
+        if (acc_cross) atomicAdd(&g.crossings[0], acc_cross);
+    }
+}
+
 // Whole ring in one block (L <= kGridRingMaxCells).
 __global__ void __launch_bounds__(1024) grid_ring_kernel(const GridStep g)
 {
@@ -345,6 +560,14 @@ cudaError_t launch_mask_draw(const GridStep &g, const GridTileGeom &geo, int gri
     return launch_mask_variant<Draw::kPhilox, kWide>(g, geo, grid, smem, s);
 }
 
+template <Draw D>
+cudaError_t launch_k1_variant(const GridStep &g, const GridTileGeom &geo, int grid, cudaStream_t s)
+{
+    const SlowdownKey sk = make_slowdown_key(g.step0, g.rc.road, g.rc.key0, g.rc.key1);
+    grid_k1_kernel<D><<<grid, kGridThreads, 0, s>>>(g, geo, sk);
+    return cudaGetLastError();
+}
+
 // Static plus dynamic shared memory exceeds the default 48 KB, so the
 // dynamic size is allowed explicitly (a per-device function attribute).
 template <Draw D>
@@ -379,6 +602,14 @@ cudaError_t launch_grid_tiled(const GridStep &g, int blocks, cudaStream_t s)
     const GridTileGeom geo = make_geom(g.ksteps, g.rc.vmax, g.rc.L);
     // the tile must own cells, and the staged span must not wrap the ring twice
     if (2u * geo.halo >= (uint32_t)kGridSpan || g.rc.L < (uint32_t)kGridSpan) return cudaErrorInvalidValue;
+    if (g.ksteps == 1 && g.rc.vmax <= 16u) {
+        // 5 blocks per SM (42 KB of shared memory each) where the list kernel fits 3
+        const int kblocks = blocks * 5 / 3;
+        const int grid = (int)((uint32_t)kblocks < geo.n_tiles ? (uint32_t)kblocks : geo.n_tiles);
+        if (g.rc.thr == 0) return launch_k1_variant<Draw::kNever>(g, geo, grid, s);
+        if (g.rc.thr > 0xFFFFFFFFull) return launch_k1_variant<Draw::kAlways>(g, geo, grid, s);
+        return launch_k1_variant<Draw::kPhilox>(g, geo, grid, s);
+    }
     if (g.ksteps == 1) {
         const GridTileGeom mg = make_mask_geom(g.rc.vmax, g.rc.L);
         const size_t msmem = grid_mask_smem(mg);

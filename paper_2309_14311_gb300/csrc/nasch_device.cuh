@@ -50,6 +50,69 @@ __device__ __forceinline__ uint32_t philox_word0(uint32_t c0, uint32_t c1, uint3
     return philox4x32_10(c0, c1, c2, c3, k0, k1).w0;
 }
 
+// The rule-3 draw of one step with the parts that do not depend on the
+// cell computed once.  The counter is (cell, step, road, 0): in round 1 the
+// product of word 2 (road) is the same for every car, so words 0 and 1 of
+// round 1's output are constants; in round 2 so is the product of word 0,
+// and round 3 xors a constant into word 2.  The key schedule is folded in
+// as well.  slowdown_word0(cell, make_slowdown_key(...)) equals
+// philox_word0(cell, step, road, kTagSlowdown, k0, k1) for every cell.
+struct SlowdownKey {
+    uint32_t k1_0;     // round 1: word 2 = hi(A * cell) ^ k1_0
+    uint32_t x2a;      // round 2: word 0 = hi(B * word 2) ^ x2a
+    uint32_t x2b;      // round 2: word 2 = round-1 word 3 ^ x2b
+    uint32_t x3;       // round 3: word 2 = hi(A * word 0) ^ x3
+    uint32_t k0[10];   // key word 0 of each round
+    uint32_t k1[10];   // key word 1 of each round
+};
+
+__host__ __device__ inline SlowdownKey make_slowdown_key(uint32_t step, uint32_t road, uint32_t k0, uint32_t k1)
+{
+    SlowdownKey s;
+    for (int r = 0; r < 10; ++r) {
+        s.k0[r] = k0 + (uint32_t)r * kWeylA;
+        s.k1[r] = k1 + (uint32_t)r * kWeylB;
+    }
+    const uint64_t pb1 = (uint64_t)kMulB * road;                       // round 1, word 2's product
+    const uint32_t u0 = (uint32_t)(pb1 >> 32) ^ step ^ s.k0[0];       // round-1 output word 0
+    const uint32_t u1 = (uint32_t)pb1;                                 // round-1 output word 1
+    const uint64_t pa2 = (uint64_t)kMulA * u0;                         // round 2, word 0's product
+    s.k1_0 = s.k1[0];
+    s.x2a = u1 ^ s.k0[1];
+    s.x2b = (uint32_t)(pa2 >> 32) ^ s.k1[1];
+    s.x3 = (uint32_t)pa2 ^ s.k1[2];                                    // round-2 output word 3, then round 3's key
+    return s;
+}
+
+__host__ __device__ __forceinline__ uint32_t slowdown_word0(uint32_t cell, const SlowdownKey &s)
+{
+    uint64_t pa = (uint64_t)kMulA * cell;                              // round 1
+    uint32_t c2 = (uint32_t)(pa >> 32) ^ s.k1_0;
+    uint32_t c3 = (uint32_t)pa;
+    uint64_t pb = (uint64_t)kMulB * c2;                                // round 2
+    uint32_t c0 = (uint32_t)(pb >> 32) ^ s.x2a;
+    uint32_t c1 = (uint32_t)pb;
+    c2 = c3 ^ s.x2b;
+    pa = (uint64_t)kMulA * c0;                                         // round 3
+    pb = (uint64_t)kMulB * c2;
+    c0 = (uint32_t)(pb >> 32) ^ c1 ^ s.k0[2];
+    c2 = (uint32_t)(pa >> 32) ^ s.x3;
+    c1 = (uint32_t)pb;
+    c3 = (uint32_t)pa;
+#pragma unroll
+    for (int r = 3; r < 9; ++r) {                                      // rounds 4-9
+        pa = (uint64_t)kMulA * c0;
+        pb = (uint64_t)kMulB * c2;
+        const uint32_t n0 = (uint32_t)(pb >> 32) ^ c1 ^ s.k0[r];
+        const uint32_t n2 = (uint32_t)(pa >> 32) ^ c3 ^ s.k1[r];
+        c1 = (uint32_t)pb;
+        c3 = (uint32_t)pa;
+        c0 = n0;
+        c2 = n2;
+    }
+    return (uint32_t)(((uint64_t)kMulB * c2) >> 32) ^ c1 ^ s.k0[9];   // round 10, word 0
+}
+
 // Parameters every step kernel shares.
 struct RoadConst {
     uint32_t L;        // ring length, 1..2^31

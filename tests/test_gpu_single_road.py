@@ -140,6 +140,30 @@ def test_grid_tiled_matches_oracle(L, N, vmax, p, k, T):
     assert_same(lib, orc, L, "grid")
 
 
+GRID_ONE_STEP = [  # (L, N, vmax, p, T): one step per launch (k = 1)
+    (40000, 8000, 5, 0.13, 30),
+    (8192 * 5 + 7, 9000, 5, 0.25, 25),         # ragged last tile
+    (50000, 30000, 5, 0.5, 40),                # rows of more than 128 cars: listed in passes
+    (100000, 99000, 3, 0.2, 30),               # nearly full
+    (16384, 16384, 5, 0.5, 3),                 # full ring: nothing moves
+    (50000, 30000, 5, 0.0, 20),                # p = 0
+    (50000, 2000, 5, 1.0, 20),                 # p = 1
+    (20000, 3000, 0, 0.5, 10),                 # vmax = 0: no halo
+    (60000, 3000, 16, 0.3, 21),                # largest vmax of the one-step kernel
+    (60000, 3000, 17, 0.3, 21),                # smallest vmax past it
+    (33000, 1, 5, 0.2, 30),                    # a car alone
+    (2**31, 4000, 5, 0.13, 24),                # wrap arithmetic at L = 2^31
+]
+
+
+@pytest.mark.parametrize("L,N,vmax,p,T", GRID_ONE_STEP)
+def test_grid_one_step_matches_oracle(L, N, vmax, p, T):
+    seed = 91 + L % 37
+    orc = oracle_run(L, N, vmax, p, seed, T, road=6)
+    lib = lib_run(L, N, vmax, p, seed, T, road=6, layout="grid", k=1, tile=8192)
+    assert_same(lib, orc, L, "grid")
+
+
 @pytest.mark.parametrize("L,N,vmax,p,T", [(200, 50, 5, 0.13, 300), (3, 2, 127, 0.5, 50), (1, 1, 3, 0.5, 5),
                                           (32768, 4000, 20, 0.3, 40), (8192, 8192, 5, 0.5, 3),
                                           (9000, 8192, 2, 0.2, 60), (500, 0, 5, 0.5, 10)])
@@ -205,7 +229,8 @@ def test_large_road_full_size(large_init):
     """The large road at full size (2^31 cells, 2^27 cars) in the launch
     configuration the benchmark times: the start state equals the oracle's,
     the first 100 steps equal the oracle's in full (state and per-step
-    statistics), the grid layout equals the agent layout after 100 steps,
+    statistics), the grid layout (one step per launch, and fused) equals
+    the agent layout after 100 steps,
     and after 10^4 steps sampled windows of cars equal the oracle's
     light-cone evolution of the same cars from the start."""
     s = WL.LARGE_ROAD
@@ -228,14 +253,17 @@ def test_large_road_full_size(large_init):
         xT, vT = xT.copy(), vT.copy()
         svT, _ = r.stats()
         assert len(svT) == s.T
-    with NS.Road(s.L, s.N, s.vmax, s.p, s.seed, layout="grid", k=WL.LARGE_ROAD_K["grid"]) as g:
-        g.run(T0)
-        svg, crg = g.stats()
-        assert np.array_equal(svg, sva) and np.array_equal(crg, cra)
-        xg, vg = g.read_state()   # cars in cell order
-        order = np.argsort(xa, kind="stable")
-        assert np.array_equal(xg, xa[order]) and np.array_equal(vg, va[order])
-        del xg, vg
+    # the grid layout in both launch configurations the benchmark times:
+    # one step per launch (mask-step kernel) and the fused depth
+    order = np.argsort(xa, kind="stable")
+    for kg in (1, WL.LARGE_ROAD_K["grid"]):
+        with NS.Road(s.L, s.N, s.vmax, s.p, s.seed, layout="grid", k=kg) as g:
+            g.run(T0)
+            svg, crg = g.stats()
+            assert np.array_equal(svg, sva) and np.array_equal(crg, cra), kg
+            xg, vg = g.read_state()   # cars in cell order
+            assert np.array_equal(xg, xa[order]) and np.array_equal(vg, va[order]), kg
+            del xg, vg
     # sampled light-cone windows over the full 10^4 steps
     rng = np.random.default_rng(2309)
     M = s.T + 48
