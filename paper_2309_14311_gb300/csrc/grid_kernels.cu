@@ -294,125 +294,69 @@ __global__ void __launch_bounds__(kGridThreads) grid_mask_kernel(const GridStep 
 
 // k = 1 and vmax <= 16: the one-step kernel.  A span is the tile's C =
 // 8192 - 2H owned cells with H = 16 halo cells on each side (H = 0 when
-// vmax = 0).  Each warp steps one 1024-cell row: its lanes turn 32 cells
-// each into an occupancy mask, the cars of the row are listed (a prefix sum
-// of the lanes' car counts gives each lane its first slot), and the lanes
-// take the listed cars 32 or 64 at a time, so every lane draws for the same
-// number of cars.  A car's gap is the count of trailing zeros of the masks
-// after its cell (vmax <= 16 < 32 cells in view).  Cars in the right halo
-// are not stepped: they can only move further right, out of the tile.
-// Cars in the left halo are stepped (they may move into the tile) but not
-// counted in the statistics.  Results are scattered into an all -1 buffer,
-// which leaves by one bulk store; three result buffers rotate, so the one
-// being cleared was stored two tiles earlier.  The rule-3 draw uses the
-// counter-independent parts of Philox computed on the host (SlowdownKey).
+// vmax = 0).  Per tile:
+//   1. each thread turns its 32 cells into an occupancy word (kept in shared
+//      memory for the gaps) and counts the cars it must step: those left of
+//      the right halo (a car in the right halo can only move out of the
+//      tile; one in the left halo may move in, and is stepped but not
+//      counted in the statistics);
+//   2. a block-wide prefix sum of the counts gives each thread its slots in
+//      one car list, which is padded to a multiple of 32 with a dummy car
+//      that reads and writes only padding;
+//   3. the warps take the list 32 cars at a time (two groups per warp
+//      interleaved), so every lane draws for the same number of cars and no
+//      lane is idle; a car's gap is the count of trailing zeros of the
+//      occupancy words after its cell (vmax <= 16 < 32 cells in view);
+//   4. cars are scattered into an all -1 buffer, which leaves by one bulk
+//      store; three result buffers rotate, so the one cleared during a tile
+//      was stored two tiles earlier.
+// The rule-3 draw uses the counter-independent parts of Philox computed on
+// the host (SlowdownKey).
 constexpr uint32_t kK1Stages = 2;       // staged spans: the tile being stepped and the next one loading
 constexpr uint32_t kK1Outs = 3;         // result buffers: scattered into, being stored, being cleared
-constexpr uint32_t kK1ListCap = 128;    // car-list entries per warp; a denser row is listed in several passes
-constexpr uint32_t kK1Row = 1024;       // cells per warp
-static_assert(kK1Row * kGridWarps == (uint32_t)kGridSpan, "one row per warp");
+constexpr uint32_t kK1Pad = 32;         // padding after each span buffer: the dummy car's cell and moves
+constexpr uint32_t kK1Buf = (uint32_t)kGridSpan + kK1Pad;
+constexpr uint32_t kK1ListCap = 1024;   // car-list entries; a denser tile is listed and stepped in passes
+constexpr uint32_t kK1Dummy = (uint32_t)kGridSpan;   // span index of the dummy car (empty padding)
+static_assert(kGridSpan == 32 * kGridThreads, "32 cells per thread");
 
-// One car of a row: rules 1-4.  r: its cell within the row; occ / occ_next
-// of every lane are exchanged by shuffles, so all 32 lanes call this
-// together (an inactive lane computes a dummy car and stores nothing).
+// One car: rules 1-4.  r: span index of its cell (kK1Dummy for padding);
+// returns the velocity used by the move.
 template <Draw D>
-__device__ __forceinline__ void k1_car(bool active, uint32_t r, uint32_t occ, uint32_t occ_next,
-                                       const int8_t *__restrict__ in, int8_t *__restrict__ out, uint32_t wcell,
-                                       uint32_t L, uint32_t vmax, uint32_t thr, const SlowdownKey &sk,
-                                       uint32_t count_from, bool may_wrap, uint32_t &tsum, uint32_t &tcross)
+__device__ __forceinline__ uint32_t k1_car(uint32_t r, const int8_t *__restrict__ in, int8_t *__restrict__ out,
+                                           const uint32_t *__restrict__ occ, uint32_t base, uint32_t L,
+                                           uint32_t vmax, uint32_t thr, const SlowdownKey &sk, uint32_t &cell)
 {
-    const uint32_t wm = __shfl_sync(0xFFFFFFFFu, occ, r >> 5);
-    const uint32_t wn = __shfl_sync(0xFFFFFFFFu, occ_next, r >> 5);
-    const uint32_t gap = __clz(__brev(__funnelshift_rc(wm, wn, (r & 31u) + 1u)));   // empty cells ahead
-    uint32_t vel = min(min((uint32_t)(uint8_t)in[r] + 1u, vmax), gap);               // rules 1, 2
-    uint32_t cell = wcell + r;
+    const uint32_t w = r >> 5;
+    const uint32_t gap = __clz(__brev(__funnelshift_rc(occ[w], occ[w + 1u], (r & 31u) + 1u)));   // empty cells ahead
+    uint32_t vel = min(min((uint32_t)(uint8_t)in[r] + 1u, vmax), gap);                             // rules 1, 2
+    cell = base + r;
     if (cell >= L) cell -= L;
     if (D == Draw::kAlways) {
-        vel -= vel != 0u ? 1u : 0u;                                                    // rule 3, p = 1
+        vel -= vel != 0u ? 1u : 0u;                                                                  // rule 3, p = 1
     } else if (D == Draw::kPhilox) {
         const uint32_t u = slowdown_word0(cell, sk);
-        vel -= (vel != 0u && u < thr) ? 1u : 0u;                                       // rule 3
+        vel -= (vel != 0u && u < thr) ? 1u : 0u;                                                     // rule 3
     }
-    if (active) {
-        out[r + vel] = (int8_t)vel;                                                    // rule 4
-        if (r >= count_from) {
-            tsum += vel;
-            if (may_wrap) tcross += cell + vel >= L ? 1u : 0u;
-        }
-    }
-}
-
-// One step of one row.  in / out / clr: the row in the staged span, the
-// result buffer and the buffer to clear for a later tile.  own_end: span
-// index where the cars not to step begin; count_from: cells of this row
-// before it belong to the left halo (not counted); wcell: road cell of the
-// row's first cell.
-template <Draw D>
-__device__ __forceinline__ void k1_row(const int8_t *__restrict__ in, int8_t *__restrict__ out, int8_t *clr,
-                                       uint16_t *list, uint32_t row0, bool last_row, uint32_t own_end,
-                                       uint32_t count_from, uint32_t wcell, uint32_t L, uint32_t vmax, uint32_t thr,
-                                       const SlowdownKey &sk, uint32_t &tsum, uint32_t &tcross)
-{
-    const uint32_t lane = threadIdx.x & 31u;
-    reinterpret_cast<uint4 *>(clr)[lane] = kEmpty4;
-    reinterpret_cast<uint4 *>(clr)[lane + 32u] = kEmpty4;
-
-    const uint4 *q = reinterpret_cast<const uint4 *>(in + 32u * lane);
-    const uint32_t occ = occupancy16(q[0]) | (occupancy16(q[1]) << 16);
-    uint32_t occ_next = __shfl_down_sync(0xFFFFFFFFu, occ, 1);
-    if (lane == 31u) occ_next = last_row ? 0u : occupancy16(reinterpret_cast<const uint4 *>(in + kK1Row)[0]);
-    uint32_t mine = occ;
-    const uint32_t c0 = row0 + 32u * lane;
-    if (c0 + 32u > own_end) mine = c0 >= own_end ? 0u : mine & ((1u << (own_end - c0)) - 1u);
-
-    const uint32_t n = __popc(mine);
-    uint32_t incl = n;
-#pragma unroll
-    for (uint32_t d = 1; d < 32; d <<= 1) {
-        const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, incl, d);
-        if (lane >= d) incl += t;
-    }
-    const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
-    const bool may_wrap = wcell + kK1Row + 16u >= L;   // a car of this row can pass cell L - 1
-    for (uint32_t chunk = 0; chunk < total; chunk += kK1ListCap) {
-        uint32_t pos = incl - n;
-        if (total <= kK1ListCap) {   // warp-uniform: the whole row at once
-            for (uint32_t mm = mine; mm; mm &= mm - 1u) list[pos++] = (uint16_t)(32u * lane + __clz(__brev(mm)));
-        } else {
-            for (uint32_t mm = mine; mm; mm &= mm - 1u, ++pos)
-                if (pos - chunk < kK1ListCap) list[pos - chunk] = (uint16_t)(32u * lane + __clz(__brev(mm)));
-        }
-        __syncwarp();
-        const uint32_t count = min(kK1ListCap, total - chunk);
-        for (uint32_t first = 0; first < count; first += 64u) {
-            const uint32_t i0 = first + lane, i1 = i0 + 32u;
-            const bool a0 = i0 < count, a1 = i1 < count;
-            const uint32_t r0 = list[a0 ? i0 : 0u];
-            if (first + 32u < count) {   // warp-uniform: a second car for (some) lanes
-                const uint32_t r1 = list[a1 ? i1 : 0u];
-                k1_car<D>(a0, r0, occ, occ_next, in, out, wcell, L, vmax, thr, sk, count_from, may_wrap, tsum, tcross);
-                k1_car<D>(a1, r1, occ, occ_next, in, out, wcell, L, vmax, thr, sk, count_from, may_wrap, tsum, tcross);
-            } else {
-                k1_car<D>(a0, r0, occ, occ_next, in, out, wcell, L, vmax, thr, sk, count_from, may_wrap, tsum, tcross);
-            }
-        }
-        __syncwarp();   // the list is rewritten by the next pass or tile
-    }
+    out[r + vel] = (int8_t)vel;                                                                      // rule 4
+    return vel;
 }
 
 template <Draw D>
-__global__ void __launch_bounds__(kGridThreads, 5) grid_k1_kernel(const GridStep g, const GridTileGeom geo,
+__global__ void __launch_bounds__(kGridThreads) grid_k1_kernel(const GridStep g, const GridTileGeom geo,
                                                                const SlowdownKey sk)
 {
-    __shared__ __align__(128) int8_t s_in[kK1Stages][kGridSpan];
-    __shared__ __align__(128) int8_t s_out[kK1Outs][kGridSpan];
+    __shared__ __align__(128) int8_t s_in[kK1Stages][kK1Buf];
+    __shared__ __align__(128) int8_t s_out[kK1Outs][kK1Buf];
+    __shared__ uint32_t s_occ[kGridThreads + 2];   // occupancy of each thread's cells; two empty words after
+    __shared__ uint16_t s_list[kK1ListCap];
+    __shared__ __align__(16) uint32_t s_warp[kGridWarps];
     __shared__ __align__(8) uint64_t s_full[kK1Stages];
-    __shared__ uint16_t s_list[kGridWarps][kK1ListCap];
 
     const uint32_t L = g.rc.L, vmax = g.rc.vmax, thr = (uint32_t)g.rc.thr;
     const uint32_t H = geo.halo, C = geo.tile, W = (uint32_t)kGridSpan;
     const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
-    const uint32_t row0 = warp * kK1Row;
+    const uint32_t c0 = 32u * tid;                 // first span index of this thread's cells
     // the thread that issues the copies and waits for them; its warp varies
     // with the block, so the waits of the blocks on one SM spread over its
     // schedulers
@@ -423,6 +367,11 @@ __global__ void __launch_bounds__(kGridThreads, 5) grid_k1_kernel(const GridStep
         fence_mbar_init();
     }
     for (uint32_t c = tid; c < W / 16u; c += kGridThreads) reinterpret_cast<uint4 *>(s_out[0])[c] = kEmpty4;
+    if (tid < kK1Stages * (kK1Pad / 16u)) {   // the padding the loads never write: empty cells
+        const uint32_t b = tid / (kK1Pad / 16u), q = tid % (kK1Pad / 16u);
+        reinterpret_cast<uint4 *>(s_in[b] + W)[q] = kEmpty4;
+    }
+    if (tid < 2u) s_occ[kGridThreads + tid] = 0u;
     __syncthreads();
 
     auto bulk_ok = [&](uint32_t tile) {
@@ -436,7 +385,7 @@ __global__ void __launch_bounds__(kGridThreads, 5) grid_k1_kernel(const GridStep
     }
     uint32_t parity = 0;
     bool prev_stored = false;             // the previous tile left by a bulk store (leader only)
-    unsigned long long acc_sum = 0, acc_cross = 0;
+    uint32_t tsum = 0, tcross = 0;        // statistics of this thread's cars, reduced at the end
     for (uint32_t it = 0; tile < geo.n_tiles; tile += gridDim.x, ++it) {
         const uint32_t sb = it & 1u;
         const uint32_t ob = it % kK1Outs;
@@ -445,6 +394,7 @@ __global__ void __launch_bounds__(kGridThreads, 5) grid_k1_kernel(const GridStep
         const uint32_t own_cells = min(C, L - t0);
         const uint32_t base = t0 >= H ? t0 - H : t0 + L - H;     // road cell of span index 0
         int8_t *in = s_in[sb];
+        int8_t *out = s_out[ob];
         if (tid == leader) {
             // the other stage was read by the previous tile, which every thread has finished
             const uint32_t ahead = tile + gridDim.x;
@@ -478,29 +428,94 @@ __global__ void __launch_bounds__(kGridThreads, 5) grid_k1_kernel(const GridStep
             }
             return;
         }
-        uint32_t wcell = base + row0;
-        if (wcell >= L) wcell -= L;
-        uint32_t tsum = 0, tcross = 0;
-        k1_row<D>(in + row0, s_out[ob] + row0, s_out[cb] + row0, s_list[warp], row0, warp + 1u == kGridWarps,
-                  H + own_cells, row0 >= H ? 0u : H - row0, wcell, L, vmax, thr, sk, tsum, tcross);
-        tsum = __reduce_add_sync(0xFFFFFFFFu, tsum);
-        tcross = __reduce_add_sync(0xFFFFFFFFu, tcross);
-        acc_sum += tsum;
-        acc_cross += tcross;
-        fence_proxy_async();   // the scattered result leaves by bulk store; the stage is refilled by bulk load
+        // 1. occupancy; clear this thread's cells of the buffer for the next tile
+        reinterpret_cast<uint4 *>(s_out[cb] + c0)[0] = kEmpty4;
+        reinterpret_cast<uint4 *>(s_out[cb] + c0)[1] = kEmpty4;
+        const uint4 *q = reinterpret_cast<const uint4 *>(in + c0);
+        const uint32_t occ = occupancy16(q[0]) | (occupancy16(q[1]) << 16);
+        s_occ[tid] = occ;
+        const uint32_t own_end = H + own_cells;   // cars from here on are not stepped
+        uint32_t mine = occ;
+        if (c0 + 32u > own_end) mine = c0 >= own_end ? 0u : mine & ((1u << (own_end - c0)) - 1u);
+        // 2. block-wide prefix sum of the car counts
+        const uint32_t n = __popc(mine);
+        uint32_t incl = n;
+#pragma unroll
+        for (uint32_t d = 1; d < 32; d <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+            if (lane >= d) incl += t;
+        }
+        if (lane == 31u) s_warp[warp] = incl;
         __syncthreads();
+        uint32_t before = 0, total = 0;
+#pragma unroll
+        for (uint32_t j = 0; j < kGridWarps; ++j) {
+            const uint32_t t = s_warp[j];
+            before += j < warp ? t : 0u;
+            total += t;
+        }
+        const uint32_t first_slot = before + incl - n;
+        const bool wraps = base + W + kK1Pad > L;   // the span holds cell L - 1: crossings possible
+        for (uint32_t chunk = 0; chunk < total; chunk += kK1ListCap) {
+            const uint32_t count = min(kK1ListCap, total - chunk);
+            const uint32_t padded = (count + 31u) & ~31u;
+            uint32_t pos = first_slot;
+            if (total <= kK1ListCap) {   // block-uniform: the whole tile at once
+                for (uint32_t mm = mine; mm; mm &= mm - 1u) s_list[pos++] = (uint16_t)(c0 + __clz(__brev(mm)));
+            } else {
+                for (uint32_t mm = mine; mm; mm &= mm - 1u, ++pos)
+                    if (pos - chunk < kK1ListCap) s_list[pos - chunk] = (uint16_t)(c0 + __clz(__brev(mm)));
+            }
+            if (tid < padded - count) s_list[count + tid] = (uint16_t)kK1Dummy;
+            __syncthreads();
+            // 3. groups of 32 cars: warp w takes groups w, w + 8, ...; two at a time
+            const uint32_t groups = padded >> 5;
+            for (uint32_t gi = warp; gi < groups; gi += 2u * kGridWarps) {
+                uint32_t cell0, cell1;
+                const uint32_t r0 = s_list[32u * gi + lane];
+                if (gi + kGridWarps < groups) {   // warp-uniform
+                    const uint32_t r1 = s_list[32u * (gi + kGridWarps) + lane];
+                    const uint32_t v0 = k1_car<D>(r0, in, out, s_occ, base, L, vmax, thr, sk, cell0);
+                    const uint32_t v1 = k1_car<D>(r1, in, out, s_occ, base, L, vmax, thr, sk, cell1);
+                    const bool own0 = r0 - H < own_cells, own1 = r1 - H < own_cells;
+                    tsum += (own0 ? v0 : 0u) + (own1 ? v1 : 0u);
+                    if (wraps) tcross += (own0 && cell0 + v0 >= L ? 1u : 0u) + (own1 && cell1 + v1 >= L ? 1u : 0u);
+                } else {
+                    const uint32_t v0 = k1_car<D>(r0, in, out, s_occ, base, L, vmax, thr, sk, cell0);
+                    const bool own0 = r0 - H < own_cells;
+                    tsum += own0 ? v0 : 0u;
+                    if (wraps) tcross += own0 && cell0 + v0 >= L ? 1u : 0u;
+                }
+            }
+            // 4. the scattered result leaves by bulk store; the list and the
+            // occupancy words are rewritten by the next pass or tile; the
+            // stage is refilled by a bulk load
+            fence_proxy_async();
+            __syncthreads();
+        }
+        if (total == 0u) {
+            fence_proxy_async();
+            __syncthreads();
+        }
         if (own_cells == C) {
             if (tid == leader) {
-                bulk_store(g.c_out + t0, s_out[ob] + H, C);
+                bulk_store(g.c_out + t0, out + H, C);
                 bulk_commit();
                 prev_stored = true;
             }
         } else {
-            for (uint32_t i = tid; i < own_cells; i += kGridThreads) g.c_out[t0 + i] = s_out[ob][H + i];
+            for (uint32_t i = tid; i < own_cells; i += kGridThreads) g.c_out[t0 + i] = out[H + i];
             prev_stored = false;
         }
     }
     if (tid == leader) bulk_wait_all();
+    // a thread's sums stay far below 2^32 (at most 32 cars x vmax per tile);
+    // the warp's total may not
+    unsigned long long acc_sum = tsum, acc_cross = tcross;
+    for (uint32_t d = 16; d >= 1; d >>= 1) {
+        acc_sum += __shfl_xor_sync(0xFFFFFFFFu, acc_sum, d);
+        acc_cross += __shfl_xor_sync(0xFFFFFFFFu, acc_cross, d);
+    }
     if (lane == 0) {
         if (acc_sum) atomicAdd(&g.sum_v[0], acc_sum);
         if (acc_cross) atomicAdd(&g.crossings[0], acc_cross);

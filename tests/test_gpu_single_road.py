@@ -143,7 +143,7 @@ def test_grid_tiled_matches_oracle(L, N, vmax, p, k, T):
 GRID_ONE_STEP = [  # (L, N, vmax, p, T): one step per launch (k = 1)
     (40000, 8000, 5, 0.13, 30),
     (8192 * 5 + 7, 9000, 5, 0.25, 25),         # ragged last tile
-    (50000, 30000, 5, 0.5, 40),                # rows of more than 128 cars: listed in passes
+    (50000, 30000, 5, 0.5, 40),                # tiles of more than 1024 cars: listed in passes
     (100000, 99000, 3, 0.2, 30),               # nearly full
     (16384, 16384, 5, 0.5, 3),                 # full ring: nothing moves
     (50000, 30000, 5, 0.0, 20),                # p = 0
