@@ -23,12 +23,15 @@
 //
 // Ring kernel.  For L <= kGridRingMaxCells one block holds the whole ring
 // in shared memory and runs any number of steps in one launch.
+#include <atomic>
+
 #include "tile_device.cuh"
 
 namespace nasch {
 namespace {
 
 constexpr uint32_t kGridWarps = (uint32_t)kGridThreads / 32u;
+constexpr int kMaxDevices = 64;
 constexpr uint32_t kGridStages = 2;   // spans in flight per block: the current one and one prefetched
 constexpr uint32_t kGridListCap = (uint32_t)kGridSpan;   // every span's cars fit the list
 
@@ -292,36 +295,48 @@ __global__ void __launch_bounds__(kGridThreads) grid_mask_kernel(const GridStep 
     }
 }
 
-// k = 1 and vmax <= 16: the one-step kernel.  A span is the tile's C =
-// 8192 - 2H owned cells with H = 16 halo cells on each side (H = 0 when
-// vmax = 0).  Per tile:
-//   1. each thread turns its 32 cells into an occupancy word (kept in shared
-//      memory for the gaps) and counts the cars it must step: those left of
+// k = 1 and vmax <= 16: the one-step kernel.  Every warp works alone (no
+// block barrier after set-up) on tiles of 2016 cells: it stages the tile with
+// 16 halo cells on each side (2048 cells, one bulk copy on the warp's own
+// mbarrier), steps it, and writes the 2016 cells back by one bulk store.
+// Per tile:
+//   1. each lane turns 64 cells into two occupancy words, kept in shared
+//      memory for the gaps, and counts the cars it must step: those left of
 //      the right halo (a car in the right halo can only move out of the
 //      tile; one in the left halo may move in, and is stepped but not
 //      counted in the statistics);
-//   2. a block-wide prefix sum of the counts gives each thread its slots in
-//      one car list, which is padded to a multiple of 32 with a dummy car
-//      that reads and writes only padding;
-//   3. the warps take the list 32 cars at a time (two groups per warp
-//      interleaved), so every lane draws for the same number of cars and no
-//      lane is idle; a car's gap is the count of trailing zeros of the
-//      occupancy words after its cell (vmax <= 16 < 32 cells in view);
-//   4. cars are scattered into an all -1 buffer, which leaves by one bulk
-//      store; three result buffers rotate, so the one cleared during a tile
-//      was stored two tiles earlier.
-// The rule-3 draw uses the counter-independent parts of Philox computed on
-// the host (SlowdownKey).
-constexpr uint32_t kK1Stages = 2;       // staged spans: the tile being stepped and the next one loading
-constexpr uint32_t kK1Outs = 3;         // result buffers: scattered into, being stored, being cleared
-constexpr uint32_t kK1Pad = 32;         // padding after each span buffer: the dummy car's cell and moves
-constexpr uint32_t kK1Buf = (uint32_t)kGridSpan + kK1Pad;
-constexpr uint32_t kK1ListCap = 1024;   // car-list entries; a denser tile is listed and stepped in passes
-constexpr uint32_t kK1Dummy = (uint32_t)kGridSpan;   // span index of the dummy car (empty padding)
-static_assert(kGridSpan == 32 * kGridThreads, "32 cells per thread");
+//   2. a warp prefix sum of the counts gives each lane its slots in the car
+//      list, which is padded to a multiple of 32 with a dummy car that reads
+//      and writes only padding;
+//   3. the lanes take the list 32 cars at a time, two groups interleaved, so
+//      every lane draws for the same number of cars; a car's gap is the count
+//      of trailing zeros of the occupancy words after its cell (vmax <= 16 <
+//      32 cells in view);
+//   4. cars are scattered into a buffer cleared at the start of the tile.
+// Three buffers rotate: the tile being stepped, its result, and the next
+// tile, whose copy is issued once the result buffer of the tile before has
+// been read by its store.  The rule-3 draw uses the counter-independent
+// parts of Philox computed on the host (SlowdownKey).
+constexpr uint32_t kK1Cells = 2016;                      // cells written per warp-tile
+constexpr uint32_t kK1Halo = 16;                         // cells staged on each side: vmax <= 16
+constexpr uint32_t kK1Span = kK1Cells + 2u * kK1Halo;    // staged cells: 64 per lane
+constexpr uint32_t kK1Buf = kK1Span + 32u;               // + padding: the dummy car's cell and moves
+constexpr uint32_t kK1Words = kK1Span / 32u;             // occupancy words of a span
+constexpr uint32_t kK1ListCap = 256;                     // car-list entries; a denser tile is done in passes
+constexpr uint32_t kK1Dummy = kK1Span;                   // span index of the dummy car (empty padding)
+constexpr uint32_t kK1Bufs = 3;
+constexpr int kK1Warps = 6;                              // warps per block
+static_assert(kK1Span == 64u * 32u && kK1Words == 2u * 32u, "two occupancy words per lane");
+
+struct __align__(16) K1WarpSmem {
+    int8_t buf[kK1Bufs][kK1Buf];
+    uint32_t occ[kK1Words + 3];   // occupancy words of the tile being stepped; empty words after
+    uint16_t list[kK1ListCap];
+    uint64_t full[kK1Bufs];       // bulk-copy completion, one per buffer
+};
 
 // One car: rules 1-4.  r: span index of its cell (kK1Dummy for padding);
-// returns the velocity used by the move.
+// returns the velocity used by the move and sets its cell on the road.
 template <Draw D>
 __device__ __forceinline__ uint32_t k1_car(uint32_t r, const int8_t *__restrict__ in, int8_t *__restrict__ out,
                                            const uint32_t *__restrict__ occ, uint32_t base, uint32_t L,
@@ -343,174 +358,151 @@ __device__ __forceinline__ uint32_t k1_car(uint32_t r, const int8_t *__restrict_
 }
 
 template <Draw D>
-__global__ void __launch_bounds__(kGridThreads) grid_k1_kernel(const GridStep g, const GridTileGeom geo,
-                                                               const SlowdownKey sk)
+__global__ void __launch_bounds__(32 * kK1Warps) grid_k1_kernel(const GridStep g, const uint32_t n_tiles,
+                                                                const SlowdownKey sk)
 {
-    __shared__ __align__(128) int8_t s_in[kK1Stages][kK1Buf];
-    __shared__ __align__(128) int8_t s_out[kK1Outs][kK1Buf];
-    __shared__ uint32_t s_occ[kGridThreads + 2];   // occupancy of each thread's cells; two empty words after
-    __shared__ uint16_t s_list[kK1ListCap];
-    __shared__ __align__(16) uint32_t s_warp[kGridWarps];
-    __shared__ __align__(8) uint64_t s_full[kK1Stages];
-
+    __shared__ K1WarpSmem s_w[kK1Warps];
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    K1WarpSmem &w = s_w[warp];
     const uint32_t L = g.rc.L, vmax = g.rc.vmax, thr = (uint32_t)g.rc.thr;
-    const uint32_t H = geo.halo, C = geo.tile, W = (uint32_t)kGridSpan;
-    const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
-    const uint32_t c0 = 32u * tid;                 // first span index of this thread's cells
-    // the thread that issues the copies and waits for them; its warp varies
-    // with the block, so the waits of the blocks on one SM spread over its
-    // schedulers
-    const uint32_t leader = (blockIdx.x % kGridWarps) * 32u;
+    const uint32_t nw = gridDim.x * (uint32_t)kK1Warps;
 
-    if (tid == leader) {
-        for (uint32_t b = 0; b < kK1Stages; ++b) mbar_init(&s_full[b], 1);
+    if (lane == 0) {
+        for (uint32_t b = 0; b < kK1Bufs; ++b) mbar_init(&w.full[b], 1);
         fence_mbar_init();
     }
-    for (uint32_t c = tid; c < W / 16u; c += kGridThreads) reinterpret_cast<uint4 *>(s_out[0])[c] = kEmpty4;
-    if (tid < kK1Stages * (kK1Pad / 16u)) {   // the padding the loads never write: empty cells
-        const uint32_t b = tid / (kK1Pad / 16u), q = tid % (kK1Pad / 16u);
-        reinterpret_cast<uint4 *>(s_in[b] + W)[q] = kEmpty4;
-    }
-    if (tid < 2u) s_occ[kGridThreads + tid] = 0u;
+    if (lane < 2u * kK1Bufs)   // the padding the copies never write: empty cells
+        reinterpret_cast<uint4 *>(w.buf[lane >> 1] + kK1Span)[lane & 1u] = kEmpty4;
+    if (lane < 3u) w.occ[kK1Words + lane] = 0u;
     __syncthreads();
 
-    auto bulk_ok = [&](uint32_t tile) {
-        const uint32_t t0 = tile * C;
-        return t0 >= H && t0 + C + H <= L;
+    auto bulk_ok = [&](uint32_t t) {
+        const uint32_t t0 = t * kK1Cells;
+        return t0 >= kK1Halo && t0 + kK1Cells + kK1Halo <= L;
     };
-    uint32_t tile = blockIdx.x;
-    if (tid == leader && tile < geo.n_tiles && bulk_ok(tile)) {
-        mbar_expect_tx(&s_full[0], W);
-        bulk_load(s_in[0], g.c_in + (tile * C - H), W, &s_full[0]);
-    }
-    uint32_t parity = 0;
-    bool prev_stored = false;             // the previous tile left by a bulk store (leader only)
-    uint32_t tsum = 0, tcross = 0;        // statistics of this thread's cars, reduced at the end
-    for (uint32_t it = 0; tile < geo.n_tiles; tile += gridDim.x, ++it) {
-        const uint32_t sb = it & 1u;
-        const uint32_t ob = it % kK1Outs;
-        const uint32_t cb = ob + 1u == kK1Outs ? 0u : ob + 1u;   // cleared now, scattered into by the next tile
-        const uint32_t t0 = tile * C;
-        const uint32_t own_cells = min(C, L - t0);
-        const uint32_t base = t0 >= H ? t0 - H : t0 + L - H;     // road cell of span index 0
-        int8_t *in = s_in[sb];
-        int8_t *out = s_out[ob];
-        if (tid == leader) {
-            // the other stage was read by the previous tile, which every thread has finished
-            const uint32_t ahead = tile + gridDim.x;
-            if (ahead < geo.n_tiles && bulk_ok(ahead)) {
-                fence_proxy_async();
-                mbar_expect_tx(&s_full[sb ^ 1u], W);
-                bulk_load(s_in[sb ^ 1u], g.c_in + (ahead * C - H), W, &s_full[sb ^ 1u]);
-            }
-            // buffer cb was last stored two tiles ago: that store must have read it
-            if (prev_stored) bulk_wait_read_1();
-            else bulk_wait_read_all();
-        }
+    auto issue_load = [&](uint32_t t, uint32_t b) {   // lane 0
+        fence_proxy_async();
+        mbar_expect_tx(&w.full[b], kK1Span);
+        bulk_load(w.buf[b], g.c_in + (t * kK1Cells - kK1Halo), kK1Span, &w.full[b]);
+    };
+    uint32_t tile = blockIdx.x * (uint32_t)kK1Warps + warp;
+    if (lane == 0 && tile < n_tiles && bulk_ok(tile)) issue_load(tile, 0);
+    uint32_t parity = 0;                 // bit b: phase parity of full[b]
+    uint32_t bi = 0;                     // buffer of the tile being stepped
+    uint32_t tsum = 0, tcross = 0;       // statistics of this lane's cars
+    for (; tile < n_tiles; tile += nw) {
+        const uint32_t bo = bi == 2u ? 0u : bi + 1u;   // its result
+        const uint32_t bn = bo == 2u ? 0u : bo + 1u;   // the next tile
+        const int8_t *in = w.buf[bi];
+        int8_t *out = w.buf[bo];
+        const uint32_t t0 = tile * kK1Cells;
+        const uint32_t own = min(kK1Cells, L - t0);
+        const uint32_t base = t0 >= kK1Halo ? t0 - kK1Halo : t0 + L - kK1Halo;   // road cell of span index 0
         bool ok = true;
         if (bulk_ok(tile)) {
-            if (tid == leader) ok = mbar_wait_bounded(&s_full[sb], (parity >> sb) & 1u);
-            parity ^= 1u << sb;
+            if (lane == 0) ok = mbar_wait_bounded(&w.full[bi], (parity >> bi) & 1u);
+            parity ^= 1u << bi;
         } else {
-            for (uint32_t i = tid; i < W; i += kGridThreads) {
-                uint32_t cell = base + i;
-                if (cell >= L) cell -= L;
-                in[i] = g.c_in[cell];
+            for (uint32_t i = lane; i < kK1Span; i += 32u) {
+                uint32_t c = base + i;
+                if (c >= L) c -= L;
+                w.buf[bi][i] = g.c_in[c];
             }
         }
-        if (!__syncthreads_and(ok)) {
-            if (tid == leader) {
+        if (!__all_sync(0xFFFFFFFFu, ok)) {
+            if (lane == 0) {
                 atomicOr(g.status, kStatusTimeout);
-                const uint32_t ahead = tile + gridDim.x;   // its load may still be in flight
-                if (ahead < geo.n_tiles && bulk_ok(ahead))
-                    mbar_wait_bounded(&s_full[sb ^ 1u], (parity >> (sb ^ 1u)) & 1u);
                 bulk_wait_all();
             }
-            return;
+            break;
         }
-        // 1. occupancy; clear this thread's cells of the buffer for the next tile
-        reinterpret_cast<uint4 *>(s_out[cb] + c0)[0] = kEmpty4;
-        reinterpret_cast<uint4 *>(s_out[cb] + c0)[1] = kEmpty4;
-        const uint4 *q = reinterpret_cast<const uint4 *>(in + c0);
-        const uint32_t occ = occupancy16(q[0]) | (occupancy16(q[1]) << 16);
-        s_occ[tid] = occ;
-        const uint32_t own_end = H + own_cells;   // cars from here on are not stepped
-        uint32_t mine = occ;
-        if (c0 + 32u > own_end) mine = c0 >= own_end ? 0u : mine & ((1u << (own_end - c0)) - 1u);
-        // 2. block-wide prefix sum of the car counts
-        const uint32_t n = __popc(mine);
+        __syncwarp();   // lane 0's completed wait (or the lanes' plain loads) before any lane reads the span
+        // clear the result buffer (it held the input of the tile before last)
+#pragma unroll
+        for (uint32_t k = 0; k < 4u; ++k) reinterpret_cast<uint4 *>(out)[lane + 32u * k] = kEmpty4;
+        // 1. occupancy words and the cars this lane steps
+        const uint4 *q = reinterpret_cast<const uint4 *>(in + 64u * lane);
+        const uint32_t o0 = occupancy16(q[0]) | (occupancy16(q[1]) << 16);
+        const uint32_t o1 = occupancy16(q[2]) | (occupancy16(q[3]) << 16);
+        reinterpret_cast<uint2 *>(w.occ)[lane] = make_uint2(o0, o1);
+        const uint32_t lim = kK1Halo + own;   // span indices from here on are not stepped
+        auto below = [&](uint32_t m, uint32_t c0) {   // bits of cells c0 .. c0+31 below lim
+            return c0 + 32u <= lim ? m : (c0 >= lim ? 0u : m & ((1u << (lim - c0)) - 1u));
+        };
+        const uint32_t m0 = below(o0, 64u * lane), m1 = below(o1, 64u * lane + 32u);
+        const uint32_t n = __popc(m0) + __popc(m1);
+        // 2. list slots
         uint32_t incl = n;
 #pragma unroll
         for (uint32_t d = 1; d < 32; d <<= 1) {
             const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, incl, d);
             if (lane >= d) incl += t;
         }
-        if (lane == 31u) s_warp[warp] = incl;
-        __syncthreads();
-        uint32_t before = 0, total = 0;
-#pragma unroll
-        for (uint32_t j = 0; j < kGridWarps; ++j) {
-            const uint32_t t = s_warp[j];
-            before += j < warp ? t : 0u;
-            total += t;
-        }
-        const uint32_t first_slot = before + incl - n;
-        const bool wraps = base + W + kK1Pad > L;   // the span holds cell L - 1: crossings possible
-        for (uint32_t chunk = 0; chunk < total; chunk += kK1ListCap) {
-            const uint32_t count = min(kK1ListCap, total - chunk);
+        const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+        const bool wraps = base + kK1Buf > L;   // the span holds cell L - 1: crossings possible
+        bool prefetched = false;
+        for (uint32_t chunk = 0; chunk == 0u || chunk < total; chunk += kK1ListCap) {
+            const uint32_t count = total > chunk ? min(kK1ListCap, total - chunk) : 0u;
             const uint32_t padded = (count + 31u) & ~31u;
-            uint32_t pos = first_slot;
-            if (total <= kK1ListCap) {   // block-uniform: the whole tile at once
-                for (uint32_t mm = mine; mm; mm &= mm - 1u) s_list[pos++] = (uint16_t)(c0 + __clz(__brev(mm)));
+            uint32_t pos = incl - n;
+            if (total <= kK1ListCap) {   // warp-uniform: the whole tile in one pass
+                for (uint32_t mm = m0; mm; mm &= mm - 1u) w.list[pos++] = (uint16_t)(64u * lane + __clz(__brev(mm)));
+                for (uint32_t mm = m1; mm; mm &= mm - 1u)
+                    w.list[pos++] = (uint16_t)(64u * lane + 32u + __clz(__brev(mm)));
             } else {
-                for (uint32_t mm = mine; mm; mm &= mm - 1u, ++pos)
-                    if (pos - chunk < kK1ListCap) s_list[pos - chunk] = (uint16_t)(c0 + __clz(__brev(mm)));
+                auto put = [&](uint32_t m, uint32_t c0) {
+                    for (uint32_t mm = m; mm; mm &= mm - 1u, ++pos)
+                        if (pos - chunk < kK1ListCap) w.list[pos - chunk] = (uint16_t)(c0 + __clz(__brev(mm)));
+                };
+                put(m0, 64u * lane);
+                put(m1, 64u * lane + 32u);
             }
-            if (tid < padded - count) s_list[count + tid] = (uint16_t)kK1Dummy;
-            __syncthreads();
-            // 3. groups of 32 cars: warp w takes groups w, w + 8, ...; two at a time
-            const uint32_t groups = padded >> 5;
-            for (uint32_t gi = warp; gi < groups; gi += 2u * kGridWarps) {
+            if (lane < padded - count) w.list[count + lane] = (uint16_t)kK1Dummy;
+            __syncwarp();
+            if (!prefetched) {
+                // the next tile goes into the result buffer of the tile before,
+                // once its store has read it
+                if (lane == 0) {
+                    bulk_wait_read_all();
+                    const uint32_t nx = tile + nw;
+                    if (nx < n_tiles && bulk_ok(nx)) issue_load(nx, bn);
+                }
+                prefetched = true;
+            }
+            // 3. the cars, 32 at a time, two groups interleaved
+            for (uint32_t gi = 0; gi < padded; gi += 64u) {
                 uint32_t cell0, cell1;
-                const uint32_t r0 = s_list[32u * gi + lane];
-                if (gi + kGridWarps < groups) {   // warp-uniform
-                    const uint32_t r1 = s_list[32u * (gi + kGridWarps) + lane];
-                    const uint32_t v0 = k1_car<D>(r0, in, out, s_occ, base, L, vmax, thr, sk, cell0);
-                    const uint32_t v1 = k1_car<D>(r1, in, out, s_occ, base, L, vmax, thr, sk, cell1);
-                    const bool own0 = r0 - H < own_cells, own1 = r1 - H < own_cells;
+                const uint32_t r0 = w.list[gi + lane];
+                if (gi + 32u < padded) {   // warp-uniform
+                    const uint32_t r1 = w.list[gi + 32u + lane];
+                    const uint32_t v0 = k1_car<D>(r0, in, out, w.occ, base, L, vmax, thr, sk, cell0);
+                    const uint32_t v1 = k1_car<D>(r1, in, out, w.occ, base, L, vmax, thr, sk, cell1);
+                    const bool own0 = r0 - kK1Halo < own, own1 = r1 - kK1Halo < own;
                     tsum += (own0 ? v0 : 0u) + (own1 ? v1 : 0u);
                     if (wraps) tcross += (own0 && cell0 + v0 >= L ? 1u : 0u) + (own1 && cell1 + v1 >= L ? 1u : 0u);
                 } else {
-                    const uint32_t v0 = k1_car<D>(r0, in, out, s_occ, base, L, vmax, thr, sk, cell0);
-                    const bool own0 = r0 - H < own_cells;
+                    const uint32_t v0 = k1_car<D>(r0, in, out, w.occ, base, L, vmax, thr, sk, cell0);
+                    const bool own0 = r0 - kK1Halo < own;
                     tsum += own0 ? v0 : 0u;
                     if (wraps) tcross += own0 && cell0 + v0 >= L ? 1u : 0u;
                 }
             }
-            // 4. the scattered result leaves by bulk store; the list and the
-            // occupancy words are rewritten by the next pass or tile; the
-            // stage is refilled by a bulk load
-            fence_proxy_async();
-            __syncthreads();
+            __syncwarp();   // the list is rewritten by the next pass
         }
-        if (total == 0u) {
-            fence_proxy_async();
-            __syncthreads();
-        }
-        if (own_cells == C) {
-            if (tid == leader) {
-                bulk_store(g.c_out + t0, out + H, C);
+        // 4. the result leaves by bulk store (or plain stores for a short last tile)
+        fence_proxy_async();
+        __syncwarp();
+        if (own == kK1Cells) {
+            if (lane == 0) {
+                bulk_store(g.c_out + t0, out + kK1Halo, kK1Cells);
                 bulk_commit();
-                prev_stored = true;
             }
         } else {
-            for (uint32_t i = tid; i < own_cells; i += kGridThreads) g.c_out[t0 + i] = out[H + i];
-            prev_stored = false;
+            for (uint32_t i = lane; i < own; i += 32u) g.c_out[t0 + i] = out[kK1Halo + i];
         }
+        bi = bn;
     }
-    if (tid == leader) bulk_wait_all();
-    // a thread's sums stay far below 2^32 (at most 32 cars x vmax per tile);
-    // the warp's total may not
+    if (lane == 0) bulk_wait_all();
     unsigned long long acc_sum = tsum, acc_cross = tcross;
     for (uint32_t d = 16; d >= 1; d >>= 1) {
         acc_sum += __shfl_xor_sync(0xFFFFFFFFu, acc_sum, d);
@@ -576,10 +568,28 @@ cudaError_t launch_mask_draw(const GridStep &g, const GridTileGeom &geo, int gri
 }
 
 template <Draw D>
-cudaError_t launch_k1_variant(const GridStep &g, const GridTileGeom &geo, int grid, cudaStream_t s)
+cudaError_t launch_k1_variant(const GridStep &g, uint32_t n_tiles, cudaStream_t s)
 {
+    // blocks per SM from the occupancy calculator, once per device
+    static std::atomic<int> per_sm[kMaxDevices];
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    int n = per_sm[dev].load();
+    if (n == 0) {
+        int sms = 0, b = 0;
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, grid_k1_kernel<D>, 32 * kK1Warps, 0);
+        if (e != cudaSuccess) return e;
+        n = sms * (b > 0 ? b : 1);
+        per_sm[dev].store(n);
+    }
+    const uint32_t need = (n_tiles + (uint32_t)kK1Warps - 1u) / (uint32_t)kK1Warps;
+    const int grid = (int)((uint32_t)n < need ? (uint32_t)n : need);
     const SlowdownKey sk = make_slowdown_key(g.step0, g.rc.road, g.rc.key0, g.rc.key1);
-    grid_k1_kernel<D><<<grid, kGridThreads, 0, s>>>(g, geo, sk);
+    grid_k1_kernel<D><<<grid, 32 * kK1Warps, 0, s>>>(g, n_tiles, sk);
     return cudaGetLastError();
 }
 
@@ -618,12 +628,10 @@ cudaError_t launch_grid_tiled(const GridStep &g, int blocks, cudaStream_t s)
     // the tile must own cells, and the staged span must not wrap the ring twice
     if (2u * geo.halo >= (uint32_t)kGridSpan || g.rc.L < (uint32_t)kGridSpan) return cudaErrorInvalidValue;
     if (g.ksteps == 1 && g.rc.vmax <= 16u) {
-        // 5 blocks per SM (42 KB of shared memory each) where the list kernel fits 3
-        const int kblocks = blocks * 5 / 3;
-        const int grid = (int)((uint32_t)kblocks < geo.n_tiles ? (uint32_t)kblocks : geo.n_tiles);
-        if (g.rc.thr == 0) return launch_k1_variant<Draw::kNever>(g, geo, grid, s);
-        if (g.rc.thr > 0xFFFFFFFFull) return launch_k1_variant<Draw::kAlways>(g, geo, grid, s);
-        return launch_k1_variant<Draw::kPhilox>(g, geo, grid, s);
+        const uint32_t n_tiles = (g.rc.L + kK1Cells - 1u) / kK1Cells;
+        if (g.rc.thr == 0) return launch_k1_variant<Draw::kNever>(g, n_tiles, s);
+        if (g.rc.thr > 0xFFFFFFFFull) return launch_k1_variant<Draw::kAlways>(g, n_tiles, s);
+        return launch_k1_variant<Draw::kPhilox>(g, n_tiles, s);
     }
     if (g.ksteps == 1) {
         const GridTileGeom mg = make_mask_geom(g.rc.vmax, g.rc.L);
