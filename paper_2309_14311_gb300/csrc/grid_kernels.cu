@@ -2,24 +2,24 @@
 // the car on it ("Concepts Covered": the grid representation; Handout,
 // model section rules 1-4).
 //
-// Tiled kernel.  A span of kGridSpan = 8192 cells is staged in shared
-// memory: the tile's own C = 8192 - 2H cells and a halo of H =
-// round_up(k * vmax, 16) cells on each side.  After one step a cell depends
-// on the cells within vmax of it (a car arriving from behind, the gap of
-// that car ahead), so after k fused steps the middle C cells are exact.
-// Persistent blocks walk the tiles; each span arrives by one bulk (TMA)
-// copy issued while the previous tile computes, completion counted on an
-// mbarrier, and the tile leaves by one bulk store.  Per step each of the 8
-// warps takes one 1024-cell row: lanes turn their 32 cells into an
-// occupancy bit mask, the warp compacts the row's cars into a list so the
-// draws are spread evenly over the lanes, each car's gap comes from
-// find-first-set on the masks of the cells ahead, and the car is scattered
-// into the next buffer, which was cleared to -1 one step earlier (rotating
-// buffers, one barrier per step).  Rule 2 makes the scatter collision-free.
-// Statistics of the cars that start the step in the tile's own cells are
-// reduced per warp, per block, and added to the per-step series once per
-// block.  The first and last tiles take their halo across the ring boundary
-// (modular cell index, plain loads).
+// Tiled kernels.  After one step a cell depends on the cells within vmax of
+// it (a car arriving from behind, the gap of that car ahead), so a tile
+// staged with a halo of H >= k * vmax cells on each side is exact in its
+// middle after k fused steps.  Staging is by 1-D bulk (TMA) copies into
+// shared memory, completion counted on mbarriers whose waits are bounded
+// (status word), and results leave by bulk stores.  Rule 2 makes every
+// scatter collision-free.  The first and last tiles take their halo across
+// the ring boundary (modular cell index, plain loads).
+//  - grid_tiled_kernel (k >= 2): 8192-cell spans, H = round_up(k vmax, 16);
+//    the span's cars become a sorted (position, velocity) list, k steps run
+//    on the list as in the agent form, and the list is scattered back.
+//  - grid_k1_kernel (k = 1, vmax <= 16): independent warps on 2016-cell
+//    tiles; occupancy words, a warp car list padded to whole groups of 32,
+//    gaps by trailing-zero count.
+//  - grid_mask_kernel (k = 1, vmax > 16): 1024-cell rows per warp of a
+//    block-shared 8192-cell span; gaps past the masks scanned byte by byte.
+// Statistics of the cars that start a step in a tile's own cells are
+// reduced per warp (and block) and added to the per-step series.
 //
 // Ring kernel.  For L <= kGridRingMaxCells one block holds the whole ring
 // in shared memory and runs any number of steps in one launch.
@@ -300,19 +300,22 @@ __global__ void __launch_bounds__(kGridThreads) grid_mask_kernel(const GridStep 
 // 16 halo cells on each side (2048 cells, one bulk copy on the warp's own
 // mbarrier), steps it, and writes the 2016 cells back by one bulk store.
 // Per tile:
-//   1. each lane turns 64 cells into two occupancy words, kept in shared
-//      memory for the gaps, and counts the cars it must step: those left of
-//      the right halo (a car in the right halo can only move out of the
-//      tile; one in the left halo may move in, and is stepped but not
-//      counted in the statistics);
-//   2. a warp prefix sum of the counts gives each lane its slots in the car
-//      list, which is padded to a multiple of 32 with a dummy car that reads
-//      and writes only padding;
+//   1. each lane turns 64 cells into occupancy bits and counts its cars;
+//   2. a warp prefix sum gives each lane its slots in the car list: the
+//      span indices of all cars of the span in ascending order, followed by
+//      a dummy car in the empty padding after the span, up to a multiple of
+//      32 entries and one more;
 //   3. the lanes take the list 32 cars at a time, two groups interleaved, so
-//      every lane draws for the same number of cars; a car's gap is the count
-//      of trailing zeros of the occupancy words after its cell (vmax <= 16 <
-//      32 cells in view);
+//      every lane draws for the same number of cars; a car's leader is the
+//      next list entry, so its gap is the difference of the two indices
+//      less one;
 //   4. cars are scattered into a buffer cleared at the start of the tile.
+// Only the cars the tile owns are counted in the statistics; the others
+// (halo cars, the dummy) are stepped with the rest and their results fall
+// outside the cells written back: a car in the left halo may move into the
+// tile and is stepped exactly, a car in the right halo may lack its leader
+// (beyond the span) but moves only further right.  The last owned car sees
+// its leader, or the dummy at least vmax cells ahead.
 // Three buffers rotate: the tile being stepped, its result, and the next
 // tile, whose copy is issued once the result buffer of the tile before has
 // been read by its store.  The rule-3 draw uses the counter-independent
@@ -321,39 +324,39 @@ constexpr uint32_t kK1Cells = 2016;                      // cells written per wa
 constexpr uint32_t kK1Halo = 16;                         // cells staged on each side: vmax <= 16
 constexpr uint32_t kK1Span = kK1Cells + 2u * kK1Halo;    // staged cells: 64 per lane
 constexpr uint32_t kK1Buf = kK1Span + 32u;               // + padding: the dummy car's cell and moves
-constexpr uint32_t kK1Words = kK1Span / 32u;             // occupancy words of a span
-constexpr uint32_t kK1ListCap = 256;                     // car-list entries; a denser tile is done in passes
+constexpr uint32_t kK1ListCap = 224;                     // cars per pass; a denser tile is done in passes
+constexpr uint32_t kK1ListLen = kK1ListCap + 32u;        // + padding to whole groups and one leader
 constexpr uint32_t kK1Dummy = kK1Span;                   // span index of the dummy car (empty padding)
 constexpr uint32_t kK1Bufs = 3;
 constexpr int kK1Warps = 6;                              // warps per block
-static_assert(kK1Span == 64u * 32u && kK1Words == 2u * 32u, "two occupancy words per lane");
+static_assert(kK1Span == 64u * 32u, "64 cells per lane");
+static_assert(kK1ListCap % 32u == 0u, "whole groups");
 
 struct __align__(16) K1WarpSmem {
     int8_t buf[kK1Bufs][kK1Buf];
-    uint32_t occ[kK1Words + 3];   // occupancy words of the tile being stepped; empty words after
-    uint16_t list[kK1ListCap];
+    uint16_t list[kK1ListLen];
     uint64_t full[kK1Bufs];       // bulk-copy completion, one per buffer
 };
 
-// One car: rules 1-4.  r: span index of its cell (kK1Dummy for padding);
-// returns the velocity used by the move and sets its cell on the road.
+// One car: rules 1-4.  r: span index of its cell (kK1Dummy for padding),
+// lead: its leader's; returns the velocity used by the move and sets the
+// car's cell on the road.
 template <Draw D>
-__device__ __forceinline__ uint32_t k1_car(uint32_t r, const int8_t *__restrict__ in, int8_t *__restrict__ out,
-                                           const uint32_t *__restrict__ occ, uint32_t base, uint32_t L,
-                                           uint32_t vmax, uint32_t thr, const SlowdownKey &sk, uint32_t &cell)
+__device__ __forceinline__ uint32_t k1_car(uint32_t r, uint32_t lead, const int8_t *__restrict__ in,
+                                           int8_t *__restrict__ out, uint32_t base, uint32_t L, uint32_t vmax,
+                                           uint32_t thr, const SlowdownKey &sk, uint32_t &cell)
 {
-    const uint32_t w = r >> 5;
-    const uint32_t gap = __clz(__brev(__funnelshift_rc(occ[w], occ[w + 1u], (r & 31u) + 1u)));   // empty cells ahead
-    uint32_t vel = min(min((uint32_t)(uint8_t)in[r] + 1u, vmax), gap);                             // rules 1, 2
+    const uint32_t gap = lead - r - 1u;                                                  // empty cells ahead
+    uint32_t vel = min(min((uint32_t)(uint8_t)in[r] + 1u, vmax), gap);                   // rules 1, 2
     cell = base + r;
     if (cell >= L) cell -= L;
     if (D == Draw::kAlways) {
-        vel -= vel != 0u ? 1u : 0u;                                                                  // rule 3, p = 1
+        vel -= vel != 0u ? 1u : 0u;                                                        // rule 3, p = 1
     } else if (D == Draw::kPhilox) {
         const uint32_t u = slowdown_word0(cell, sk);
-        vel -= (vel != 0u && u < thr) ? 1u : 0u;                                                     // rule 3
+        vel -= (vel != 0u && u < thr) ? 1u : 0u;                                           // rule 3
     }
-    out[r + vel] = (int8_t)vel;                                                                      // rule 4
+    out[r + vel] = (int8_t)vel;                                                            // rule 4
     return vel;
 }
 
@@ -373,7 +376,6 @@ __global__ void __launch_bounds__(32 * kK1Warps) grid_k1_kernel(const GridStep g
     }
     if (lane < 2u * kK1Bufs)   // the padding the copies never write: empty cells
         reinterpret_cast<uint4 *>(w.buf[lane >> 1] + kK1Span)[lane & 1u] = kEmpty4;
-    if (lane < 3u) w.occ[kK1Words + lane] = 0u;
     __syncthreads();
 
     auto bulk_ok = [&](uint32_t t) {
@@ -420,17 +422,11 @@ __global__ void __launch_bounds__(32 * kK1Warps) grid_k1_kernel(const GridStep g
         // clear the result buffer (it held the input of the tile before last)
 #pragma unroll
         for (uint32_t k = 0; k < 4u; ++k) reinterpret_cast<uint4 *>(out)[lane + 32u * k] = kEmpty4;
-        // 1. occupancy words and the cars this lane steps
+        // 1. this lane's cars
         const uint4 *q = reinterpret_cast<const uint4 *>(in + 64u * lane);
-        const uint32_t o0 = occupancy16(q[0]) | (occupancy16(q[1]) << 16);
-        const uint32_t o1 = occupancy16(q[2]) | (occupancy16(q[3]) << 16);
-        reinterpret_cast<uint2 *>(w.occ)[lane] = make_uint2(o0, o1);
-        const uint32_t lim = kK1Halo + own;   // span indices from here on are not stepped
-        auto below = [&](uint32_t m, uint32_t c0) {   // bits of cells c0 .. c0+31 below lim
-            return c0 + 32u <= lim ? m : (c0 >= lim ? 0u : m & ((1u << (lim - c0)) - 1u));
-        };
-        const uint32_t m0 = below(o0, 64u * lane), m1 = below(o1, 64u * lane + 32u);
-        const uint32_t n = __popc(m0) + __popc(m1);
+        const uint32_t m0 = occupancy16(q[0]) | (occupancy16(q[1]) << 16);
+        const uint32_t m1 = occupancy16(q[2]) | (occupancy16(q[3]) << 16);
+        const uint32_t n0 = __popc(m0), n = n0 + __popc(m1);
         // 2. list slots
         uint32_t incl = n;
 #pragma unroll
@@ -440,48 +436,47 @@ __global__ void __launch_bounds__(32 * kK1Warps) grid_k1_kernel(const GridStep g
         }
         const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
         const bool wraps = base + kK1Buf > L;   // the span holds cell L - 1: crossings possible
-        bool prefetched = false;
         for (uint32_t chunk = 0; chunk == 0u || chunk < total; chunk += kK1ListCap) {
             const uint32_t count = total > chunk ? min(kK1ListCap, total - chunk) : 0u;
             const uint32_t padded = (count + 31u) & ~31u;
-            uint32_t pos = incl - n;
-            if (total <= kK1ListCap) {   // warp-uniform: the whole tile in one pass
+            if (total <= kK1ListCap) {   // warp-uniform: every car in one pass
+                uint32_t pos = incl - n;
                 for (uint32_t mm = m0; mm; mm &= mm - 1u) w.list[pos++] = (uint16_t)(64u * lane + __clz(__brev(mm)));
                 for (uint32_t mm = m1; mm; mm &= mm - 1u)
                     w.list[pos++] = (uint16_t)(64u * lane + 32u + __clz(__brev(mm)));
-            } else {
+            } else {   // ranks chunk .. chunk + count (the last one: the pass's leader entry)
+                uint32_t pos = incl - n;
                 auto put = [&](uint32_t m, uint32_t c0) {
                     for (uint32_t mm = m; mm; mm &= mm - 1u, ++pos)
-                        if (pos - chunk < kK1ListCap) w.list[pos - chunk] = (uint16_t)(c0 + __clz(__brev(mm)));
+                        if (pos - chunk <= count) w.list[pos - chunk] = (uint16_t)(c0 + __clz(__brev(mm)));
                 };
                 put(m0, 64u * lane);
                 put(m1, 64u * lane + 32u);
             }
-            if (lane < padded - count) w.list[count + lane] = (uint16_t)kK1Dummy;
+            // dummies after the last car, and the leader of the last group
+            // (a pass before the last is a whole number of groups, its leader entry a car)
+            if (chunk + count == total && lane <= padded - count) w.list[count + lane] = (uint16_t)kK1Dummy;
             __syncwarp();
-            if (!prefetched) {
+            if (chunk == 0u && lane == 0) {
                 // the next tile goes into the result buffer of the tile before,
                 // once its store has read it
-                if (lane == 0) {
-                    bulk_wait_read_all();
-                    const uint32_t nx = tile + nw;
-                    if (nx < n_tiles && bulk_ok(nx)) issue_load(nx, bn);
-                }
-                prefetched = true;
+                bulk_wait_read_all();
+                const uint32_t nx = tile + nw;
+                if (nx < n_tiles && bulk_ok(nx)) issue_load(nx, bn);
             }
             // 3. the cars, 32 at a time, two groups interleaved
             for (uint32_t gi = 0; gi < padded; gi += 64u) {
                 uint32_t cell0, cell1;
-                const uint32_t r0 = w.list[gi + lane];
+                const uint32_t r0 = w.list[gi + lane], l0 = w.list[gi + lane + 1u];
                 if (gi + 32u < padded) {   // warp-uniform
-                    const uint32_t r1 = w.list[gi + 32u + lane];
-                    const uint32_t v0 = k1_car<D>(r0, in, out, w.occ, base, L, vmax, thr, sk, cell0);
-                    const uint32_t v1 = k1_car<D>(r1, in, out, w.occ, base, L, vmax, thr, sk, cell1);
+                    const uint32_t r1 = w.list[gi + 32u + lane], l1 = w.list[gi + 33u + lane];
+                    const uint32_t v0 = k1_car<D>(r0, l0, in, out, base, L, vmax, thr, sk, cell0);
+                    const uint32_t v1 = k1_car<D>(r1, l1, in, out, base, L, vmax, thr, sk, cell1);
                     const bool own0 = r0 - kK1Halo < own, own1 = r1 - kK1Halo < own;
                     tsum += (own0 ? v0 : 0u) + (own1 ? v1 : 0u);
                     if (wraps) tcross += (own0 && cell0 + v0 >= L ? 1u : 0u) + (own1 && cell1 + v1 >= L ? 1u : 0u);
                 } else {
-                    const uint32_t v0 = k1_car<D>(r0, in, out, w.occ, base, L, vmax, thr, sk, cell0);
+                    const uint32_t v0 = k1_car<D>(r0, l0, in, out, base, L, vmax, thr, sk, cell0);
                     const bool own0 = r0 - kK1Halo < own;
                     tsum += own0 ? v0 : 0u;
                     if (wraps) tcross += own0 && cell0 + v0 >= L ? 1u : 0u;
