@@ -158,7 +158,7 @@ def kernel_source_hash() -> str:
 NCU_TRAFFIC: dict[str, dict] = {
     "agent_tiled_k16": {"source_hash": "4dffaea02c8beb22", "captured_bytes": 167851776 + 122708736,
                         "scale": 4, "bytes_per_launch": 4 * (167851776 + 122708736)},
-    "grid_tiled_k1": {"source_hash": "4dffaea02c8beb22", "captured_bytes": 268537088 + 221754624,
+    "grid_k1": {"source_hash": "4dffaea02c8beb22", "captured_bytes": 268537088 + 221754624,
                       "scale": 8, "bytes_per_launch": 8 * (268537088 + 221754624)},
 }
 
@@ -342,9 +342,9 @@ def run_ours(args):
     g1.synchronize()
     s1 = timed_device_run(g1, 1, args.k1_steps)
     b1 = GRID_BYTES_PER_CELL * spec.L
-    roofline_hbm = {"bound": "hbm", "kernel": "grid_tiled_k1", "achieved": b1 * args.k1_steps / s1 / 1e9,
+    roofline_hbm = {"bound": "hbm", "kernel": "grid_k1", "achieved": b1 * args.k1_steps / s1 / 1e9,
                     "peak": hbm_peak, "unit": "GB/s", "frac": b1 * args.k1_steps / s1 / 1e9 / hbm_peak,
-                    "traffic": traffic_for("grid_tiled_k1"), "peak_source": f"{hbm_kind} hbm_gbs",
+                    "traffic": traffic_for("grid_k1"), "peak_source": f"{hbm_kind} hbm_gbs",
                     "algorithmic_bytes_per_launch": b1, "launch_ms": s1 / args.k1_steps * 1e3,
                     "vehicle_updates_per_s": spec.N * args.k1_steps / s1,
                     "cell_updates_per_s": spec.L * args.k1_steps / s1}

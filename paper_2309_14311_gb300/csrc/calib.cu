@@ -13,14 +13,18 @@ namespace {
 
 constexpr int kChains = 8;   // independent draws in flight per thread
 
+// Draws keyed as in a step: within one step (i) the counter's cell word
+// varies from draw to draw and the step word does not, so the parts of the
+// rounds that depend only on the step are shared by the kChains draws, as
+// they are by the cars of one step in the kernels.
 __global__ void __launch_bounds__(256) philox_rate_kernel(uint32_t k0, uint32_t k1, uint32_t iters,
                                                           uint32_t *sink)
 {
-    const uint32_t cell = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t cell = (blockIdx.x * blockDim.x + threadIdx.x) * (uint32_t)kChains;
     uint32_t acc = 0;
     for (uint32_t i = 0; i < iters; i += kChains) {
 #pragma unroll
-        for (int j = 0; j < kChains; ++j) acc ^= philox_word0(cell, i + (uint32_t)j, 7u, kTagSlowdown, k0, k1);
+        for (int j = 0; j < kChains; ++j) acc ^= philox_word0(cell + (uint32_t)j, i, 7u, kTagSlowdown, k0, k1);
     }
     if (acc == 0x9E3779B9u) sink[0] = acc;   // keeps the draws live; practically never taken
 }

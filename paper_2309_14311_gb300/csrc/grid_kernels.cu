@@ -10,14 +10,13 @@
 // (status word), and results leave by bulk stores.  Rule 2 makes every
 // scatter collision-free.  The first and last tiles take their halo across
 // the ring boundary (modular cell index, plain loads).
-//  - grid_tiled_kernel (k >= 2): 8192-cell spans, H = round_up(k vmax, 16);
+//  - grid_tiled_kernel (k >= 2, or vmax > 16): 8192-cell spans,
+//    H = round_up(k vmax, 16);
 //    the span's cars become a sorted (position, velocity) list, k steps run
 //    on the list as in the agent form, and the list is scattered back.
-//  - grid_k1_kernel (k = 1, vmax <= 16): independent warps on 2016-cell
-//    tiles; occupancy words, a warp car list padded to whole groups of 32,
-//    gaps by trailing-zero count.
-//  - grid_mask_kernel (k = 1, vmax > 16): 1024-cell rows per warp of a
-//    block-shared 8192-cell span; gaps past the masks scanned byte by byte.
+//  - grid_k1_kernel (k = 1, vmax <= 16): independent warps on 3040-cell
+//    tiles stepped in place; a warp car list sorted by cell, padded to whole
+//    groups of 32, gaps from the next entry.
 // Statistics of the cars that start a step in a tile's own cells are
 // reduced per warp (and block) and added to the per-step series.
 //
@@ -139,215 +138,59 @@ __global__ void __launch_bounds__(kGridThreads) grid_tiled_kernel(const GridStep
     }
 }
 
-// k = 1: the mask-step kernel.  One step per tile does not repay turning the
-// span into a list, so each warp steps its 1024-cell row directly from the
-// occupancy masks (grid_step): two staged spans, two work buffers rotating
-// with the stage, car lists of up to 512 entries per warp.
-constexpr uint32_t kMaskStages = 2;
-constexpr uint32_t kMaskListCap = 512;
-
-template <Draw D, bool kWide>
-__global__ void __launch_bounds__(kGridThreads) grid_mask_kernel(const GridStep g, const GridTileGeom geo)
-{
-    extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ __align__(8) uint64_t s_full[kMaskStages];
-    __shared__ unsigned long long s_sum[kMaxFusedSteps];
-    __shared__ unsigned long long s_cross[kMaxFusedSteps];
-    __shared__ uint16_t s_list[kGridWarps][kMaskListCap];
-
-    const RoadConst rc = g.rc;
-    const uint32_t L = rc.L;
-    const uint32_t H = geo.halo;
-    const uint32_t C = geo.tile;
-    const uint32_t W = (uint32_t)kGridSpan;
-    const uint32_t WP = geo.padded;
-    const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
-    int8_t *const pool = reinterpret_cast<int8_t *>(smem);
-    // five buffers: stages 0..2 (bulk-load targets), work 3, work 4.  A tile's
-    // steps rotate over (its stage, work a, work b): the stage is free once
-    // step 0 has read it, until it is refilled for the tile three ahead.
-    auto buf = [&](uint32_t b) { return pool + b * WP; };
-
-    for (int i = tid; i < g.ksteps; i += kGridThreads) {
-        s_sum[i] = 0ull;
-        s_cross[i] = 0ull;
-    }
-    if (tid == 0) {
-        for (uint32_t b = 0; b < kMaskStages; ++b) mbar_init(&s_full[b], 1);
-        fence_mbar_init();
-    }
-    // stage padding (never written by the loads) and both work buffers start empty
-    for (uint32_t b = 0; b < kMaskStages; ++b)
-        for (uint32_t c = W / 16u + tid; c < WP / 16u; c += kGridThreads) reinterpret_cast<uint4 *>(buf(b))[c] = kEmpty4;
-    for (uint32_t c = tid; c < 2u * WP / 16u; c += kGridThreads)
-        reinterpret_cast<uint4 *>(buf(kMaskStages))[c] = kEmpty4;
-    __syncthreads();
-
-    auto bulk_ok = [&](uint32_t tile) {
-        const uint32_t t0 = tile * C;
-        return t0 >= H && t0 + C + H <= L;
-    };
-    uint32_t parity = 0;                  // bit b: phase parity of s_full[b]
-    int clean = (int)kMaskStages;         // a work buffer known to be all -1, or -1 if none
-    uint32_t tile = blockIdx.x;
-    if (tid == 0) {
-        // the first two spans of this block
-        for (uint32_t b = 0; b + 1 < kMaskStages; ++b) {
-            const uint32_t t = tile + b * gridDim.x;
-            if (t < geo.n_tiles && bulk_ok(t)) {
-                fence_proxy_async();
-                mbar_expect_tx(&s_full[b], W);
-                bulk_load(buf(b), g.c_in + (t * C - H), W, &s_full[b]);
-            }
-        }
-    }
-    for (uint32_t it = 0; tile < geo.n_tiles; tile += gridDim.x, ++it) {
-        const uint32_t sb = it % kMaskStages;
-        const uint32_t t0 = tile * C;
-        const uint32_t own_cells = min(C, L - t0);
-        const uint32_t base = t0 >= H ? t0 - H : t0 + L - H;   // road cell of buffer index 0
-        const uint32_t ahead = tile + (kMaskStages - 1u) * gridDim.x;
-        const uint32_t ab = (it + kMaskStages - 1u) % kMaskStages;   // its stage: the one tile it-1 used
-        if (tid == 0) {
-            // earlier bulk stores must have read their source before buffers are reused
-            bulk_wait_read_all();
-            if (ahead < geo.n_tiles && bulk_ok(ahead)) {
-                fence_proxy_async();
-                mbar_expect_tx(&s_full[ab], W);
-                bulk_load(buf(ab), g.c_in + (ahead * C - H), W, &s_full[ab]);
-            }
-        }
-        int8_t *in = buf(sb);
-        bool ok = true;
-        if (bulk_ok(tile)) {
-            // one thread waits for the span; the barrier below releases the
-            // others (waiting warps would otherwise take issue slots)
-            if (tid == 0) ok = mbar_wait_bounded(&s_full[sb], (parity >> sb) & 1u);
-            parity ^= 1u << sb;
-        } else {
-            for (uint32_t i = tid; i < W; i += kGridThreads) {
-                uint32_t cell = base + i;
-                if (cell >= L) cell -= L;
-                in[i] = g.c_in[cell];
-            }
-        }
-        if (!__syncthreads_and(ok)) {
-            if (tid == 0) {
-                atomicOr(g.status, kStatusTimeout);
-                // let the loads still in flight land before the block's memory goes
-                for (uint32_t d = 1; d < kMaskStages; ++d) {
-                    const uint32_t t = tile + d * gridDim.x, b = (it + d) % kMaskStages;
-                    if (t < geo.n_tiles && bulk_ok(t)) mbar_wait_bounded(&s_full[b], (parity >> b) & 1u);
-                }
-                bulk_wait_all();
-            }
-            return;
-        }
-        // rotation (stage, wa, wb); step 0 writes wa, which must be empty
-        const uint32_t wa = clean >= 0 ? (uint32_t)clean : kMaskStages;
-        const uint32_t wb = wa == kMaskStages ? kMaskStages + 1u : kMaskStages;
-        if (clean < 0) {
-            for (uint32_t c = tid; c < WP / 16u; c += kGridThreads) reinterpret_cast<uint4 *>(buf(wa))[c] = kEmpty4;
-            __syncthreads();
-        }
-        // buffer at rotation position i (selected arithmetically: no local array)
-        auto rot = [&](uint32_t i) { return i == 0u ? sb : (i == 1u ? wa : wb); };
-        for (int s = 0; s < g.ksteps; ++s) {
-            const uint32_t i0 = (uint32_t)s % 3u;
-            const uint32_t i1 = i0 == 2u ? 0u : i0 + 1u;
-            const uint32_t i2 = i1 == 2u ? 0u : i1 + 1u;
-            uint32_t tsum = 0, tcross = 0;
-            grid_step<D, kWide, kGridCellsPerLane, kMaskListCap>(rc, buf(rot(i0)), buf(rot(i1)), buf(rot(i2)), geo,
-                                                                 own_cells, base, g.step0 + (uint32_t)s, s_list[warp],
-                                                                 tsum, tcross);
-            tsum = __reduce_add_sync(0xFFFFFFFFu, tsum);
-            tcross = __reduce_add_sync(0xFFFFFFFFu, tcross);
-            if (lane == 0 && (tsum | tcross)) {
-                atomicAdd(&s_sum[s], (unsigned long long)tsum);
-                atomicAdd(&s_cross[s], (unsigned long long)tcross);
-            }
-            // the result may leave by bulk store, and a cleared stage may be
-            // refilled by a bulk load
-            if (s + 1 == g.ksteps) fence_proxy_async();
-            __syncthreads();
-        }
-        const uint32_t k3 = (uint32_t)g.ksteps % 3u;
-        const int8_t *fin = buf(rot(k3));
-        const uint32_t cleared = rot(k3 == 2u ? 0u : k3 + 1u);   // cleared during the last step
-        clean = cleared >= kMaskStages ? (int)cleared : -1;
-
-        if (own_cells == C) {
-            if (tid == 0) {
-                bulk_store(g.c_out + t0, fin + H, C);
-                bulk_commit();
-            }
-        } else {
-            for (uint32_t i = tid; i < own_cells; i += kGridThreads) g.c_out[t0 + i] = fin[H + i];
-            // the next tile may clear or scatter into this buffer
-            __syncthreads();
-        }
-    }
-    if (tid == 0) bulk_wait_all();
-    __syncthreads();
-    for (int i = tid; i < g.ksteps; i += kGridThreads) {
-        if (s_sum[i]) atomicAdd(&g.sum_v[i], s_sum[i]);
-        if (s_cross[i]) atomicAdd(&g.crossings[i], s_cross[i]);
-    }
-}
-
 // k = 1 and vmax <= 16: the one-step kernel.  Every warp works alone (no
-// block barrier after set-up) on tiles of 2016 cells: it stages the tile with
-// 16 halo cells on each side (2048 cells, one bulk copy on the warp's own
-// mbarrier), steps it, and writes the 2016 cells back by one bulk store.
-// Per tile:
-//   1. each lane turns 64 cells into occupancy bits and counts its cars;
+// block barrier after set-up) on tiles of kK1Cells cells: it stages the tile
+// with 16 halo cells on each side (kK1Span cells, one bulk copy on the
+// warp's own mbarrier), steps it in place, and writes the tile back by one
+// bulk store.  Per tile:
+//   1. each lane turns its 32 * kK1Words cells into occupancy bits and counts
+//      its cars;
 //   2. a warp prefix sum gives each lane its slots in the car list: the
-//      span indices of all cars of the span in ascending order, followed by
-//      a dummy car in the empty padding after the span, up to a multiple of
-//      32 entries and one more;
-//   3. the lanes take the list 32 cars at a time, two groups interleaved, so
+//      span index and velocity of every car of the span in ascending order,
+//      followed by a dummy car in the padding after the span, up to a
+//      multiple of 32 entries and one more;
+//   3. with every car listed, the span is cleared to -1;
+//   4. the lanes take the list 32 cars at a time, two groups interleaved, so
 //      every lane draws for the same number of cars; a car's leader is the
 //      next list entry, so its gap is the difference of the two indices
-//      less one;
-//   4. cars are scattered into a buffer cleared at the start of the tile.
+//      less one; each car is scattered back into the span (in place).
 // Only the cars the tile owns are counted in the statistics; the others
 // (halo cars, the dummy) are stepped with the rest and their results fall
 // outside the cells written back: a car in the left halo may move into the
 // tile and is stepped exactly, a car in the right halo may lack its leader
 // (beyond the span) but moves only further right.  The last owned car sees
 // its leader, or the dummy at least vmax cells ahead.
-// Three buffers rotate: the tile being stepped, its result, and the next
-// tile, whose copy is issued once the result buffer of the tile before has
-// been read by its store.  The rule-3 draw uses the counter-independent
+// Two buffers alternate: the tile being stepped and the next tile, whose
+// copy is issued once the tile before has been read by its store.  The rule-3 draw uses the counter-independent
 // parts of Philox computed on the host (SlowdownKey).
-constexpr uint32_t kK1Cells = 2016;                      // cells written per warp-tile
+constexpr uint32_t kK1Words = 3;                         // occupancy words (32 cells each) per lane
 constexpr uint32_t kK1Halo = 16;                         // cells staged on each side: vmax <= 16
-constexpr uint32_t kK1Span = kK1Cells + 2u * kK1Halo;    // staged cells: 64 per lane
-constexpr uint32_t kK1Buf = kK1Span + 32u;               // + padding: the dummy car's cell and moves
-constexpr uint32_t kK1ListCap = 224;                     // cars per pass; a denser tile is done in passes
+constexpr uint32_t kK1Span = 1024u * kK1Words;           // staged cells
+constexpr uint32_t kK1Cells = kK1Span - 2u * kK1Halo;    // cells written per warp-tile
+constexpr uint32_t kK1Buf = kK1Span + 32u;               // + padding: the dummy car's and halo cars' moves
+constexpr uint32_t kK1ListCap = 112u * kK1Words / 32u * 32u;   // cars per pass; a denser tile is done in passes
 constexpr uint32_t kK1ListLen = kK1ListCap + 32u;        // + padding to whole groups and one leader
-constexpr uint32_t kK1Dummy = kK1Span;                   // span index of the dummy car (empty padding)
-constexpr uint32_t kK1Bufs = 3;
-constexpr int kK1Warps = 6;                              // warps per block
-static_assert(kK1Span == 64u * 32u, "64 cells per lane");
+constexpr uint32_t kK1Dummy = kK1Span;                   // span index of the dummy car (padding), velocity 0
+constexpr uint32_t kK1Bufs = 2;
+constexpr int kK1Warps = 4;                              // warps per block
 static_assert(kK1ListCap % 32u == 0u, "whole groups");
 
 struct __align__(16) K1WarpSmem {
     int8_t buf[kK1Bufs][kK1Buf];
-    uint16_t list[kK1ListLen];
+    uint32_t list[kK1ListLen];    // span index | velocity << 16
     uint64_t full[kK1Bufs];       // bulk-copy completion, one per buffer
 };
 
-// One car: rules 1-4.  r: span index of its cell (kK1Dummy for padding),
-// lead: its leader's; returns the velocity used by the move and sets the
-// car's cell on the road.
+// One car: rules 1-4.  e: its list entry (span index | velocity << 16),
+// lead: the leader's entry; returns the velocity used by the move and sets
+// the car's cell on the road.
 template <Draw D>
-__device__ __forceinline__ uint32_t k1_car(uint32_t r, uint32_t lead, const int8_t *__restrict__ in,
-                                           int8_t *__restrict__ out, uint32_t base, uint32_t L, uint32_t vmax,
-                                           uint32_t thr, const SlowdownKey &sk, uint32_t &cell)
+__device__ __forceinline__ uint32_t k1_car(uint32_t e, uint32_t lead, int8_t *span, uint32_t base, uint32_t L,
+                                           uint32_t vmax, uint32_t thr, const SlowdownKey &sk, uint32_t &cell)
 {
-    const uint32_t gap = lead - r - 1u;                                                  // empty cells ahead
-    uint32_t vel = min(min((uint32_t)(uint8_t)in[r] + 1u, vmax), gap);                   // rules 1, 2
+    const uint32_t r = e & 0xFFFFu;
+    const uint32_t gap = (lead & 0xFFFFu) - r - 1u;                                      // empty cells ahead
+    uint32_t vel = min(min((e >> 16) + 1u, vmax), gap);                                 // rules 1, 2
     cell = base + r;
     if (cell >= L) cell -= L;
     if (D == Draw::kAlways) {
@@ -356,7 +199,7 @@ __device__ __forceinline__ uint32_t k1_car(uint32_t r, uint32_t lead, const int8
         const uint32_t u = slowdown_word0(cell, sk);
         vel -= (vel != 0u && u < thr) ? 1u : 0u;                                           // rule 3
     }
-    out[r + vel] = (int8_t)vel;                                                            // rule 4
+    span[r + vel] = (int8_t)vel;                                                           // rule 4
     return vel;
 }
 
@@ -374,8 +217,6 @@ __global__ void __launch_bounds__(32 * kK1Warps) grid_k1_kernel(const GridStep g
         for (uint32_t b = 0; b < kK1Bufs; ++b) mbar_init(&w.full[b], 1);
         fence_mbar_init();
     }
-    if (lane < 2u * kK1Bufs)   // the padding the copies never write: empty cells
-        reinterpret_cast<uint4 *>(w.buf[lane >> 1] + kK1Span)[lane & 1u] = kEmpty4;
     __syncthreads();
 
     auto bulk_ok = [&](uint32_t t) {
@@ -393,10 +234,8 @@ __global__ void __launch_bounds__(32 * kK1Warps) grid_k1_kernel(const GridStep g
     uint32_t bi = 0;                     // buffer of the tile being stepped
     uint32_t tsum = 0, tcross = 0;       // statistics of this lane's cars
     for (; tile < n_tiles; tile += nw) {
-        const uint32_t bo = bi == 2u ? 0u : bi + 1u;   // its result
-        const uint32_t bn = bo == 2u ? 0u : bo + 1u;   // the next tile
-        const int8_t *in = w.buf[bi];
-        int8_t *out = w.buf[bo];
+        const uint32_t bn = bi ^ 1u;     // the other buffer: the next tile, or a dense tile's result
+        int8_t *span = w.buf[bi];
         const uint32_t t0 = tile * kK1Cells;
         const uint32_t own = min(kK1Cells, L - t0);
         const uint32_t base = t0 >= kK1Halo ? t0 - kK1Halo : t0 + L - kK1Halo;   // road cell of span index 0
@@ -408,7 +247,7 @@ __global__ void __launch_bounds__(32 * kK1Warps) grid_k1_kernel(const GridStep g
             for (uint32_t i = lane; i < kK1Span; i += 32u) {
                 uint32_t c = base + i;
                 if (c >= L) c -= L;
-                w.buf[bi][i] = g.c_in[c];
+                span[i] = g.c_in[c];
             }
         }
         if (!__all_sync(0xFFFFFFFFu, ok)) {
@@ -419,14 +258,16 @@ __global__ void __launch_bounds__(32 * kK1Warps) grid_k1_kernel(const GridStep g
             break;
         }
         __syncwarp();   // lane 0's completed wait (or the lanes' plain loads) before any lane reads the span
-        // clear the result buffer (it held the input of the tile before last)
+        // 1. this lane's cars: occupancy of its 32 * kK1Words cells
+        const uint32_t c0 = 32u * kK1Words * lane;
+        const uint4 *q = reinterpret_cast<const uint4 *>(span + c0);
+        uint32_t m[kK1Words];
+        uint32_t n = 0;
 #pragma unroll
-        for (uint32_t k = 0; k < 4u; ++k) reinterpret_cast<uint4 *>(out)[lane + 32u * k] = kEmpty4;
-        // 1. this lane's cars
-        const uint4 *q = reinterpret_cast<const uint4 *>(in + 64u * lane);
-        const uint32_t m0 = occupancy16(q[0]) | (occupancy16(q[1]) << 16);
-        const uint32_t m1 = occupancy16(q[2]) | (occupancy16(q[3]) << 16);
-        const uint32_t n0 = __popc(m0), n = n0 + __popc(m1);
+        for (uint32_t j = 0; j < kK1Words; ++j) {
+            m[j] = occupancy16(q[2u * j]) | (occupancy16(q[2u * j + 1u]) << 16);
+            n += __popc(m[j]);
+        }
         // 2. list slots
         uint32_t incl = n;
 #pragma unroll
@@ -436,55 +277,70 @@ __global__ void __launch_bounds__(32 * kK1Warps) grid_k1_kernel(const GridStep g
         }
         const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
         const bool wraps = base + kK1Buf > L;   // the span holds cell L - 1: crossings possible
+        // a tile with more cars than the list holds is listed in passes from
+        // the intact span, so its result goes to the other buffer (once the
+        // store of the tile before has read it) and the next copy waits
+        const bool dense = total > kK1ListCap;   // warp-uniform
+        int8_t *out = span;
+        if (dense) {
+            if (lane == 0) bulk_wait_read_all();
+            __syncwarp();
+            out = w.buf[bn];
+#pragma unroll
+            for (uint32_t k = 0; k < 2u * kK1Words; ++k) reinterpret_cast<uint4 *>(out)[lane + 32u * k] = kEmpty4;
+        }
+        auto entry = [&](uint32_t r) { return r | (uint32_t)(uint8_t)span[r] << 16; };
         for (uint32_t chunk = 0; chunk == 0u || chunk < total; chunk += kK1ListCap) {
             const uint32_t count = total > chunk ? min(kK1ListCap, total - chunk) : 0u;
             const uint32_t padded = (count + 31u) & ~31u;
-            if (total <= kK1ListCap) {   // warp-uniform: every car in one pass
-                uint32_t pos = incl - n;
-                for (uint32_t mm = m0; mm; mm &= mm - 1u) w.list[pos++] = (uint16_t)(64u * lane + __clz(__brev(mm)));
-                for (uint32_t mm = m1; mm; mm &= mm - 1u)
-                    w.list[pos++] = (uint16_t)(64u * lane + 32u + __clz(__brev(mm)));
+            uint32_t pos = incl - n;
+            if (!dense) {
+#pragma unroll
+                for (uint32_t j = 0; j < kK1Words; ++j)
+                    for (uint32_t mm = m[j]; mm; mm &= mm - 1u) w.list[pos++] = entry(c0 + 32u * j + __clz(__brev(mm)));
             } else {   // ranks chunk .. chunk + count (the last one: the pass's leader entry)
-                uint32_t pos = incl - n;
-                auto put = [&](uint32_t m, uint32_t c0) {
-                    for (uint32_t mm = m; mm; mm &= mm - 1u, ++pos)
-                        if (pos - chunk <= count) w.list[pos - chunk] = (uint16_t)(c0 + __clz(__brev(mm)));
-                };
-                put(m0, 64u * lane);
-                put(m1, 64u * lane + 32u);
+#pragma unroll
+                for (uint32_t j = 0; j < kK1Words; ++j)
+                    for (uint32_t mm = m[j]; mm; mm &= mm - 1u, ++pos)
+                        if (pos - chunk <= count) w.list[pos - chunk] = entry(c0 + 32u * j + __clz(__brev(mm)));
             }
             // dummies after the last car, and the leader of the last group
             // (a pass before the last is a whole number of groups, its leader entry a car)
-            if (chunk + count == total && lane <= padded - count) w.list[count + lane] = (uint16_t)kK1Dummy;
+            if (chunk + count == total && lane <= padded - count) w.list[count + lane] = kK1Dummy;
             __syncwarp();
-            if (chunk == 0u && lane == 0) {
-                // the next tile goes into the result buffer of the tile before,
-                // once its store has read it
-                bulk_wait_read_all();
-                const uint32_t nx = tile + nw;
-                if (nx < n_tiles && bulk_ok(nx)) issue_load(nx, bn);
+            if (!dense) {
+                // 3. every car is listed: clear the span, and copy the next tile
+                // into the other buffer once the store of the tile before has read it
+#pragma unroll
+                for (uint32_t k = 0; k < 2u * kK1Words; ++k) reinterpret_cast<uint4 *>(span)[lane + 32u * k] = kEmpty4;
+                if (lane == 0) {
+                    bulk_wait_read_all();
+                    const uint32_t nx = tile + nw;
+                    if (nx < n_tiles && bulk_ok(nx)) issue_load(nx, bn);
+                }
+                __syncwarp();
             }
-            // 3. the cars, 32 at a time, two groups interleaved
+            // 4. the cars, 32 at a time, two groups interleaved
             for (uint32_t gi = 0; gi < padded; gi += 64u) {
                 uint32_t cell0, cell1;
-                const uint32_t r0 = w.list[gi + lane], l0 = w.list[gi + lane + 1u];
+                const uint32_t e0 = w.list[gi + lane], l0 = w.list[gi + lane + 1u];
                 if (gi + 32u < padded) {   // warp-uniform
-                    const uint32_t r1 = w.list[gi + 32u + lane], l1 = w.list[gi + 33u + lane];
-                    const uint32_t v0 = k1_car<D>(r0, l0, in, out, base, L, vmax, thr, sk, cell0);
-                    const uint32_t v1 = k1_car<D>(r1, l1, in, out, base, L, vmax, thr, sk, cell1);
-                    const bool own0 = r0 - kK1Halo < own, own1 = r1 - kK1Halo < own;
+                    const uint32_t e1 = w.list[gi + 32u + lane], l1 = w.list[gi + 33u + lane];
+                    const uint32_t v0 = k1_car<D>(e0, l0, out, base, L, vmax, thr, sk, cell0);
+                    const uint32_t v1 = k1_car<D>(e1, l1, out, base, L, vmax, thr, sk, cell1);
+                    const bool own0 = (e0 & 0xFFFFu) - kK1Halo < own, own1 = (e1 & 0xFFFFu) - kK1Halo < own;
                     tsum += (own0 ? v0 : 0u) + (own1 ? v1 : 0u);
                     if (wraps) tcross += (own0 && cell0 + v0 >= L ? 1u : 0u) + (own1 && cell1 + v1 >= L ? 1u : 0u);
                 } else {
-                    const uint32_t v0 = k1_car<D>(r0, l0, in, out, base, L, vmax, thr, sk, cell0);
-                    const bool own0 = r0 - kK1Halo < own;
+                    const uint32_t v0 = k1_car<D>(e0, l0, out, base, L, vmax, thr, sk, cell0);
+                    const bool own0 = (e0 & 0xFFFFu) - kK1Halo < own;
                     tsum += own0 ? v0 : 0u;
                     if (wraps) tcross += own0 && cell0 + v0 >= L ? 1u : 0u;
                 }
             }
             __syncwarp();   // the list is rewritten by the next pass
         }
-        // 4. the result leaves by bulk store (or plain stores for a short last tile)
+        // 5. the result leaves by bulk store (or plain stores for a short last tile)
         fence_proxy_async();
         __syncwarp();
         if (own == kK1Cells) {
@@ -495,7 +351,14 @@ __global__ void __launch_bounds__(32 * kK1Warps) grid_k1_kernel(const GridStep g
         } else {
             for (uint32_t i = lane; i < own; i += 32u) g.c_out[t0 + i] = out[kK1Halo + i];
         }
-        bi = bn;
+        if (dense) {   // the span is free: the next tile goes there
+            if (lane == 0) {
+                const uint32_t nx = tile + nw;
+                if (nx < n_tiles && bulk_ok(nx)) issue_load(nx, bi);
+            }
+        } else {
+            bi = bn;
+        }
     }
     if (lane == 0) bulk_wait_all();
     unsigned long long acc_sum = tsum, acc_cross = tcross;
@@ -533,34 +396,6 @@ GridTileGeom make_geom(int ksteps, uint32_t vmax, uint32_t L)
 
 // two stages, two outputs, and the car list (uint16 position + uint8 velocity)
 size_t grid_tiled_smem(const GridTileGeom &geo) { return 4u * (size_t)geo.padded + 3u * (size_t)kGridListCap; }
-
-// the mask-step kernel reads past the span (look-ahead) and scatters up to
-// vmax cells past it: padded buffers, two stages and two work buffers
-GridTileGeom make_mask_geom(uint32_t vmax, uint32_t L)
-{
-    GridTileGeom geo = make_geom(1, vmax, L);
-    geo.padded = (uint32_t)kGridSpan + 16u * ((vmax + 15u) / 16u + 2u);
-    return geo;
-}
-size_t grid_mask_smem(const GridTileGeom &geo) { return 4u * (size_t)geo.padded; }
-
-template <Draw D, bool kWide>
-cudaError_t launch_mask_variant(const GridStep &g, const GridTileGeom &geo, int grid, size_t smem, cudaStream_t s)
-{
-    cudaError_t e = cudaFuncSetAttribute(grid_mask_kernel<D, kWide>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    grid_mask_kernel<D, kWide><<<grid, kGridThreads, smem, s>>>(g, geo);
-    return cudaGetLastError();
-}
-
-template <bool kWide>
-cudaError_t launch_mask_draw(const GridStep &g, const GridTileGeom &geo, int grid, size_t smem, cudaStream_t s)
-{
-    if (g.rc.thr == 0) return launch_mask_variant<Draw::kNever, kWide>(g, geo, grid, smem, s);
-    if (g.rc.thr > 0xFFFFFFFFull) return launch_mask_variant<Draw::kAlways, kWide>(g, geo, grid, smem, s);
-    return launch_mask_variant<Draw::kPhilox, kWide>(g, geo, grid, smem, s);
-}
 
 template <Draw D>
 cudaError_t launch_k1_variant(const GridStep &g, uint32_t n_tiles, cudaStream_t s)
@@ -627,14 +462,6 @@ cudaError_t launch_grid_tiled(const GridStep &g, int blocks, cudaStream_t s)
         if (g.rc.thr == 0) return launch_k1_variant<Draw::kNever>(g, n_tiles, s);
         if (g.rc.thr > 0xFFFFFFFFull) return launch_k1_variant<Draw::kAlways>(g, n_tiles, s);
         return launch_k1_variant<Draw::kPhilox>(g, n_tiles, s);
-    }
-    if (g.ksteps == 1) {
-        const GridTileGeom mg = make_mask_geom(g.rc.vmax, g.rc.L);
-        const size_t msmem = grid_mask_smem(mg);
-        const int mblocks = blocks * 5 / 3;   // the mask kernel fits 5 blocks per SM where the list kernel fits 3
-        const int grid = (int)((uint32_t)mblocks < mg.n_tiles ? (uint32_t)mblocks : mg.n_tiles);
-        return g.rc.vmax > 16u ? launch_mask_draw<true>(g, mg, grid, msmem, s)
-                               : launch_mask_draw<false>(g, mg, grid, msmem, s);
     }
     const size_t smem = grid_tiled_smem(geo);
     const int grid = (int)((uint32_t)blocks < geo.n_tiles ? (uint32_t)blocks : geo.n_tiles);

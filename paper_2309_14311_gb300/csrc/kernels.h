@@ -24,11 +24,11 @@ constexpr int kAgentTileSpanSmall = 32 * 8;
 // Whole-ring agent kernel: one block of up to 1024 threads x 8 cars.
 constexpr int kAgentRingMaxCars = 1024 * 8;
 
-// Grid tiled kernel: a span of kGridSpan cells staged per tile = the tile's
-// own kGridSpan - 2H cells plus a halo of H = round_up(k * vmax, 16) cells on
-// each side; 8 warps, one 1024-cell row each (32 cells per lane).
+// Grid tiled kernel (k >= 2): a span of kGridSpan cells staged per tile =
+// the tile's own kGridSpan - 2H cells plus a halo of H = round_up(k * vmax,
+// 16) cells on each side; 256 threads, 32 cells each.  (The one-step kernel
+// has tiles of its own.)
 constexpr int kGridThreads = 256;
-constexpr int kGridCellsPerLane = 32;
 constexpr int kGridSpan = 8192;
 constexpr int kGridTileCells = kGridSpan;   // the `tile` parameter value that selects the tiled kernel
 

@@ -243,134 +243,6 @@ struct GridTileGeom {
     uint32_t nwork;     // rotating output buffers: 2 for k = 1, else 3
 };
 
-// One synchronous step over a staged span: read `cur`, scatter every car
-// into `nxt` (already all -1), and clear `clr` for the step after.  The span
-// is cut into rows of 32 * CPL cells, one per warp (the block has
-// kGridSpan / (32 * CPL) warps): each lane turns its CPL cells into an
-// occupancy mask, the warp compacts the row's cars into a list of cell
-// indices, and the lanes then take the cars of the list in turn, so that
-// every lane applies rules 1-4 to the same number of cars (a lane's own
-// cells hold 0..CPL cars).  A car's gap comes from its owner lane's mask and
-// the next lane's mask (shuffles) by a shift and find-first-set.
-// kWide: vmax > 16, gaps may reach past the two masks.
-// kListCap: entries of the warp's car list; a row with more cars is done in
-// several passes over its masks.
-template <Draw D, bool kWide, int CPL, uint32_t kListCap = 32u * CPL>
-__device__ __forceinline__ void grid_step(const RoadConst &rc, const int8_t *__restrict__ cur, int8_t *nxt,
-                                          int8_t *clr, const GridTileGeom &geo, uint32_t own_cells, uint32_t base,
-                                          uint32_t step, uint16_t *list, uint32_t &tsum, uint32_t &tcross)
-{
-    static_assert(CPL == 16 || CPL == 32, "16 or 32 cells per lane");
-    constexpr uint32_t kRow = 32u * CPL;
-    constexpr uint32_t kWarps = (uint32_t)kGridSpan / kRow;
-    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
-    const uint32_t row0 = warp * kRow;
-    const uint32_t H = geo.halo;
-    const uint32_t L = rc.L;
-
-    uint4 *clr4 = reinterpret_cast<uint4 *>(clr + row0);
-    clr4[lane] = kEmpty4;
-    if (CPL == 32) clr4[lane + 32] = kEmpty4;
-    if (warp == kWarps - 1)
-        for (uint32_t c = lane; c < (geo.padded - (uint32_t)kGridSpan) / 16u; c += 32u)
-            reinterpret_cast<uint4 *>(clr + kGridSpan)[c] = kEmpty4;
-
-    const uint4 *mine = reinterpret_cast<const uint4 *>(cur + row0 + CPL * lane);
-    // every lane also reads the chunk after its own cells: cheaper than a
-    // branch for the one lane (31) whose next cells belong to the next row
-    uint32_t m, m_next;
-    if (CPL == 32) {
-        m = occupancy16(mine[0]) | (occupancy16(mine[1]) << 16);
-        const uint32_t beyond = occupancy16(mine[2]);   // first 16 cells after (the next row, or padding)
-        m_next = __shfl_down_sync(0xFFFFFFFFu, m, 1);
-        if (lane == 31) m_next = beyond;
-    } else {
-        m = occupancy16(mine[0]);
-        const uint32_t beyond = occupancy16(mine[1]);
-        m_next = __shfl_down_sync(0xFFFFFFFFu, m, 1);
-        if (lane == 31) m_next = beyond;
-    }
-    const uint32_t n = __popc(m);
-    uint32_t incl = n;
-#pragma unroll
-    for (uint32_t d = 1; d < 32; d <<= 1) {
-        const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, incl, d);
-        if (lane >= d) incl += t;
-    }
-    const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
-    if (total == 0) return;
-
-    // one car: rules 1-4 from its row index r and its owner lane's masks;
-    // computed without branches (an idle lane computes a dummy car and does
-    // not store), so two cars per lane interleave
-    auto car = [&](bool active, uint32_t r, uint32_t wm, uint32_t wn) {
-        const uint32_t bit = r & (CPL - 1u);
-        const uint32_t src = CPL == 32 ? r >> 5 : r >> 4;
-        const uint32_t after = CPL == 32 ? __funnelshift_rc(wm, wn, bit + 1u) : (wm | (wn << 16)) >> (bit + 1u);
-        // with vmax <= 16 the masks always cover the cells a gap can need
-        uint32_t gap = after ? (uint32_t)(__ffs(after) - 1) : 32u;
-        const uint32_t idx = row0 + r;
-        if (kWide && active) {
-            // the masks know the next 32 cells (16 fewer for the row's last
-            // lane; 31 - bit with 16 cells per lane); past them, scan the bytes
-            uint32_t known = CPL == 32 ? (src == 31u ? 47u - bit : 32u) : 31u - bit;
-            if (gap > known) gap = known;
-            while (gap == known && gap < rc.vmax) {
-                if (cur[idx + 1u + gap] >= 0) break;
-                ++gap;
-                ++known;
-            }
-        }
-        uint32_t cell = base + idx;
-        if (cell >= L) cell -= L;
-        uint32_t vel = min(min((uint32_t)(uint8_t)cur[idx] + 1u, rc.vmax), gap);   // rules 1, 2
-        if (D == Draw::kAlways) {
-            vel -= vel > 0u ? 1u : 0u;                                              // rule 3, p = 1
-        } else if (D == Draw::kPhilox) {
-            const uint32_t u = philox_word0(cell, step, rc.road, kTagSlowdown, rc.key0, rc.key1);
-            vel -= (vel > 0u && u < (uint32_t)rc.thr) ? 1u : 0u;                    // rule 3
-        }
-        if (active) {
-            nxt[idx + vel] = (int8_t)vel;                                           // rule 4
-            if (idx - H < own_cells) {
-                tsum += vel;
-                tcross += (cell + vel >= L) ? 1u : 0u;
-            }
-        }
-    };
-    constexpr uint32_t kShift = CPL == 32 ? 5u : 4u;
-    for (uint32_t chunk = 0; chunk < total; chunk += kListCap) {
-        // list the cars of ranks [chunk, chunk + kListCap) of the row
-        uint32_t pos = incl - n;
-        if (total <= kListCap) {   // warp-uniform: the whole row in one pass
-            for (uint32_t mm = m; mm; mm &= mm - 1u) list[pos++] = (uint16_t)(CPL * lane + (uint32_t)(__ffs(mm) - 1));
-        } else if (pos < chunk + kListCap && pos + n > chunk) {
-            for (uint32_t mm = m; mm; mm &= mm - 1u, ++pos)
-                if (pos >= chunk && pos < chunk + kListCap)
-                    list[pos - chunk] = (uint16_t)(CPL * lane + (uint32_t)(__ffs(mm) - 1));
-        }
-        __syncwarp();
-        const uint32_t count = min(kListCap, total - chunk);
-        for (uint32_t first = 0; first < count; first += 64u) {
-            const uint32_t i0 = first + lane, i1 = i0 + 32u;
-            const bool a0 = i0 < count, a1 = i1 < count;
-            const uint32_t r0 = a0 ? (uint32_t)list[i0] : 0u;
-            const uint32_t wm0 = __shfl_sync(0xFFFFFFFFu, m, r0 >> kShift);
-            const uint32_t wn0 = __shfl_sync(0xFFFFFFFFu, m_next, r0 >> kShift);
-            if (first + 32u < count) {   // warp-uniform: a second car for (some) lanes
-                const uint32_t r1 = a1 ? (uint32_t)list[i1] : 0u;
-                const uint32_t wm1 = __shfl_sync(0xFFFFFFFFu, m, r1 >> kShift);
-                const uint32_t wn1 = __shfl_sync(0xFFFFFFFFu, m_next, r1 >> kShift);
-                car(a0, r0, wm0, wn0);
-                car(a1, r1, wm1, wn1);
-            } else {
-                car(a0, r0, wm0, wn0);
-            }
-        }
-        __syncwarp();   // the list is rewritten by the next pass or step
-    }
-}
-
 // The span-list method of a grid tile (used when the staged span's cars fit
 // the list): the cars of the staged span `in` become a list sorted by
 // position (cell index within the span, velocity); k synchronous steps are
