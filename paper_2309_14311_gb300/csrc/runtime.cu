@@ -378,9 +378,7 @@ int nasch_create_ex(const nasch_params *prm, nasch_handle *out)
         }
         h->ring = prm->tile == 0 && h->L <= kGridRingMaxCells;
         h->tile = kGridTileCells;
-        // one step per launch is fastest where the one-step kernel applies
-        // (vmax <= 16); otherwise 8 steps fused on the span list
-        h->k = prm->k ? prm->k : (h->vmax <= 16 ? 1 : 8);
+        h->k = prm->k ? prm->k : 8;
         // the halo round_up(k * vmax, 16) on each side must leave the tile cells
         // of its own: clamp k so that 2 * halo < the staged span
         const int kfit = h->vmax > 0 ? std::max(1, ((kGridSpan / 2 - 16) / h->vmax)) : kMaxFusedSteps;
