@@ -83,13 +83,20 @@ void plan_road(const nasch_params &p, int64_t T, double rho_star, int k_agent, i
             k = p.k ? p.k : kRingK;
             *n_items = 1;
         } else {
-            rd.type = kBatchGridTile;
             k = p.k ? p.k : k_grid;
             const int kfit = p.vmax > 0 ? std::max(1, (kGridSpan / 2 - 16) / p.vmax) : kMaxFusedSteps;
             k = std::min(k, kfit);
             rd.halo = grid_halo(k, (uint32_t)p.vmax);
-            rd.tile = (uint32_t)kGridSpan - 2u * rd.halo;
-            *n_items = (p.L + rd.tile - 1) / rd.tile;
+            if (rd.halo <= kKwMaxHalo) {   // warp-tiles of the list method
+                rd.type = kBatchGridWarp;
+                rd.tile = kKwSpan - 2u * rd.halo;
+                const int64_t per_item = (int64_t)rd.tile * (kBatchThreads / 32);
+                *n_items = (p.L + per_item - 1) / per_item;
+            } else {                       // one block-wide span per item
+                rd.type = kBatchGridTile;
+                rd.tile = (uint32_t)kGridSpan - 2u * rd.halo;
+                *n_items = (p.L + rd.tile - 1) / rd.tile;
+            }
         }
     }
     rd.k = (uint32_t)k;

@@ -15,6 +15,7 @@ enum BatchType : uint32_t {
     kBatchGridTile = 1,    // grid layout, one staged 8192-cell span per item
     kBatchAgentRing = 2,   // agent layout, N <= 2048: the whole ring in one item
     kBatchGridRing = 3,    // grid layout, L <= 8192: the whole ring in one item
+    kBatchGridWarp = 4,    // grid layout, H <= 512: 8 warp-tiles of 2048 staged cells per item (list method)
 };
 
 constexpr int kBatchThreads = 256;
@@ -33,7 +34,8 @@ struct BatchRoadDev {
     uint32_t sbase;                    // the road's super-step at launch super_step 0 (serving; 0 in batches)
     uint32_t pad0;
     uint32_t halo;                     // grid: H cells per side; agent: halo cars per warp-tile
-    uint32_t tile;                     // grid: owned cells per item; agent: owned cars per warp-tile
+    uint32_t tile;                     // grid: owned cells per item (per warp-tile for kBatchGridWarp);
+                                       // agent: owned cars per warp-tile
     int32_t *x[2];
     uint8_t *v[2];
     int8_t *cells[2];

@@ -7,8 +7,12 @@
 //   agent tile: 16 warp-tiles of 256 consecutive cars, two per warp (32 lanes
 //               x 8 cars in registers, leader by warp shuffle, halo of
 //               round_up(k, 8));
-//   grid tile:  one staged 8192-cell span (tile + halos of round_up(k*vmax,16)),
-//               stepped as a list of its cars (the span-list method);
+//   grid warp:  8 warp-tiles, one per warp, of 2048 staged cells (tile + halos
+//               of round_up(k*vmax,16) <= 512), each stepped by its warp alone
+//               as a list of its cars (the list method of the single-road
+//               fused kernel);
+//   grid tile:  one staged 8192-cell span for larger halos, stepped as a list
+//               of its cars by the whole block (the span-list method);
 //   agent ring: a whole ring of N <= 2048 cars in one block;
 //   grid ring:  a whole ring of L <= 8192 cells in shared memory.
 // The step code is the single-road kernels' (tile_device.cuh), so a road in
@@ -98,6 +102,54 @@ __device__ __forceinline__ void batch_grid_tile(const BatchRoadDev &rd, const Ro
     }
 }
 
+// Per warp: its staged span, and the list of the span's cars.
+struct BatchWarpSmem {
+    int8_t span[kKwBuf];
+    uint16_t pos[kKwList];
+    uint8_t vel[kKwList];
+};
+
+template <Draw D>
+__device__ __forceinline__ void batch_grid_warp(const BatchRoadDev &rd, const RoadConst &rc, uint32_t item_tile,
+                                                uint32_t par, uint32_t step0, int kk, int8_t *pool,
+                                                unsigned long long *s_sum, unsigned long long *s_cross)
+{
+    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+    BatchWarpSmem &w = reinterpret_cast<BatchWarpSmem *>(pool)[warp];
+    const uint32_t L = rd.L, H = rd.halo, C = rd.tile;
+    const int8_t *c_in = par ? rd.cells[1] : rd.cells[0];
+    int8_t *c_out = par ? rd.cells[0] : rd.cells[1];
+    const uint32_t t0 = (item_tile * (uint32_t)(kBatchThreads / 32) + warp) * C;
+    if (t0 >= L) return;
+    const uint32_t own = min(C, L - t0);
+    const uint32_t base = t0 >= H ? t0 - H : t0 + L - H;
+    if (t0 >= H && t0 + C + H <= L) {
+        const uint4 *src = reinterpret_cast<const uint4 *>(c_in + (t0 - H));
+#pragma unroll
+        for (uint32_t k = 0; k < kKwSpan / 512u; ++k)
+            reinterpret_cast<uint4 *>(w.span)[lane + 32u * k] = __ldg(src + lane + 32u * k);
+    } else {
+        for (uint32_t i = lane; i < kKwSpan; i += 32u) {
+            uint32_t c = base + i;
+            if (c >= L) c -= L;
+            w.span[i] = c_in[c];
+        }
+    }
+    __syncwarp();
+    grid_warp_steps<D>(rc, w.span, w.pos, w.vel, H, own, base, step0, kk, []() {},
+                       [&](int s, uint32_t sum, uint32_t cross) {
+                           if (sum) atomicAdd(&s_sum[s], (unsigned long long)sum);
+                           if (cross) atomicAdd(&s_cross[s], (unsigned long long)cross);
+                       });
+    if (own == C) {
+        const uint4 *f4 = reinterpret_cast<const uint4 *>(w.span + H);
+        uint4 *dst = reinterpret_cast<uint4 *>(c_out + t0);
+        for (uint32_t c = lane; c < C / 16u; c += 32u) dst[c] = f4[c];
+    } else {
+        for (uint32_t i = lane; i < own; i += 32u) c_out[t0 + i] = w.span[H + i];
+    }
+}
+
 template <Draw D>
 __device__ __forceinline__ void batch_item(const BatchRoadDev &rd, const RoadConst &rc, uint32_t item_tile,
                                            uint32_t par, uint32_t step0, int kk, uint32_t padded, int8_t *pool,
@@ -107,6 +159,9 @@ __device__ __forceinline__ void batch_item(const BatchRoadDev &rd, const RoadCon
     switch (rd.type) {
     case kBatchAgentTile:
         batch_agent_tile<D>(rd, rc, item_tile, par, step0, kk, s_sum, s_cross);
+        break;
+    case kBatchGridWarp:
+        batch_grid_warp<D>(rd, rc, item_tile, par, step0, kk, pool, s_sum, s_cross);
         break;
     case kBatchGridTile:
         batch_grid_tile<D>(rd, rc, item_tile, par, step0, kk, pool, s_first, s_count, s_sum, s_cross);
@@ -248,7 +303,7 @@ __global__ void __launch_bounds__(256) batch_floyd_expand_kernel(const BatchRoad
         const BatchRoadDev rd = roads[r];
         const uint64_t *bm = bitmaps[r];
         const uint32_t words = (rd.L + 63u) / 64u;
-        const bool grid = rd.type == kBatchGridTile || rd.type == kBatchGridRing;
+        const bool grid = rd.type == kBatchGridTile || rd.type == kBatchGridRing || rd.type == kBatchGridWarp;
         if (grid) {
             for (uint32_t w = tid; w < words; w += 256u)
                 for (uint64_t bits = bm[w]; bits; bits &= bits - 1) rd.cells[0][64u * w + (uint32_t)__ffsll(bits) - 1u] = 0;
@@ -292,7 +347,11 @@ __global__ void __launch_bounds__(256) batch_floyd_expand_kernel(const BatchRoad
 size_t batch_smem_bytes(uint32_t padded)
 {
     (void)padded;
-    return 5u * (size_t)kGridSpan;
+    // the larger of: a block-wide span (stage, out, and its list) and the
+    // eight warp-tiles of the list method
+    const size_t span = 5u * (size_t)kGridSpan;
+    const size_t warps = (size_t)(kBatchThreads / 32) * sizeof(BatchWarpSmem);
+    return span > warps ? span : warps;
 }
 
 int batch_blocks_per_sm(uint32_t padded)

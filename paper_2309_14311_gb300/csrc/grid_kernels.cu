@@ -373,27 +373,13 @@ __global__ void __launch_bounds__(32 * kK1Warps) grid_k1_kernel(const GridStep g
 }
 
 // k >= 2 with k * vmax <= 512: the fused warp kernel.  Every warp works alone
-// on tiles of kKwSpan - 2H cells, H = round_up(k * vmax, 16): it stages the
-// tile with H halo cells on each side (one bulk copy on its own mbarrier),
-// lists the span's cars in cell order (position, velocity) in shared memory
-// and clears the span, runs the k steps on the list, scatters the cars that
-// end in the tile's own cells back into the span and writes the tile back by
-// one bulk store.  On the list a car's leader is the next entry; the lanes
-// take the list 32 cars at a time in ascending order, two groups at once, and
-// all lanes read (their car and its leader) before any lane writes, so every
-// car sees its leader's start-of-step position: the next groups are still
-// unmoved.  After the last car come dummy cars beyond the span, so the last
-// car's gap is at least the distance to the span's end, which is wrong only
-// for cars whose results fall in the right halo (the light cone of k steps
-// reaches k * vmax <= H cells back).  Statistics count the cars whose cell
-// at the start of the step is one of the tile's own.
-constexpr uint32_t kKwSpan = 2048;                      // staged cells per warp-tile
-constexpr uint32_t kKwBuf = kKwSpan + 32u;              // + padding for the cars moving past the span
-constexpr uint32_t kKwList = kKwSpan + 64u;             // every cell a car, + dummies and one leader
-constexpr uint32_t kKwMaxHalo = 512;                    // H limit: the tile keeps at least half the span
-constexpr uint32_t kKwDummy = 0xF000u;                  // position of the dummy cars: beyond any move
+// (no block barrier after set-up) on tiles of kKwSpan - 2H cells, H =
+// round_up(k * vmax, 16): it stages the tile with its halos by one bulk copy
+// on its own mbarrier, runs the k steps by the list method
+// (grid_warp_steps), and writes the tile back by one bulk store.  Two
+// buffers per warp alternate: the next tile's copy is issued as soon as the
+// list is built, once the store of the tile before has read its buffer.
 constexpr int kKwWarps = 4;                             // warps per block
-static_assert(kKwSpan % 64u == 0u, "whole occupancy words per lane");
 
 struct __align__(16) KwWarpSmem {
     int8_t buf[2][kKwBuf];
@@ -411,11 +397,10 @@ __global__ void __launch_bounds__(32 * kKwWarps) grid_warp_kernel(const GridStep
     __shared__ KwWarpSmem s_w[kKwWarps];
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
     KwWarpSmem &w = s_w[warp];
-    const uint32_t L = g.rc.L, vmax = g.rc.vmax, thr = (uint32_t)g.rc.thr;
+    const uint32_t L = g.rc.L;
     const uint32_t C = kKwSpan - 2u * H;                  // cells written per tile
     const uint32_t nw = gridDim.x * (uint32_t)kKwWarps;
     const int ksteps = g.ksteps;
-    constexpr uint32_t kWords = kKwSpan / 1024u;          // occupancy words per lane
 
     if (lane == 0) {
         for (uint32_t b = 0; b < 2u; ++b) mbar_init(&w.full[b], 1);
@@ -461,107 +446,19 @@ __global__ void __launch_bounds__(32 * kKwWarps) grid_warp_kernel(const GridStep
             break;
         }
         __syncwarp();
-        // 1. the list: cars in cell order
-        const uint32_t c0 = 32u * kWords * lane;
-        const uint4 *q = reinterpret_cast<const uint4 *>(span + c0);
-        uint32_t m[kWords];
-        uint32_t n = 0;
-#pragma unroll
-        for (uint32_t j = 0; j < kWords; ++j) {
-            m[j] = occupancy16(q[2u * j]) | (occupancy16(q[2u * j + 1u]) << 16);
-            n += __popc(m[j]);
-        }
-        uint32_t incl = n;
-#pragma unroll
-        for (uint32_t d = 1; d < 32; d <<= 1) {
-            const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, incl, d);
-            if (lane >= d) incl += t;
-        }
-        const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
-        const uint32_t padded = (total + 31u) & ~31u;   // whole groups
-        uint32_t p = incl - n;
-#pragma unroll
-        for (uint32_t j = 0; j < kWords; ++j)
-            for (uint32_t mm = m[j]; mm; mm &= mm - 1u, ++p) {
-                const uint32_t c = c0 + 32u * j + __clz(__brev(mm));
-                w.pos[p] = (uint16_t)c;
-                w.vel[p] = (uint8_t)span[c];
-            }
-        for (uint32_t i = total + lane; i <= padded; i += 32u) {
-            w.pos[i] = (uint16_t)kKwDummy;
-            w.vel[i] = 0;
-        }
-        __syncwarp();
-        // the span is free until the scatter: clear it; the next tile goes into
-        // the other buffer once the store of the tile before has read it
-#pragma unroll
-        for (uint32_t k = 0; k < kKwSpan / 512u; ++k) reinterpret_cast<uint4 *>(span)[lane + 32u * k] = kEmpty4;
-        if (lane == 0) {
-            bulk_wait_read_all();
-            const uint32_t nx = tile + nw;
-            if (nx < n_tiles && bulk_ok(nx)) issue_load(nx, bn);
-        }
-        const bool wraps = base + kKwSpan + (uint32_t)ksteps * vmax > L;   // crossings possible
-        // 2. k steps on the list
-        for (int s = 0; s < ksteps; ++s) {
-            const uint32_t step = g.step0 + (uint32_t)s;
-            uint32_t tsum = 0, tcross = 0;
-            for (uint32_t gi = 0; gi < padded; gi += 64u) {
-                const bool two = gi + 32u < padded;   // warp-uniform
-                const uint32_t i0 = gi + lane, i1 = i0 + 32u;
-                const uint32_t x0 = w.pos[i0], l0 = w.pos[i0 + 1u];
-                uint32_t v0 = w.vel[i0];
-                uint32_t x1 = 0, l1 = 0, v1 = 0;
-                if (two) {
-                    x1 = w.pos[i1];
-                    l1 = w.pos[i1 + 1u];
-                    v1 = w.vel[i1];
+        grid_warp_steps<D>(
+            g.rc, span, w.pos, w.vel, H, own, base, g.step0, ksteps,
+            [&]() {   // the next tile goes into the other buffer once the store of the tile before has read it
+                if (lane == 0) {
+                    bulk_wait_read_all();
+                    const uint32_t nx = tile + nw;
+                    if (nx < n_tiles && bulk_ok(nx)) issue_load(nx, bn);
                 }
-                __syncwarp();   // every lane has read before any lane writes
-                v0 = min(min(v0 + 1u, vmax), l0 - x0 - 1u);                  // rules 1, 2
-                uint32_t cell0 = base + x0;
-                if (cell0 >= L) cell0 -= L;
-                if (D == Draw::kAlways) {
-                    v0 -= v0 != 0u ? 1u : 0u;                                  // rule 3, p = 1
-                } else if (D == Draw::kPhilox) {
-                    const uint32_t u0 = philox_word0(cell0, step, g.rc.road, kTagSlowdown, g.rc.key0, g.rc.key1);
-                    v0 -= (v0 != 0u && u0 < thr) ? 1u : 0u;                    // rule 3
-                }
-                w.pos[i0] = (uint16_t)(x0 + v0);                               // rule 4
-                w.vel[i0] = (uint8_t)v0;
-                const bool own0 = x0 - H < own;
-                tsum += own0 ? v0 : 0u;
-                if (wraps) tcross += own0 && cell0 + v0 >= L ? 1u : 0u;
-                if (two) {
-                    v1 = min(min(v1 + 1u, vmax), l1 - x1 - 1u);
-                    uint32_t cell1 = base + x1;
-                    if (cell1 >= L) cell1 -= L;
-                    if (D == Draw::kAlways) {
-                        v1 -= v1 != 0u ? 1u : 0u;
-                    } else if (D == Draw::kPhilox) {
-                        const uint32_t u1 = philox_word0(cell1, step, g.rc.road, kTagSlowdown, g.rc.key0, g.rc.key1);
-                        v1 -= (v1 != 0u && u1 < thr) ? 1u : 0u;
-                    }
-                    w.pos[i1] = (uint16_t)(x1 + v1);
-                    w.vel[i1] = (uint8_t)v1;
-                    const bool own1 = x1 - H < own;
-                    tsum += own1 ? v1 : 0u;
-                    if (wraps) tcross += own1 && cell1 + v1 >= L ? 1u : 0u;
-                }
-            }
-            tsum = __reduce_add_sync(0xFFFFFFFFu, tsum);
-            tcross = __reduce_add_sync(0xFFFFFFFFu, tcross);
-            if (lane == 0) {
-                w.sum[s] += tsum;
-                w.cross[s] += tcross;
-            }
-            __syncwarp();
-        }
-        // 3. the cars that end in the tile's own cells go back into the span
-        for (uint32_t i = lane; i < total; i += 32u) {
-            const uint32_t x = w.pos[i];
-            if (x - H < own) span[x] = (int8_t)w.vel[i];
-        }
+            },
+            [&](int s, uint32_t sum, uint32_t cross) {
+                w.sum[s] += sum;
+                w.cross[s] += cross;
+            });
         fence_proxy_async();
         __syncwarp();
         if (own == C) {

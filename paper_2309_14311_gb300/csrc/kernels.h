@@ -32,6 +32,14 @@ constexpr int kGridThreads = 256;
 constexpr int kGridSpan = 8192;
 constexpr int kGridTileCells = kGridSpan;   // the `tile` parameter value that selects the tiled kernel
 
+// Warp-tiles of the list method (fused grid steps by one warp): staged cells
+// per warp-tile and the largest halo (the tile keeps at least half the span).
+constexpr uint32_t kKwSpan = 2048;
+constexpr uint32_t kKwBuf = kKwSpan + 32u;              // + padding
+constexpr uint32_t kKwList = kKwSpan + 64u;             // every cell a car, + dummies and one leader
+constexpr uint32_t kKwMaxHalo = 512;
+constexpr uint32_t kKwDummy = 0xF000u;                  // position of the dummy cars: beyond any move
+
 // Status word bits set by kernels (read by the host after a launch).
 constexpr unsigned int kStatusTimeout = 1u;   // a bounded wait on an async copy ran out
 

@@ -243,6 +243,132 @@ struct GridTileGeom {
     uint32_t nwork;     // rotating output buffers: 2 for k = 1, else 3
 };
 
+// ---- the list method for one warp (fused grid steps) ----
+//
+// A warp-tile is a staged span of kKwSpan cells: the tile's own cells with a
+// halo of H >= k * vmax cells on each side.  The warp lists the span's cars
+// in cell order (position, velocity) and clears the span, runs the k steps
+// on the list, and scatters the cars that end in the tile's own cells back
+// into the span.  A car's leader is the next list entry; the lanes take the
+// list 32 cars at a time in ascending order, two groups at once, and every
+// lane reads (its car and the leader) before any lane writes, so each car
+// sees its leader's start-of-step position (the later groups have not moved
+// yet).  After the last car come dummy cars far beyond the span, so the last
+// car's gap is at least the distance to the span's end; that is wrong only
+// for cars within vmax of the end, and the error moves back at most vmax
+// cells a step, which keeps it in the right halo.  Statistics count the cars
+// whose cell at the start of a step is one of the tile's own.
+
+// Fused steps of one warp-tile.  span: kKwBuf bytes of shared memory holding
+// the staged cells (span index 0 = road cell `base`); on return its cells
+// [H, H + own) hold the result.  pos / vel: kKwList entries of shared memory.
+// after_list() is called by every lane once the span has been read (it may
+// be reused from then on); add(s, sum, cross) by lane 0 with step s's
+// statistics of this warp-tile.
+template <Draw D, class AfterList, class Add>
+__device__ __forceinline__ void grid_warp_steps(const RoadConst &rc, int8_t *span, uint16_t *pos, uint8_t *vel,
+                                                uint32_t H, uint32_t own, uint32_t base, uint32_t step0, int ksteps,
+                                                AfterList after_list, Add add)
+{
+    constexpr uint32_t kWords = kKwSpan / 1024u;          // occupancy words per lane
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t L = rc.L, vmax = rc.vmax, thr = (uint32_t)rc.thr;
+    // 1. the list: cars in cell order
+    const uint32_t c0 = 32u * kWords * lane;
+    const uint4 *q = reinterpret_cast<const uint4 *>(span + c0);
+    uint32_t m[kWords];
+    uint32_t n = 0;
+#pragma unroll
+    for (uint32_t j = 0; j < kWords; ++j) {
+        m[j] = occupancy16(q[2u * j]) | (occupancy16(q[2u * j + 1u]) << 16);
+        n += __popc(m[j]);
+    }
+    uint32_t incl = n;
+#pragma unroll
+    for (uint32_t d = 1; d < 32; d <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+        if (lane >= d) incl += t;
+    }
+    const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+    const uint32_t padded = (total + 31u) & ~31u;   // whole groups
+    uint32_t p = incl - n;
+#pragma unroll
+    for (uint32_t j = 0; j < kWords; ++j)
+        for (uint32_t mm = m[j]; mm; mm &= mm - 1u, ++p) {
+            const uint32_t c = c0 + 32u * j + __clz(__brev(mm));
+            pos[p] = (uint16_t)c;
+            vel[p] = (uint8_t)span[c];
+        }
+    for (uint32_t i = total + lane; i <= padded; i += 32u) {
+        pos[i] = (uint16_t)kKwDummy;
+        vel[i] = 0;
+    }
+    __syncwarp();
+    // the span is free until the scatter
+#pragma unroll
+    for (uint32_t k = 0; k < kKwSpan / 512u; ++k) reinterpret_cast<uint4 *>(span)[lane + 32u * k] = kEmpty4;
+    after_list();
+    const bool wraps = base + kKwSpan + (uint32_t)ksteps * vmax > L;   // crossings possible
+    // 2. k steps on the list
+    for (int s = 0; s < ksteps; ++s) {
+        const uint32_t step = step0 + (uint32_t)s;
+        uint32_t tsum = 0, tcross = 0;
+        for (uint32_t gi = 0; gi < padded; gi += 64u) {
+            const bool two = gi + 32u < padded;   // warp-uniform
+            const uint32_t i0 = gi + lane, i1 = i0 + 32u;
+            const uint32_t x0 = pos[i0], l0 = pos[i0 + 1u];
+            uint32_t v0 = vel[i0];
+            uint32_t x1 = 0, l1 = 0, v1 = 0;
+            if (two) {
+                x1 = pos[i1];
+                l1 = pos[i1 + 1u];
+                v1 = vel[i1];
+            }
+            __syncwarp();   // every lane has read before any lane writes
+            v0 = min(min(v0 + 1u, vmax), l0 - x0 - 1u);                  // rules 1, 2
+            uint32_t cell0 = base + x0;
+            if (cell0 >= L) cell0 -= L;
+            if (D == Draw::kAlways) {
+                v0 -= v0 != 0u ? 1u : 0u;                                  // rule 3, p = 1
+            } else if (D == Draw::kPhilox) {
+                const uint32_t u0 = philox_word0(cell0, step, rc.road, kTagSlowdown, rc.key0, rc.key1);
+                v0 -= (v0 != 0u && u0 < thr) ? 1u : 0u;                    // rule 3
+            }
+            pos[i0] = (uint16_t)(x0 + v0);                                 // rule 4
+            vel[i0] = (uint8_t)v0;
+            const bool own0 = x0 - H < own;
+            tsum += own0 ? v0 : 0u;
+            if (wraps) tcross += own0 && cell0 + v0 >= L ? 1u : 0u;
+            if (two) {
+                v1 = min(min(v1 + 1u, vmax), l1 - x1 - 1u);
+                uint32_t cell1 = base + x1;
+                if (cell1 >= L) cell1 -= L;
+                if (D == Draw::kAlways) {
+                    v1 -= v1 != 0u ? 1u : 0u;
+                } else if (D == Draw::kPhilox) {
+                    const uint32_t u1 = philox_word0(cell1, step, rc.road, kTagSlowdown, rc.key0, rc.key1);
+                    v1 -= (v1 != 0u && u1 < thr) ? 1u : 0u;
+                }
+                pos[i1] = (uint16_t)(x1 + v1);
+                vel[i1] = (uint8_t)v1;
+                const bool own1 = x1 - H < own;
+                tsum += own1 ? v1 : 0u;
+                if (wraps) tcross += own1 && cell1 + v1 >= L ? 1u : 0u;
+            }
+        }
+        tsum = __reduce_add_sync(0xFFFFFFFFu, tsum);
+        tcross = __reduce_add_sync(0xFFFFFFFFu, tcross);
+        if (lane == 0) add(s, tsum, tcross);
+        __syncwarp();
+    }
+    // 3. the cars that end in the tile's own cells go back into the span
+    for (uint32_t i = lane; i < total; i += 32u) {
+        const uint32_t x = pos[i];
+        if (x - H < own) span[x] = (int8_t)vel[i];
+    }
+    __syncwarp();
+}
+
 // The span-list method of a grid tile (used when the staged span's cars fit
 // the list): the cars of the staged span `in` become a list sorted by
 // position (cell index within the span, velocity); k synchronous steps are
