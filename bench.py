@@ -139,13 +139,20 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def kernel_source_hash() -> str:
+# The sources that define each measured kernel (a change to any of them
+# invalidates its recorded traffic).
+KERNEL_SOURCES = {
+    "agent_tiled_k16": ("agent_kernels.cu", "tile_device.cuh", "nasch_device.cuh", "kernels.h"),
+    "grid_k1": ("grid_kernels.cu", "tile_device.cuh", "nasch_device.cuh", "kernels.h"),
+}
+
+
+def kernel_source_hash(kernel: str) -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2309_14311_gb300", "csrc")
-    for fn in sorted(os.listdir(csrc)):
-        if fn.endswith((".cu", ".cuh", ".h")):
-            with open(os.path.join(csrc, fn), "rb") as f:
-                h.update(f.read())
+    for fn in KERNEL_SOURCES[kernel]:
+        with open(os.path.join(csrc, fn), "rb") as f:
+            h.update(f.read())
     return h.hexdigest()[:16]
 
 
@@ -153,19 +160,15 @@ def kernel_source_hash() -> str:
 # one ncu --set full capture of the small profiling case (bench.py --profile),
 # scaled to a launch of the large road by the units it processes (x4 cars for
 # the agent kernel, x8 cells for the grid kernel; the traffic of these
-# streaming kernels grows in proportion).  Keyed by the kernel source hash the
-# capture was taken on: a changed kernel reports null until it is re-captured.
-NCU_TRAFFIC: dict[str, dict] = {
-    "agent_tiled_k16": {"source_hash": "4dffaea02c8beb22", "captured_bytes": 167851776 + 122708736,
-                        "scale": 4, "bytes_per_launch": 4 * (167851776 + 122708736)},
-    "grid_k1": {"source_hash": "4dffaea02c8beb22", "captured_bytes": 268537088 + 221754624,
-                      "scale": 8, "bytes_per_launch": 8 * (268537088 + 221754624)},
-}
+# streaming kernels grows in proportion).  Keyed by the hash of the kernel's
+# sources when it was captured: a changed kernel reports null until it is
+# captured again.
+NCU_TRAFFIC: dict[str, dict] = {}
 
 
 def traffic_for(kernel: str):
     rec = NCU_TRAFFIC.get(kernel)
-    if rec and rec.get("source_hash") == kernel_source_hash():
+    if rec and rec.get("source_hash") == kernel_source_hash(kernel):
         return rec["bytes_per_launch"]
     return None
 
