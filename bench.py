@@ -163,7 +163,12 @@ def kernel_source_hash(kernel: str) -> str:
 # streaming kernels grows in proportion).  Keyed by the hash of the kernel's
 # sources when it was captured: a changed kernel reports null until it is
 # captured again.
-NCU_TRAFFIC: dict[str, dict] = {}
+NCU_TRAFFIC: dict[str, dict] = {
+    "agent_tiled_k16": {"source_hash": "f348db7d4b9b86f6", "captured_bytes": 167957248 + 122387712,
+                        "scale": 4, "bytes_per_launch": 4 * (167957248 + 122387712)},
+    "grid_k1": {"source_hash": "acb9760453662904", "captured_bytes": 268562944 + 219382272,
+                "scale": 8, "bytes_per_launch": 8 * (268562944 + 219382272)},
+}
 
 
 def traffic_for(kernel: str):
@@ -478,9 +483,10 @@ def run_served(args, NS, batch_res):
     mean_work = sum(r["N"] * r["T"] for r in rows) / len(rows)
     capacity = batch_res["batched_vehicle_updates_per_s"] / mean_work     # requests per second
     rate = args.serve_load * capacity
-    out = SV.run_poisson(rows, rate=rate, memory_budget=args.serve_budget_gb << 30, steps_per_tick=8,
-                         time_limit_s=args.serve_time_limit)
+    out = SV.run_poisson(rows, rate=rate, memory_budget=args.serve_budget_gb << 30,
+                         steps_per_tick=args.serve_steps_per_tick, time_limit_s=args.serve_time_limit)
     out["offered_load"] = args.serve_load
+    out["steps_per_tick"] = args.serve_steps_per_tick
     out["budget_bytes"] = args.serve_budget_gb << 30
     return out
 
@@ -609,9 +615,10 @@ def run_workload(args):
         mean_work = sum(r["N"] * r["T"] for r in rows) / len(rows)
         cap = args.serve_capacity or 3.5e11
         rate = args.serve_load * cap / mean_work
-        res = SV.run_poisson(rows, rate=rate, memory_budget=args.serve_budget_gb << 30, steps_per_tick=8,
-                             time_limit_s=args.serve_time_limit)
-        out.update(res, assumed_capacity_vehicle_updates_per_s=cap, offered_load=args.serve_load)
+        res = SV.run_poisson(rows, rate=rate, memory_budget=args.serve_budget_gb << 30,
+                             steps_per_tick=args.serve_steps_per_tick, time_limit_s=args.serve_time_limit)
+        out.update(res, assumed_capacity_vehicle_updates_per_s=cap, offered_load=args.serve_load,
+                   steps_per_tick=args.serve_steps_per_tick)
     print(json.dumps(out), flush=True)
     return 0
 
@@ -657,6 +664,7 @@ def main(argv=None):
     ap.add_argument("--serve-load", type=float, default=0.7)
     ap.add_argument("--serve-budget-gb", type=int, default=40)
     ap.add_argument("--serve-time-limit", type=float, default=120.0)
+    ap.add_argument("--serve-steps-per-tick", type=int, default=8, help="super-step launches per scheduling round")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-steps", type=int, default=10)
     ap.add_argument("--ref-steps-per-step", type=int, default=2)

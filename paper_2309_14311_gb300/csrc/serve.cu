@@ -411,19 +411,22 @@ int enqueue_tick(nasch_server s, int buf)
         const int64_t runs = std::min<int64_t>(M, r->super - r->done_super);
         for (int64_t j = 0; j < runs; ++j) active[(size_t)j] = (uint32_t)k;
         r->rd.sbase = (uint32_t)r->done_super;
+    }
+    // every resident road's descriptor, in one copy of the slots up to the
+    // highest in use (the others are never listed); the staging copy must stay
+    // unchanged until this asynchronous copy has run: ticks alternate between
+    // two staging buffers, and a buffer is reused only after the tick that
+    // used it has finished
+    int top = 0;
+    for (auto *r : s->resident) {
         s->h_slots[buf][r->slot] = r->rd;
+        top = std::max(top, r->slot + 1);
     }
     cudaError_t e = cudaMemcpyAsync(s->d_items[buf], s->h_items[buf], (size_t)total * sizeof(BatchItem),
                                     cudaMemcpyHostToDevice, s->stream);
-    // descriptors of this tick's roads (only their slots change)
-    for (auto *r : act) {
-        if (e != cudaSuccess) break;
-        // the staging copy must stay unchanged until this asynchronous copy has
-        // run: ticks alternate between two staging buffers, and a buffer is
-        // reused only after the tick that used it has finished
-        e = cudaMemcpyAsync(s->d_slots + r->slot, s->h_slots[buf] + r->slot, sizeof(BatchRoadDev),
-                            cudaMemcpyHostToDevice, s->stream);
-    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(s->d_slots, s->h_slots[buf], (size_t)top * sizeof(BatchRoadDev), cudaMemcpyHostToDevice,
+                            s->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->d_counters[buf], 0, sizeof(uint32_t) * (size_t)M, s->stream);
     for (int64_t j = 0; j < M && e == cudaSuccess; ++j) {
         BatchLaunch bl;
