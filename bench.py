@@ -514,6 +514,12 @@ def run_workload(args):
     serve                the seed-11 request stream (first --serve-requests),
                          Poisson arrivals at --serve-load x capacity, 40 GB
                          budget; p50/p99 latency and aggregate rate;
+    snapshots            output while running: a 2^28-cell road (2^24 cars)
+                         run for --other-steps steps with no output, with
+                         snapshots of its cells every 50 and every 10 steps
+                         (pinned host ring of 4 slots), and with a 4096-pixel
+                         space-time raster row every step; the slowdown of
+                         each against no output;
     k-sweep              the large road (2^31 cells, 2^27 cars) in each
                          layout at each fusion depth k of --sweep-k: rates
                          over --other-steps steps after 2k warm-up steps."""
@@ -525,7 +531,29 @@ def run_workload(args):
     NS.load(build_if_missing=True)
     stream = torch.cuda.Stream()
     out = {"workload": args.workload}
-    if args.workload == "k-sweep":
+    if args.workload == "snapshots":
+        L, N = 1 << 28, 1 << 24
+        steps = max(args.other_steps, 100) // 100 * 100
+        pinned = torch.empty((4, L), dtype=torch.int8, pin_memory=True)
+        snaps = pinned.numpy()
+        rows = np.zeros((steps, 4096), np.uint8)
+        rows_out = []
+        for layout, k in (("agent", 16), ("grid", 1)):
+            with NS.Road(L, N, 5, 0.13, 1, 0, layout=layout, k=k, stream=stream) as r:
+                r.run_output(2 * k, 0, None, None)   # warm-up
+                res = {}
+                for name, per, sn, rw in (("off", 0, None, None), ("snap_every_50", 50, snaps, None),
+                                          ("snap_every_10", 10, snaps, None), ("raster_every_1", 1, None, rows)):
+                    t0 = time.perf_counter()
+                    r.run_output(steps, per, sn, rw)
+                    sec = time.perf_counter() - t0
+                    res[name] = {"vehicle_updates_per_s": N * steps / sec, "seconds": sec}
+                base = res["off"]["seconds"]
+                for v in res.values():
+                    v["slowdown"] = v["seconds"] / base
+                rows_out.append({"layout": layout, "k": k, "steps": steps, "snapshot_bytes": L, **res})
+        out.update(L=L, N=N, rows=rows_out)
+    elif args.workload == "k-sweep":
         s = WL.LARGE_ROAD
         rows = []
         for layout in ("agent", "grid"):
@@ -669,7 +697,8 @@ def main(argv=None):
     ap.add_argument("--cpu-steps", type=int, default=10)
     ap.add_argument("--ref-steps-per-step", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["large-road", "ensemble", "fundamental-diagram", "serve", "k-sweep"],
+    ap.add_argument("--workload", choices=["large-road", "ensemble", "fundamental-diagram", "serve", "k-sweep",
+                                           "snapshots"],
                     default="large-road", help="large-road is the benchmark line; the others print their own line")
     ap.add_argument("--sweep-k", default="1,2,4,8,16,32", help="fusion depths of the k-sweep workload")
     ap.add_argument("--roads", type=int, default=4096)

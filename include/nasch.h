@@ -126,6 +126,27 @@ int nasch_set_state(nasch_handle h, const int32_t *x_host, const uint8_t *v_host
  * then the per-step sum_v and crossings).  Asynchronous. */
 int nasch_run(nasch_handle h, int64_t steps);
 
+/* Run with output: the handout's `per` parameter (Handout, parameter file
+ * and output: a density and velocity picture of the road every `per`
+ * steps, none when per = 0) and its space-time diagram (Fig. 1).  Enqueues
+ * `steps` steps; after each full chunk of `per` steps (counted from this
+ * call) takes snapshot j = 0, 1, ...:
+ *   snap_host (may be NULL): the road's L cells (-1 empty, else the velocity;
+ *     an agent road is scattered into cells) go to snap_host + (j mod
+ *     snap_cap) * L, so snap_cap >= steps / per keeps them all; caller-owned,
+ *     pinned host memory lets the copy overlap the following steps;
+ *   raster_host (may be NULL): one row of raster_width pixels (1 <=
+ *     raster_width <= L) goes to raster_host + (j mod raster_cap) *
+ *     raster_width; pixel i covers the cells c with floor(c * raster_width /
+ *     L) = i and holds floor(255 * cars / cells) of them.
+ * A partial last chunk (steps not a multiple of per) runs without a
+ * snapshot.  per = 0, or both outputs NULL, runs the steps with no output.
+ * Returns once every copy is in host memory (synchronises the stream).
+ * NASCH_EINVAL for negative steps or per, or a capacity or width out of
+ * range; NASCH_ECUDA if staging memory cannot be allocated. */
+int nasch_run_output(nasch_handle h, int64_t steps, int64_t per, int8_t *snap_host, int64_t snap_cap,
+                     uint8_t *raster_host, int32_t raster_width, int64_t raster_cap);
+
 /* Copy the current state to the host.  Agent layout: cars in their cyclic
  * order.  Grid layout: cars in increasing cell order.  cap is the capacity
  * of both arrays in elements and must be >= N.  Synchronises the stream. */

@@ -189,6 +189,25 @@ def grid_segment(L, cells, first, vmax, p, seed, road=0, step0=0, T=1):
     return c[m: W - m].copy()
 
 
+def raster_row(L: int, x: np.ndarray, width: int) -> np.ndarray:
+    """One row of the space-time diagram (Fig. 1: the road's cells across,
+    time down; darker where cars are) at `width` pixels: pixel i covers the
+    cells c with floor(c * width / L) == i and holds floor(255 * cars / cells)
+    over them.  x: the cars' cells.  Written from that definition: each car's
+    pixel by integer division, each pixel's cell count by counting the cells
+    that map to it."""
+    L, width = int(L), int(width)
+    assert 1 <= width <= L
+    x = np.asarray(x, dtype=np.int64)
+    cars = np.bincount((x * width) // L, minlength=width)[:width]
+    if L <= 1 << 24:
+        cells = np.bincount((np.arange(L, dtype=np.int64) * width) // L, minlength=width)
+    else:   # the first cell of pixel i is ceil(i * L / width)
+        first = (np.arange(width + 1, dtype=object) * L + width - 1) // width
+        cells = np.array([int(first[i + 1] - first[i]) for i in range(width)], dtype=np.int64)
+    return ((255 * cars) // cells).astype(np.uint8)
+
+
 def set_threads(n: int) -> int:
     """Set the OpenMP build's thread count; returns the count now in force."""
     return int(_load(True).oracle_set_threads(int(n)))

@@ -178,6 +178,11 @@ struct nasch_road {
     uint64_t stats_first = 0;
     unsigned long long *d_sum = nullptr, *d_cross = nullptr;
     int64_t stats_cap = 0;
+    // output (nasch_run_output), made on first use: two staging copies of
+    // the cells, a copy stream and the events that order them
+    int8_t *stage[2] = {nullptr, nullptr};
+    cudaStream_t io_stream = nullptr;
+    cudaEvent_t ev_ready[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr};
 };
 
 namespace {
@@ -223,6 +228,13 @@ void free_road(nasch_road *h)
     cudaFree(h->d_sum);
     cudaFree(h->d_cross);
     cudaFree(h->d_status);
+    if (h->io_stream) cudaStreamSynchronize(h->io_stream);
+    for (int i = 0; i < 2; ++i) {
+        cudaFree(h->stage[i]);
+        if (h->ev_ready[i]) cudaEventDestroy(h->ev_ready[i]);
+        if (h->ev_free[i]) cudaEventDestroy(h->ev_free[i]);
+    }
+    if (h->io_stream) cudaStreamDestroy(h->io_stream);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;
 }
@@ -295,6 +307,86 @@ int choose_layout(const nasch_params *prm)
     // State bytes per step: agent 10 per car (read + write x and v), grid 2
     // per cell; equal at density 0.2.
     return (double)prm->N < 0.2 * (double)prm->L ? NASCH_LAYOUT_AGENT : NASCH_LAYOUT_GRID;
+}
+
+// Enqueue `steps` steps on the handle's stream (validated by the caller).
+int run_steps(nasch_road *h, int64_t steps)
+{
+    if (steps == 0) return NASCH_OK;
+    const int64_t used = (int64_t)(h->step - h->stats_first);
+    int st = ensure_stats(h, used + steps);
+    if (st) return st;
+    unsigned long long *sum = h->d_sum + used;
+    unsigned long long *cross = h->d_cross + used;
+    cudaError_t e = cudaMemsetAsync(sum, 0, (size_t)steps * 8, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(cross, 0, (size_t)steps * 8, h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(statistics)");
+    const RoadConst rc = road_const(h);
+
+    if (h->layout == NASCH_LAYOUT_AGENT) {
+        AgentStep a;
+        a.status = h->d_status;
+        a.N = (uint32_t)h->N;
+        a.rc = rc;
+        if (h->N == 0) {
+            h->step += (uint64_t)steps;
+            return NASCH_OK;
+        }
+        if (h->ring) {
+            // the whole run in launches of up to 2^20 steps
+            for (int64_t done = 0; done < steps;) {
+                const int64_t kk = std::min<int64_t>(steps - done, 1 << 20);
+                a.x_in = h->x[h->cur];
+                a.v_in = h->v[h->cur];
+                a.x_out = h->x[h->cur ^ 1];
+                a.v_out = h->v[h->cur ^ 1];
+                a.step0 = (uint32_t)(h->step + (uint64_t)done);
+                a.ksteps = (int)kk;
+                a.sum_v = sum + done;
+                a.crossings = cross + done;
+                e = launch_agent_ring(a, h->stream);
+                if (e != cudaSuccess) return cuda_fail(e, "agent ring kernel");
+                h->cur ^= 1;
+                done += kk;
+            }
+        } else {
+            for (int64_t done = 0; done < steps;) {
+                const int kk = (int)std::min<int64_t>(steps - done, h->k);
+                a.x_in = h->x[h->cur];
+                a.v_in = h->v[h->cur];
+                a.x_out = h->x[h->cur ^ 1];
+                a.v_out = h->v[h->cur ^ 1];
+                a.step0 = (uint32_t)(h->step + (uint64_t)done);
+                a.ksteps = kk;
+                a.sum_v = sum + done;
+                a.crossings = cross + done;
+                e = launch_agent_tiled(a, h->tile, h->blocks, h->stream);
+                if (e != cudaSuccess) return cuda_fail(e, "agent tiled kernel");
+                h->cur ^= 1;
+                done += kk;
+            }
+        }
+    } else {
+        GridStep g;
+        g.status = h->d_status;
+        g.rc = rc;
+        for (int64_t done = 0; done < steps;) {
+            const int kk = h->ring ? (int)std::min<int64_t>(steps - done, 1 << 20)
+                                   : (int)std::min<int64_t>(steps - done, h->k);
+            g.c_in = h->cells[h->cur];
+            g.c_out = h->cells[h->cur ^ 1];
+            g.step0 = (uint32_t)(h->step + (uint64_t)done);
+            g.ksteps = kk;
+            g.sum_v = sum + done;
+            g.crossings = cross + done;
+            e = h->ring ? launch_grid_ring(g, h->stream) : launch_grid_tiled(g, h->blocks, h->stream);
+            if (e != cudaSuccess) return cuda_fail(e, h->ring ? "grid ring kernel" : "grid tiled kernel");
+            h->cur ^= 1;
+            done += kk;
+        }
+    }
+    h->step += (uint64_t)steps;
+    return NASCH_OK;
 }
 
 }  // namespace
@@ -455,81 +547,94 @@ int nasch_run(nasch_handle h, int64_t steps)
     TraceRange trace("nasch_run");
     if (!h) return fail(NASCH_EINVAL, "handle is NULL");
     if (steps < 0) return fail(NASCH_EINVAL, "steps=%lld < 0", (long long)steps);
-    if (steps == 0) return NASCH_OK;
-    const int64_t used = (int64_t)(h->step - h->stats_first);
-    int st = ensure_stats(h, used + steps);
-    if (st) return st;
-    unsigned long long *sum = h->d_sum + used;
-    unsigned long long *cross = h->d_cross + used;
-    cudaError_t e = cudaMemsetAsync(sum, 0, (size_t)steps * 8, h->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(cross, 0, (size_t)steps * 8, h->stream);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(statistics)");
-    const RoadConst rc = road_const(h);
+    return run_steps(h, steps);
+}
 
-    if (h->layout == NASCH_LAYOUT_AGENT) {
-        AgentStep a;
-        a.status = h->d_status;
-        a.N = (uint32_t)h->N;
-        a.rc = rc;
-        if (h->N == 0) {
-            h->step += (uint64_t)steps;
-            return NASCH_OK;
-        }
-        if (h->ring) {
-            // the whole run in launches of up to 2^20 steps
-            for (int64_t done = 0; done < steps;) {
-                const int64_t kk = std::min<int64_t>(steps - done, 1 << 20);
-                a.x_in = h->x[h->cur];
-                a.v_in = h->v[h->cur];
-                a.x_out = h->x[h->cur ^ 1];
-                a.v_out = h->v[h->cur ^ 1];
-                a.step0 = (uint32_t)(h->step + (uint64_t)done);
-                a.ksteps = (int)kk;
-                a.sum_v = sum + done;
-                a.crossings = cross + done;
-                e = launch_agent_ring(a, h->stream);
-                if (e != cudaSuccess) return cuda_fail(e, "agent ring kernel");
-                h->cur ^= 1;
-                done += kk;
-            }
-        } else {
-            for (int64_t done = 0; done < steps;) {
-                const int kk = (int)std::min<int64_t>(steps - done, h->k);
-                a.x_in = h->x[h->cur];
-                a.v_in = h->v[h->cur];
-                a.x_out = h->x[h->cur ^ 1];
-                a.v_out = h->v[h->cur ^ 1];
-                a.step0 = (uint32_t)(h->step + (uint64_t)done);
-                a.ksteps = kk;
-                a.sum_v = sum + done;
-                a.crossings = cross + done;
-                e = launch_agent_tiled(a, h->tile, h->blocks, h->stream);
-                if (e != cudaSuccess) return cuda_fail(e, "agent tiled kernel");
-                h->cur ^= 1;
-                done += kk;
-            }
-        }
-    } else {
-        GridStep g;
-        g.status = h->d_status;
-        g.rc = rc;
-        for (int64_t done = 0; done < steps;) {
-            const int kk = h->ring ? (int)std::min<int64_t>(steps - done, 1 << 20)
-                                   : (int)std::min<int64_t>(steps - done, h->k);
-            g.c_in = h->cells[h->cur];
-            g.c_out = h->cells[h->cur ^ 1];
-            g.step0 = (uint32_t)(h->step + (uint64_t)done);
-            g.ksteps = kk;
-            g.sum_v = sum + done;
-            g.crossings = cross + done;
-            e = h->ring ? launch_grid_ring(g, h->stream) : launch_grid_tiled(g, h->blocks, h->stream);
-            if (e != cudaSuccess) return cuda_fail(e, h->ring ? "grid ring kernel" : "grid tiled kernel");
-            h->cur ^= 1;
-            done += kk;
-        }
+int nasch_run_output(nasch_handle h, int64_t steps, int64_t per, int8_t *snap_host, int64_t snap_cap,
+                     uint8_t *raster_host, int32_t raster_width, int64_t raster_cap)
+{
+    clear_error();
+    TraceRange trace("nasch_run_output");
+    if (!h) return fail(NASCH_EINVAL, "handle is NULL");
+    if (steps < 0 || per < 0) return fail(NASCH_EINVAL, "steps=%lld, per=%lld: negative", (long long)steps, (long long)per);
+    const bool snap = snap_host != nullptr, raster = raster_host != nullptr;
+    if (snap && snap_cap < 1) return fail(NASCH_EINVAL, "snap_cap=%lld < 1", (long long)snap_cap);
+    if (raster && (raster_cap < 1 || raster_width < 1 || (int64_t)raster_width > h->L))
+        return fail(NASCH_EINVAL, "raster_width=%d outside 1..L=%lld or raster_cap=%lld < 1", raster_width,
+                    (long long)h->L, (long long)raster_cap);
+    if (per == 0 || (!snap && !raster)) {   // output off
+        int st = run_steps(h, steps);
+        return st ? st : sync_and_check(h);
     }
-    h->step += (uint64_t)steps;
-    return NASCH_OK;
+    const size_t L = (size_t)h->L;
+    cudaError_t e = cudaSuccess;
+    // staging: snapshots leave from a copy of the cells, so the copy to the
+    // host overlaps the next steps; an agent road is scattered into one
+    const bool staged = snap || h->layout == NASCH_LAYOUT_AGENT;
+    for (int i = 0; i < 2 && staged && e == cudaSuccess; ++i) {
+        if (!h->stage[i]) e = cudaMalloc(&h->stage[i], L);
+        if (e == cudaSuccess && !h->ev_ready[i]) e = cudaEventCreateWithFlags(&h->ev_ready[i], cudaEventDisableTiming);
+        if (e == cudaSuccess && !h->ev_free[i]) e = cudaEventCreateWithFlags(&h->ev_free[i], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess && snap && !h->io_stream) e = cudaStreamCreateWithFlags(&h->io_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_fail(e, "output buffers");
+    uint8_t *d_rows = nullptr;
+    const size_t row_bytes = raster ? (size_t)raster_width : 0;
+    if (raster) {
+        e = cudaMallocAsync(&d_rows, (size_t)raster_cap * row_bytes, h->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "raster rows");
+    }
+    int64_t j = 0;   // snapshots taken
+    int st = NASCH_OK;
+    for (int64_t done = 0; done < steps && st == NASCH_OK;) {
+        const int64_t chunk = std::min(per, steps - done);
+        st = run_steps(h, chunk);
+        if (st) break;
+        done += chunk;
+        if (chunk < per) break;   // a partial last chunk takes no snapshot
+        const int b = (int)(j & 1);
+        const int8_t *src = h->cells[h->cur];
+        if (staged) {
+            // staging buffer b: its copy to the host two snapshots ago must be done
+            if (j >= 2 && snap) e = cudaStreamWaitEvent(h->stream, h->ev_free[b], 0);
+            if (e == cudaSuccess) {
+                if (h->layout == NASCH_LAYOUT_GRID) {
+                    e = cudaMemcpyAsync(h->stage[b], h->cells[h->cur], L, cudaMemcpyDeviceToDevice, h->stream);
+                } else {
+                    e = cudaMemsetAsync(h->stage[b], 0xFF, L, h->stream);
+                    if (e == cudaSuccess && h->N > 0)
+                        e = launch_scatter_agent_to_grid(h->x[h->cur], h->v[h->cur], (uint32_t)h->N, h->stage[b],
+                                                         h->stream);
+                }
+            }
+            src = h->stage[b];
+        }
+        if (e == cudaSuccess && raster)
+            e = launch_raster_row(src, (uint32_t)h->L, (uint32_t)raster_width,
+                                  d_rows + (size_t)(j % raster_cap) * row_bytes, h->sms, h->stream);
+        if (e == cudaSuccess && snap) {
+            e = cudaEventRecord(h->ev_ready[b], h->stream);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(h->io_stream, h->ev_ready[b], 0);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(snap_host + (size_t)(j % snap_cap) * L, h->stage[b], L, cudaMemcpyDeviceToHost,
+                                    h->io_stream);
+            if (e == cudaSuccess) e = cudaEventRecord(h->ev_free[b], h->io_stream);
+        }
+        if (e != cudaSuccess) st = cuda_fail(e, "snapshot");
+        ++j;
+    }
+    if (st == NASCH_OK && raster && j > 0) {
+        const int64_t rows = std::min(j, raster_cap);
+        e = cudaMemcpyAsync(raster_host, d_rows, (size_t)rows * row_bytes, cudaMemcpyDeviceToHost, h->stream);
+        if (e != cudaSuccess) st = cuda_fail(e, "raster rows to host");
+    }
+    if (d_rows) cudaFreeAsync(d_rows, h->stream);
+    if (h->io_stream) {
+        e = cudaStreamSynchronize(h->io_stream);
+        if (e != cudaSuccess && st == NASCH_OK) st = cuda_fail(e, "snapshot copies");
+    }
+    const int st2 = sync_and_check(h);
+    return st ? st : st2;
 }
 
 int nasch_read_state(nasch_handle h, int32_t *x_host, uint8_t *v_host, int64_t cap)

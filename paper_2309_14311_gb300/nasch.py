@@ -94,6 +94,7 @@ def _declare(lib) -> None:
         "nasch_create_ex": (ctypes.c_int, [P, P]),
         "nasch_set_state": (ctypes.c_int, [H, P, P, i64, u64]),
         "nasch_run": (ctypes.c_int, [H, i64]),
+        "nasch_run_output": (ctypes.c_int, [H, i64, i64, P, i64, P, i32, i64]),
         "nasch_read_state": (ctypes.c_int, [H, P, P, i64]),
         "nasch_read_grid": (ctypes.c_int, [H, P, i64]),
         "nasch_stats": (ctypes.c_int, [H, u64, i64, P, P]),
@@ -238,6 +239,22 @@ class Road:
 
     def run(self, steps: int) -> None:
         _check(load().nasch_run(self._h, steps))
+
+    def run_output(self, steps: int, per: int, snapshots: np.ndarray | None = None,
+                   raster: np.ndarray | None = None) -> None:
+        """Run `steps` steps with output after every `per` steps: snapshot j
+        of the cells into snapshots[j % len(snapshots)] (shape (n, L), int8)
+        and raster row j into raster[j % len(raster)] (shape (n, width),
+        uint8).  Either may be None.  Synchronous."""
+        sp, sn, rp, rw, rn = None, 0, None, 0, 0
+        if snapshots is not None:
+            assert snapshots.dtype == np.int8 and snapshots.ndim == 2 and snapshots.shape[1] == self.L
+            assert snapshots.flags.c_contiguous
+            sp, sn = _ptr(snapshots), snapshots.shape[0]
+        if raster is not None:
+            assert raster.dtype == np.uint8 and raster.ndim == 2 and raster.flags.c_contiguous
+            rp, rw, rn = _ptr(raster), raster.shape[1], raster.shape[0]
+        _check(load().nasch_run_output(self._h, steps, per, sp, sn, rp, rw, rn))
 
     def synchronize(self) -> None:
         _check(load().nasch_synchronize(self._h))

@@ -16,7 +16,7 @@ def load(name):
             toks = val.split()
             if k == "p":
                 out[k] = float(toks[0])
-            elif k in ("x", "v") or k.startswith(("x@", "v@")):
+            elif k in ("x", "v", "row") or k.startswith(("x@", "v@")):
                 out[k] = [int(t) for t in toks]
             else:
                 out[k] = int(toks[0])
