@@ -610,7 +610,7 @@ def run_workload(args):
                    plain_vehicle_updates_per_s=pwork / plain,
                    speedup=(work / inf.run_seconds) / (pwork / plain))
     elif args.workload == "fundamental-diagram":
-        roads = WL.fundamental_diagram_roads(replicas=args.replicas, L=args.fd_L)
+        roads = WL.fundamental_diagram_roads(replicas=args.replicas, L=args.fd_L, vmax=args.fd_vmax)
         T = WL.FD_T
         t0 = time.perf_counter()
         with NS.Batch(roads, [T] * len(roads), stream=stream) as b:
@@ -626,17 +626,29 @@ def run_workload(args):
         L = args.fd_L
         for (N, p), sums in sorted(table.items()):
             steps = T - WL.FD_WARMUP
-            J = [s / (L * steps) for s in sums]            # time-averaged flux per replica
-            v = [s / (N * steps) for s in sums]            # time-averaged mean velocity
-            row = {"rho": N / L, "p": p, "J": float(np.mean(J)), "J_sd": float(np.std(J)),
-                   "v": float(np.mean(v)), "replicas": len(J)}
+            J = np.array([s / (L * steps) for s in sums])  # time-averaged flux per replica
+            v = np.array([s / (N * steps) for s in sums])  # time-averaged mean velocity
+            se = float(J.std(ddof=1) / np.sqrt(len(J))) if len(J) > 1 else 0.0
+            row = {"rho": N / L, "p": p, "J": float(J.mean()), "J_sd": float(J.std(ddof=1)) if len(J) > 1 else 0.0,
+                   "J_ci95": 1.96 * se, "v": float(v.mean()), "replicas": len(J)}
+            rho = N / L
+            theory = None
             if p == 0.0:
-                row["J_p0_theory"] = min(5 * N / L, 1 - N / L)
+                theory = min(args.fd_vmax * rho, 1 - rho)   # deterministic steady state
+            elif args.fd_vmax == 1:
+                theory = WL.flux_vmax1(rho, p)
+            if theory is not None:
+                row["J_theory"] = theory
+                row["J_minus_theory"] = row["J"] - theory
             rows.append(row)
         work = sum(r["N"] for r in roads) * T
-        out.update(roads=len(roads), L=L, T=T, warmup=WL.FD_WARMUP, vehicle_updates=work,
+        checked = [r for r in rows if "J_theory" in r]
+        out.update(roads=len(roads), L=L, T=T, warmup=WL.FD_WARMUP, vmax=args.fd_vmax, vehicle_updates=work,
                    batched_gpu_seconds=inf.run_seconds, wall_seconds=wall,
-                   vehicle_updates_per_s=work / inf.run_seconds, table=rows)
+                   vehicle_updates_per_s=work / inf.run_seconds,
+                   theory_rows=len(checked),
+                   max_abs_J_minus_theory=max((abs(r["J_minus_theory"]) for r in checked), default=None),
+                   table=rows)
     elif args.workload == "serve":
         from paper_2309_14311_gb300 import serve as SV
         rows = WL.request_stream()[: args.serve_requests]
@@ -705,6 +717,7 @@ def main(argv=None):
     ap.add_argument("--plain-roads", type=int, default=256)
     ap.add_argument("--replicas", type=int, default=128)
     ap.add_argument("--fd-L", type=int, default=10**6)
+    ap.add_argument("--fd-vmax", type=int, default=5, help="vmax of the fundamental-diagram roads (1: exact flux known)")
     ap.add_argument("--serve-capacity", type=float, default=0.0,
                     help="vehicle-updates/s the offered load is scaled to (0: 3.5e11)")
     ap.add_argument("--profile", choices=["agent", "grid"], default=None,

@@ -57,6 +57,8 @@
 
 #define ORACLE_TAG_SLOWDOWN 0u
 #define ORACLE_TAG_INIT 1u
+#define ORACLE_TAG_EXIT 2u
+#define ORACLE_TAG_ENTRY 3u
 
 /* ------------------------------------------------------------------------ */
 /* Philox4x32-10 (Salmon et al., SC'11, section on the Philox family).       */
@@ -265,6 +267,83 @@ int oracle_grid_run(int64_t L, int32_t vmax, uint64_t thr, uint64_t seed, uint32
         memcpy(cells, next, (size_t)L);
         if (sum_v) sum_v[t] = moved;
         if (crossings) crossings[t] = wrapped;
+    }
+    free(next);
+    return status;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Open road (the handout's "Variations": other boundary conditions).  The   */
+/* road is cells 0..L-1 with an entry before cell 0 and an exit after cell    */
+/* L-1, no ring.  The paper gives no rules for them; the reading:             */
+/*   - the exit is open at step t with probability beta: word 0 of            */
+/*     Philox(ctr = (0, t, road, 2)) < ceil(beta * 2^32).  The leading car    */
+/*     (no car ahead of it on the road) sees an unbounded road when the exit  */
+/*     is open, and the end of the road (L-1-x empty cells) when it is        */
+/*     closed; a car whose move passes cell L-1 leaves the road;              */
+/*   - rules 1-4 otherwise as on the ring, from start-of-step positions;      */
+/*   - after the moves, if cell 0 is empty, a car enters there with velocity  */
+/*     0 with probability alpha: word 0 of Philox(ctr = (0, t, road, 3)) <    */
+/*     ceil(alpha * 2^32).                                                    */
+/* Per step: sum_v = velocities of the moves (the leaving cars included),     */
+/* crossings = cars that left.                                               */
+/* ------------------------------------------------------------------------ */
+static uint32_t boundary_word(uint64_t seed, uint32_t road, uint64_t step, uint32_t tag)
+{
+    uint32_t ctr[4] = {0u, (uint32_t)step, road, tag};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t out[4];
+    oracle_philox4x32_10(ctr, key, out);
+    return out[0];
+}
+
+int oracle_open_run(int64_t L, int32_t vmax, uint64_t thr, uint64_t thr_entry, uint64_t thr_exit, uint64_t seed,
+                    uint32_t road, uint64_t step0, int64_t T, int8_t *cells, uint64_t *sum_v, uint64_t *crossings)
+{
+    if (L < 1 || L > ((int64_t)1 << 31) || vmax < 0 || vmax > 127 || T < 0) return ORACLE_EINVAL;
+    int8_t *next = (int8_t *)malloc((size_t)L);
+    if (!next) return ORACLE_ENOMEM;
+    int status = ORACLE_OK;
+    for (int64_t t = 0; t < T && status == ORACLE_OK; ++t) {
+        uint64_t step = step0 + (uint64_t)t;
+        const int exit_open = (uint64_t)boundary_word(seed, road, step, ORACLE_TAG_EXIT) < thr_exit;
+        uint64_t moved = 0, left = 0;
+        int collided = 0;
+        memset(next, -1, (size_t)L);
+        for (int64_t j = 0; j < L; ++j) {
+            if (cells[j] < 0) continue;
+            int64_t vel = (int64_t)cells[j] + 1;              /* rule 1 */
+            if (vel > vmax) vel = vmax;
+            int64_t gap = 0;                                  /* rule 2 */
+            while (gap < vel) {
+                int64_t ahead = j + gap + 1;
+                if (ahead >= L) {                             /* past the end of the road */
+                    if (!exit_open) break;                    /* closed: the road ends at L-1 */
+                    gap = vel;                                /* open: nothing ahead */
+                    break;
+                }
+                if (cells[ahead] >= 0) break;
+                gap += 1;
+            }
+            if (vel > gap) vel = gap;
+            if (vel > 0) {                                    /* rule 3 */
+                if ((uint64_t)slowdown_word(seed, road, j, step) < thr) vel -= 1;
+            }
+            int64_t dest = j + vel;                           /* rule 4 */
+            moved += (uint64_t)vel;
+            if (dest >= L) {                                  /* leaves the road */
+                left += 1;
+                continue;
+            }
+            if (next[dest] != -1) collided += 1;
+            next[dest] = (int8_t)vel;
+        }
+        if (collided) status = ORACLE_ECOLLIDE;
+        if (next[0] < 0 && (uint64_t)boundary_word(seed, road, step, ORACLE_TAG_ENTRY) < thr_entry)
+            next[0] = 0;                                      /* a car enters at rest */
+        memcpy(cells, next, (size_t)L);
+        if (sum_v) sum_v[t] = moved;
+        if (crossings) crossings[t] = left;
     }
     free(next);
     return status;

@@ -74,6 +74,8 @@ def _load(openmp: bool) -> ctypes.CDLL:
         lib.oracle_agent_run.restype = ctypes.c_int
         lib.oracle_grid_run.argtypes = [i64, i32, u64, u64, u32, u64, i64, P, P, P]
         lib.oracle_grid_run.restype = ctypes.c_int
+        lib.oracle_open_run.argtypes = [i64, i32, u64, u64, u64, u64, u32, u64, i64, P, P, P]
+        lib.oracle_open_run.restype = ctypes.c_int
         lib.oracle_agent_to_grid.argtypes = [i64, i64, P, P, P]
         lib.oracle_agent_to_grid.restype = ctypes.c_int
         lib.oracle_agent_segment.argtypes = [i64, i64, i32, u64, u64, u32, u64, i64, P, P]
@@ -156,6 +158,20 @@ def grid_run(cells, vmax, p, seed, road=0, step0=0, T=1, *, openmp=False, thr=No
                                        _ptr(c), _ptr(sv), _ptr(cr))
     _check(st, "grid_run")
     return c, sv, cr
+
+
+def open_run(cells, vmax, p, alpha, beta, seed, road=0, step0=0, T=1, *, thr=None):
+    """Open road (entry before cell 0 with probability alpha, exit after cell
+    L-1 open with probability beta; see oracle_open_run): T steps on a copy
+    of `cells` (int8, -1 empty).  Returns (cells, sum_v[T], crossings[T])
+    with crossings = cars that left."""
+    c = np.ascontiguousarray(cells, dtype=np.int8).copy()
+    sv = np.zeros(max(T, 1), np.uint64)
+    cr = np.zeros(max(T, 1), np.uint64)
+    t = slow_threshold(p) if thr is None else thr
+    _check(_load(False).oracle_open_run(len(c), vmax, t, slow_threshold(alpha), slow_threshold(beta), seed, road,
+                                        step0, T, _ptr(c), _ptr(sv), _ptr(cr)), "oracle_open_run")
+    return c, sv[:T], cr[:T]
 
 
 def agent_to_grid(L, x, v) -> np.ndarray:

@@ -53,16 +53,25 @@ def fd_cars(i: int, L: int = FD_L) -> int:
     return max(1, min(L, (L * (1260 + 880 * i) + 31500) // 63000))
 
 
-def fundamental_diagram_roads(replicas: int = 128, L: int = FD_L, densities: int = FD_DENSITIES, ps=FD_PS):
-    """The density sweep: densities x ps x replicas roads of L cells, vmax 5.
-    Replica r uses seed r + 1; the road id is the flat index (density-major)."""
+def fundamental_diagram_roads(replicas: int = 128, L: int = FD_L, densities: int = FD_DENSITIES, ps=FD_PS,
+                              vmax: int = 5):
+    """The density sweep: densities x ps x replicas roads of L cells (vmax 5
+    by default).  Replica r uses seed r + 1; the road id is the flat index
+    (density-major)."""
     roads = []
     for i in range(densities):
         for j, p in enumerate(ps):
             for r in range(replicas):
-                roads.append(dict(L=L, N=fd_cars(i, L), vmax=5, p=p, seed=r + 1,
+                roads.append(dict(L=L, N=fd_cars(i, L), vmax=vmax, p=p, seed=r + 1,
                                   road_id=(i * len(ps) + j) * replicas + r))
     return roads
+
+
+def flux_vmax1(rho: float, p: float) -> float:
+    """Steady-state flux of the vmax = 1 model with parallel update
+    (Schreckenberg, Schadschneider, Nagel & Ito, Phys. Rev. E 51, 1995):
+    J = (1 - sqrt(1 - 4 (1 - p) rho (1 - rho))) / 2."""
+    return 0.5 * (1.0 - (1.0 - 4.0 * (1.0 - p) * rho * (1.0 - rho)) ** 0.5)
 
 
 def _load_table(name: str):

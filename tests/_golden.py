@@ -14,7 +14,7 @@ def load(name):
                 continue
             k, val = (s.strip() for s in line.split("=", 1))
             toks = val.split()
-            if k == "p":
+            if k in ("p", "alpha", "beta"):
                 out[k] = float(toks[0])
             elif k in ("x", "v", "row") or k.startswith(("x@", "v@")):
                 out[k] = [int(t) for t in toks]
