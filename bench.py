@@ -520,6 +520,11 @@ def run_workload(args):
                          (pinned host ring of 4 slots), and with a 4096-pixel
                          space-time raster row every step; the slowdown of
                          each against no output;
+    open-road            the large road opened (entry alpha = 0.5 before cell
+                         0, exit beta = 0.5 after cell L-1; grid layout, one
+                         step per launch): rates over --other-steps steps
+                         and the fraction of the measured HBM copy bandwidth
+                         (2 B per cell-step);
     k-sweep              the large road (2^31 cells, 2^27 cars) in each
                          layout at each fusion depth k of --sweep-k: rates
                          over --other-steps steps after 2k warm-up steps."""
@@ -531,7 +536,27 @@ def run_workload(args):
     NS.load(build_if_missing=True)
     stream = torch.cuda.Stream()
     out = {"workload": args.workload}
-    if args.workload == "snapshots":
+    if args.workload == "open-road":
+        spec = WL.LARGE_ROAD
+        steps = max(args.other_steps, 10)
+        with NS.Road(spec.L, spec.N, spec.vmax, spec.p, spec.seed, spec.road_id, layout="grid", open=(0.5, 0.5),
+                     stream=stream) as r:
+            r.run(5)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            r.run(steps)
+            b.record(stream)
+            b.synchronize()
+            sec = a.elapsed_time(b) / 1e3
+            cells = r.read_grid()
+            cars_now = int((cells >= 0).sum())
+        hbm_peak, hbm_kind = measured_peaks()
+        gbs = 2.0 * spec.L * steps / sec / 1e9
+        out.update(L=spec.L, N_start=spec.N, cars_after=cars_now, alpha=0.5, beta=0.5, steps=steps,
+                   cell_updates_per_s=spec.L * steps / sec, launch_ms=sec / steps * 1e3,
+                   roofline_hbm={"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
+                                 "frac": gbs / hbm_peak, "peak_source": f"{hbm_kind} hbm_gbs"})
+    elif args.workload == "snapshots":
         L, N = 1 << 28, 1 << 24
         steps = max(args.other_steps, 100) // 100 * 100
         pinned = torch.empty((4, L), dtype=torch.int8, pin_memory=True)
@@ -710,7 +735,7 @@ def main(argv=None):
     ap.add_argument("--ref-steps-per-step", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", choices=["large-road", "ensemble", "fundamental-diagram", "serve", "k-sweep",
-                                           "snapshots"],
+                                           "snapshots", "open-road"],
                     default="large-road", help="large-road is the benchmark line; the others print their own line")
     ap.add_argument("--sweep-k", default="1,2,4,8,16,32", help="fusion depths of the k-sweep workload")
     ap.add_argument("--roads", type=int, default=4096)

@@ -113,6 +113,22 @@ int nasch_create(int64_t L, int64_t N, int vmax, double p, uint64_t seed, nasch_
 /* As nasch_create with every parameter of nasch_params. */
 int nasch_create_ex(const nasch_params *prm, nasch_handle *out);
 
+/* An open road (Handout, "Variations": other boundary conditions): cells
+ * 0..L-1 with an entry before cell 0 and an exit after cell L-1 instead of
+ * the ring.  Each step: the exit is open with probability beta (word 0 of
+ * Philox with counter (0, step, road, 2) below ceil(beta * 2^32)); the
+ * leading car then sees an unbounded road, else the road's end; the four
+ * rules move every car as on the ring, and a car whose move passes cell L-1
+ * leaves (counted in the step's crossings); then, if cell 0 is empty, a car
+ * enters it at rest with probability alpha (counter (0, step, road, 3)).
+ * The road starts with N cars placed as by nasch_create.  Grid layout only
+ * (layout AUTO or GRID; AGENT is NASCH_EINVAL), one step per launch (k and
+ * tile are ignored), any L >= 1.  The car count changes: read the state
+ * with nasch_read_grid (nasch_read_state is NASCH_EINVAL);
+ * nasch_set_state takes any N in 0..L.  NASCH_EINVAL also for alpha or beta
+ * outside [0, 1]. */
+int nasch_create_open(const nasch_params *prm, double alpha, double beta, nasch_handle *out);
+
 /* Replace the state: N cars (N must equal the handle's N) at positions
  * x_host[0..N-1] (distinct, in [0, L), in cyclic order: a rotation of an
  * increasing sequence) with velocities v_host[0..N-1] <= vmax; the next

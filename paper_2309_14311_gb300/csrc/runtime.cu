@@ -178,6 +178,9 @@ struct nasch_road {
     uint64_t stats_first = 0;
     unsigned long long *d_sum = nullptr, *d_cross = nullptr;
     int64_t stats_cap = 0;
+    // open road (nasch_create_open): grid layout, one step per launch
+    bool open = false;
+    uint64_t thr_entry = 0, thr_exit = 0;
     // output (nasch_run_output), made on first use: two staging copies of
     // the cells, a copy stream and the events that order them
     int8_t *stage[2] = {nullptr, nullptr};
@@ -366,6 +369,26 @@ int run_steps(nasch_road *h, int64_t steps)
                 done += kk;
             }
         }
+    } else if (h->open) {
+        GridStep g;
+        g.status = h->d_status;
+        g.rc = rc;
+        for (int64_t done = 0; done < steps; ++done) {
+            const uint32_t step = (uint32_t)(h->step + (uint64_t)done);
+            const uint32_t k0 = (uint32_t)h->seed, k1 = (uint32_t)(h->seed >> 32);
+            // the step's exit and entry draws (counter words 3: tags 2 and 3)
+            const bool exit_open = (uint64_t)philox4x32_10(0u, step, h->road, 2u, k0, k1).w0 < h->thr_exit;
+            const bool entry = (uint64_t)philox4x32_10(0u, step, h->road, 3u, k0, k1).w0 < h->thr_entry;
+            g.c_in = h->cells[h->cur];
+            g.c_out = h->cells[h->cur ^ 1];
+            g.step0 = step;
+            g.ksteps = 1;
+            g.sum_v = sum + done;
+            g.crossings = cross + done;
+            e = launch_grid_open(g, exit_open, entry, h->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "open road kernel");
+            h->cur ^= 1;
+        }
     } else {
         GridStep g;
         g.status = h->d_status;
@@ -389,33 +412,8 @@ int run_steps(nasch_road *h, int64_t steps)
     return NASCH_OK;
 }
 
-}  // namespace
-
-extern "C" {
-
-void nasch_params_init(nasch_params *prm)
+int create_road(const nasch_params *prm, bool open, uint64_t thr_entry, uint64_t thr_exit, nasch_handle *out)
 {
-    if (!prm) return;
-    std::memset(prm, 0, sizeof(*prm));
-    prm->vmax = 5;
-    prm->layout = NASCH_LAYOUT_AUTO;
-}
-
-const char *nasch_last_error(void) { return g_last_error.c_str(); }
-
-uint64_t nasch_slow_threshold(double p) { return slow_threshold(p); }
-
-int nasch_floyd_init(int64_t L, int64_t N, uint64_t seed, uint32_t road_id, int32_t *x_host)
-{
-    clear_error();
-    if (!x_host && N > 0) return fail(NASCH_EINVAL, "x_host is NULL");
-    return floyd_init_host(L, N, seed, road_id, x_host);
-}
-
-int nasch_create_ex(const nasch_params *prm, nasch_handle *out)
-{
-    clear_error();
-    TraceRange trace("nasch_create");
     if (!out) return fail(NASCH_EINVAL, "out is NULL");
     *out = nullptr;
     int st = validate_params(prm);
@@ -430,6 +428,9 @@ int nasch_create_ex(const nasch_params *prm, nasch_handle *out)
     h->seed = prm->seed;
     h->road = prm->road_id;
     h->layout = choose_layout(prm);
+    h->open = open;
+    h->thr_entry = thr_entry;
+    h->thr_exit = thr_exit;
     st = device_info(&h->device, &h->sms);
     if (st) {
         delete h;
@@ -468,14 +469,14 @@ int nasch_create_ex(const nasch_params *prm, nasch_handle *out)
             free_road(h);
             return fail(NASCH_EINVAL, "grid tile must be %d", kGridTileCells);
         }
-        h->ring = prm->tile == 0 && h->L <= kGridRingMaxCells;
+        h->ring = !open && prm->tile == 0 && h->L <= kGridRingMaxCells;
         h->tile = kGridTileCells;
-        h->k = prm->k ? prm->k : 8;
+        h->k = open ? 1 : (prm->k ? prm->k : 8);
         // the halo round_up(k * vmax, 16) on each side must leave the tile cells
         // of its own: clamp k so that 2 * halo < the staged span
         const int kfit = h->vmax > 0 ? std::max(1, ((kGridSpan / 2 - 16) / h->vmax)) : kMaxFusedSteps;
         h->k = std::min(h->k, kfit);
-        if (!h->ring && h->L < (int64_t)kGridSpan) {
+        if (!open && !h->ring && h->L < (int64_t)kGridSpan) {
             free_road(h);
             return fail(NASCH_EINVAL, "L=%lld too short for the tiled grid kernel (needs L >= %d)",
                         (long long)h->L, kGridSpan);
@@ -512,6 +513,51 @@ int nasch_create_ex(const nasch_params *prm, nasch_handle *out)
     return NASCH_OK;
 }
 
+}  // namespace
+
+extern "C" {
+
+void nasch_params_init(nasch_params *prm)
+{
+    if (!prm) return;
+    std::memset(prm, 0, sizeof(*prm));
+    prm->vmax = 5;
+    prm->layout = NASCH_LAYOUT_AUTO;
+}
+
+const char *nasch_last_error(void) { return g_last_error.c_str(); }
+
+uint64_t nasch_slow_threshold(double p) { return slow_threshold(p); }
+
+int nasch_floyd_init(int64_t L, int64_t N, uint64_t seed, uint32_t road_id, int32_t *x_host)
+{
+    clear_error();
+    if (!x_host && N > 0) return fail(NASCH_EINVAL, "x_host is NULL");
+    return floyd_init_host(L, N, seed, road_id, x_host);
+}
+
+int nasch_create_ex(const nasch_params *prm, nasch_handle *out)
+{
+    clear_error();
+    TraceRange trace("nasch_create");
+    return create_road(prm, false, 0, 0, out);
+}
+
+int nasch_create_open(const nasch_params *prm, double alpha, double beta, nasch_handle *out)
+{
+    clear_error();
+    TraceRange trace("nasch_create_open");
+    if (!prm) return fail(NASCH_EINVAL, "params is NULL");
+    if (!(alpha >= 0.0 && alpha <= 1.0) || !(beta >= 0.0 && beta <= 1.0))
+        return fail(NASCH_EINVAL, "alpha=%g and beta=%g must lie in [0, 1]", alpha, beta);
+    if (prm->layout == NASCH_LAYOUT_AGENT) return fail(NASCH_EINVAL, "an open road uses the grid layout");
+    nasch_params q = *prm;
+    q.layout = NASCH_LAYOUT_GRID;
+    q.k = 1;
+    q.tile = 0;
+    return create_road(&q, true, slow_threshold(alpha), slow_threshold(beta), out);
+}
+
 int nasch_create(int64_t L, int64_t N, int vmax, double p, uint64_t seed, nasch_handle *out)
 {
     nasch_params prm;
@@ -528,14 +574,21 @@ int nasch_set_state(nasch_handle h, const int32_t *x_host, const uint8_t *v_host
 {
     clear_error();
     if (!h) return fail(NASCH_EINVAL, "handle is NULL");
-    if (N != h->N) return fail(NASCH_EINVAL, "N=%lld differs from the handle's N=%lld", (long long)N, (long long)h->N);
+    if (h->open ? (N < 0 || N > h->L) : N != h->N)
+        return fail(NASCH_EINVAL, "N=%lld: must equal the handle's N=%lld (a ring) or lie in 0..L (an open road)",
+                    (long long)N, (long long)h->N);
     if (N > 0 && (!x_host || !v_host)) return fail(NASCH_EINVAL, "NULL state array");
     int st = validate_state(h->L, N, h->vmax, x_host, v_host, h->layout == NASCH_LAYOUT_AGENT);
     if (st) return st;
     cudaError_t e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    const int64_t n_before = h->N;
+    h->N = N;
     st = upload_state(h, x_host, v_host);
-    if (st) return st;
+    if (st) {
+        h->N = n_before;
+        return st;
+    }
     h->step = step;
     h->stats_first = step;
     return NASCH_OK;
@@ -641,6 +694,7 @@ int nasch_read_state(nasch_handle h, int32_t *x_host, uint8_t *v_host, int64_t c
 {
     clear_error();
     if (!h) return fail(NASCH_EINVAL, "handle is NULL");
+    if (h->open) return fail(NASCH_EINVAL, "an open road's car count changes: read its cells with nasch_read_grid");
     if (cap < h->N) return fail(NASCH_EINVAL, "cap=%lld < N=%lld", (long long)cap, (long long)h->N);
     if (h->N > 0 && (!x_host || !v_host)) return fail(NASCH_EINVAL, "NULL output array");
     int st = sync_and_check(h);

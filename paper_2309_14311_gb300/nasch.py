@@ -92,6 +92,7 @@ def _declare(lib) -> None:
         "nasch_params_init": (None, [P]),
         "nasch_create": (ctypes.c_int, [i64, i64, ctypes.c_int, dbl, u64, P]),
         "nasch_create_ex": (ctypes.c_int, [P, P]),
+        "nasch_create_open": (ctypes.c_int, [P, dbl, dbl, P]),
         "nasch_set_state": (ctypes.c_int, [H, P, P, i64, u64]),
         "nasch_run": (ctypes.c_int, [H, i64]),
         "nasch_run_output": (ctypes.c_int, [H, i64, i64, P, i64, P, i32, i64]),
@@ -189,10 +190,14 @@ def calibrate_philox(draws_per_thread: int = 1 << 14) -> float:
 
 
 class Road:
-    """One ring road with device-resident state (a ``nasch_handle``)."""
+    """One road with device-resident state (a ``nasch_handle``): a ring, or
+    with ``open=(alpha, beta)`` an open road (entry before cell 0 with
+    probability alpha, exit after cell L-1 open with probability beta; grid
+    layout, one step per launch)."""
 
     def __init__(self, L: int, N: int, vmax: int = 5, p: float = 0.0, seed: int = 0, road_id: int = 0,
-                 layout: str | int = "auto", k: int = 0, tile: int = 0, stream=None):
+                 layout: str | int = "auto", k: int = 0, tile: int = 0, stream=None,
+                 open: tuple[float, float] | None = None):
         lib = load()
         prm = Params()
         lib.nasch_params_init(ctypes.byref(prm))
@@ -202,7 +207,10 @@ class Road:
         prm.stream = _stream_handle(stream)
         self._stream_ref = stream
         h = ctypes.c_void_p()
-        _check(lib.nasch_create_ex(ctypes.byref(prm), ctypes.byref(h)))
+        if open is None:
+            _check(lib.nasch_create_ex(ctypes.byref(prm), ctypes.byref(h)))
+        else:
+            _check(lib.nasch_create_open(ctypes.byref(prm), float(open[0]), float(open[1]), ctypes.byref(h)))
         self._h = h
         self.L, self.N, self.vmax, self.p, self.seed, self.road_id = L, N, vmax, p, seed, road_id
 
