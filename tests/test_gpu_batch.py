@@ -100,14 +100,14 @@ def test_order_and_fusion_depth_do_not_matter():
 
 
 def test_uneven_ensemble_subset():
-    """The 160 smallest-work roads of the seed-7 ensemble, full length, against
-    the oracle, and 8 larger ones checked on light-cone windows of cars."""
+    """The 256 smallest-work roads of the seed-7 ensemble, full length, against
+    the oracle, and 16 others checked on light-cone windows of cars."""
     rows = WL.uneven_ensemble()
     order = sorted(range(len(rows)), key=lambda i: rows[i]["N"] * rows[i]["T"])
-    small = order[:160]
+    small = order[:256]
     rng = np.random.default_rng(5)
-    mids = [i for i in order[160:] if rows[i]["T"] <= 3000 and rows[i]["N"] > 2048]
-    big = list(rng.choice(mids, 8, replace=False))
+    mids = [i for i in order[256:] if rows[i]["T"] <= 3000 and rows[i]["N"] > 2048]
+    big = list(rng.choice(mids, 16, replace=False))
     pick = small + big
     roads = [WL.road_params(rows[i]) for i in pick]
     steps = [rows[i]["T"] for i in pick]
@@ -143,6 +143,64 @@ def test_fundamental_diagram_subset_matches_oracle():
         b.wait()
         for i in range(0, len(roads), 5):
             check_road(b, i, dict(roads[i], T=T))
+
+
+def _invariants(b, i, r):
+    """Car count, distinct cells, velocities within vmax, and the statistics'
+    length, on a road of the batch."""
+    cells = b.read_grid(i)
+    occ = cells >= 0
+    assert int(occ.sum()) == r["N"], (i, "car count")
+    assert int(cells[occ].max(initial=0)) <= r["vmax"], (i, "vmax")
+    sv, cr = b.stats(i)
+    assert len(sv) == r["T"] and len(cr) == r["T"]
+    return cells
+
+
+def test_fundamental_diagram_full_size():
+    """The sweep at full size: one replica per (density, p), L = 10^6, T =
+    12000, in the layouts the batch picks.  Every road: invariants, and the
+    same cells and statistics when every road is forced into the other
+    layout.  Every fourth road: light-cone windows of 40 cars after the 12000
+    steps against the oracle run from the same start."""
+    roads = WL.fundamental_diagram_roads(replicas=1)
+    T = WL.FD_T
+    with NS.Batch(roads, [T] * len(roads)) as b:
+        b.wait()
+        layouts = [b.layout(i) for i in range(len(roads))]
+        assert NS.LAYOUT_AGENT in layouts and NS.LAYOUT_GRID in layouts
+        cells = [_invariants(b, i, dict(r, T=T)) for i, r in enumerate(roads)]
+        stats = [b.stats(i) for i in range(len(roads))]
+    other = [dict(r, layout="grid" if lay == NS.LAYOUT_AGENT else "agent") for r, lay in zip(roads, layouts)]
+    with NS.Batch(other, [T] * len(other)) as b2:
+        b2.wait()
+        for i in range(len(other)):
+            assert np.array_equal(b2.read_grid(i), cells[i]), (i, "layout")
+            sv, cr = b2.stats(i)
+            assert np.array_equal(sv, stats[i][0]) and np.array_equal(cr, stats[i][1]), (i, "layout stats")
+    rng = np.random.default_rng(12)
+    for i in range(0, len(roads), 4):
+        r = roads[i]
+        x0 = O.floyd_init(r["L"], r["N"], r["seed"], r["road_id"])
+        M = T + 40
+        start = int(rng.integers(0, r["N"]))
+        idx = (start + np.arange(M)) % r["N"]
+        wx, wv = O.agent_segment(r["L"], x0[idx], np.zeros(M, np.uint8), r["vmax"], r["p"], r["seed"],
+                                 r["road_id"], 0, T, openmp=True)
+        assert np.array_equal(cells[i][wx], wv.astype(np.int8)), (i, "window")
+
+
+@pytest.mark.parametrize("layout", ["agent", "grid"])
+def test_reference_case_thousand_seeds(layout):
+    """The handout's reference case (200 cars on 1000 cells, p = 0.13, vmax =
+    5, 1000 steps) for seeds 1..1000, all in one batch, against the oracle."""
+    s = WL.REFERENCE_CASE
+    roads = [dict(L=s.L, N=s.N, vmax=s.vmax, p=s.p, seed=seed, road_id=0, layout=layout)
+             for seed in range(1, 1001)]
+    with NS.Batch(roads, [s.T] * len(roads)) as b:
+        b.wait()
+        for i, r in enumerate(roads):
+            check_road(b, i, dict(r, T=s.T))
 
 
 def test_wait_timeout_and_cancel():
