@@ -89,11 +89,6 @@ cudaError_t launch_grid_tiled(const GridStep &g, int blocks, cudaStream_t s);
 cudaError_t launch_grid_ring(const GridStep &g, cudaStream_t s);
 
 // cells[x[i]] = v[i] for i < N into a grid already filled with -1.
-// One step of an open road (grid layout; see open_kernels.cu): the exit's
-// and the entry's outcomes for the step are decided by the caller.
-cudaError_t launch_grid_open(const GridStep &g, bool exit_open, bool entry, cudaStream_t s);
-// One row of the space-time raster from a road's cells (see output_kernels.cu).
-cudaError_t launch_raster_row(const int8_t *cells, uint32_t L, uint32_t W, uint8_t *row, int sms, cudaStream_t s);
 cudaError_t launch_scatter_agent_to_grid(const int32_t *x, const uint8_t *v, uint32_t N,
                                          int8_t *cells, cudaStream_t s);
 // Philox of n counters (testing).

@@ -17,6 +17,7 @@
 // ring's fused kernels), lets a car enter on cell 0, and writes the tile.
 #include <atomic>
 
+#include "road_output.h"
 #include "tile_device.cuh"
 
 namespace nasch {

@@ -4,7 +4,7 @@
 // Pixel i of a row of W pixels covers the cells c with floor(c * W / L) = i,
 // that is [ceil(i L / W), ceil((i + 1) L / W)), and holds
 // floor(255 * cars / cells) of that range: 0 empty, 255 full.
-#include "kernels.h"
+#include "road_output.h"
 
 namespace nasch {
 namespace {

@@ -11,10 +11,13 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <atomic>
+#include <thread>
 #include <vector>
 
 #include "nasch.h"
 #include "kernels.h"
+#include "road_output.h"
 #include "runtime_internal.h"
 
 namespace nasch {
@@ -121,15 +124,58 @@ int floyd_init_host(int64_t L, int64_t N, uint64_t seed, uint32_t road, int32_t 
 // sequence (the cars' cyclic order on the ring).
 int validate_state(int64_t L, int64_t N, int vmax, const int32_t *x, const uint8_t *v, bool need_cyclic)
 {
-    int64_t descents = 0;
-    for (int64_t i = 0; i < N; ++i) {
-        if (x[i] < 0 || x[i] >= L) return fail(NASCH_EINVAL, "x[%lld]=%d outside [0, L)", (long long)i, x[i]);
-        if (v[i] > vmax) return fail(NASCH_EINVAL, "v[%lld]=%d above vmax=%d", (long long)i, v[i], vmax);
-        if (N >= 2) {
-            const int32_t nx = x[(i + 1) % N];
-            if (nx == x[i]) return fail(NASCH_EINVAL, "two cars on cell %d", x[i]);
-            if (nx < x[i]) ++descents;
+    // One pass over the cars, split over the host's cores: each chunk finds
+    // its first bad car (a cell outside the road, a velocity above vmax, the
+    // same cell as the next car) and counts the descents of x (the ring
+    // order allows exactly one).  The first bad car of the lowest chunk is
+    // reported.
+    struct Part {
+        int64_t bad = -1;   // index of the first bad car
+        int kind = 0;       // 1 cell, 2 velocity, 3 same cell as the next
+        int64_t descents = 0;
+    };
+    const int64_t chunk = int64_t(1) << 22;
+    const int64_t n_parts = N == 0 ? 0 : (N + chunk - 1) / chunk;
+    std::vector<Part> parts((size_t)n_parts);
+    auto work = [&](int64_t part) {
+        Part &r = parts[(size_t)part];
+        const int64_t a = part * chunk, b = std::min(N, a + chunk);
+        for (int64_t i = a; i < b; ++i) {
+            const int32_t xi = x[i];
+            const int32_t nx = i + 1 < N ? x[i + 1] : x[0];
+            int kind = 0;
+            if (xi < 0 || xi >= L) kind = 1;
+            else if (v[i] > vmax) kind = 2;
+            else if (N >= 2 && nx == xi) kind = 3;
+            if (kind) {
+                r.bad = i;
+                r.kind = kind;
+                return;
+            }
+            r.descents += (N >= 2 && nx < xi) ? 1 : 0;
         }
+    };
+    const int64_t workers = std::min<int64_t>(n_parts, std::max(1u, std::thread::hardware_concurrency()));
+    if (workers <= 1) {
+        for (int64_t q = 0; q < n_parts; ++q) work(q);
+    } else {
+        std::atomic<int64_t> next{0};
+        std::vector<std::thread> pool;
+        for (int64_t t = 0; t < workers; ++t)
+            pool.emplace_back([&]() {
+                for (int64_t q = next.fetch_add(1); q < n_parts; q = next.fetch_add(1)) work(q);
+            });
+        for (auto &th : pool) th.join();
+    }
+    int64_t descents = 0;
+    for (const Part &r : parts) {
+        if (r.bad >= 0) {
+            const int64_t i = r.bad;
+            if (r.kind == 1) return fail(NASCH_EINVAL, "x[%lld]=%d outside [0, L)", (long long)i, x[i]);
+            if (r.kind == 2) return fail(NASCH_EINVAL, "v[%lld]=%d above vmax=%d", (long long)i, v[i], vmax);
+            return fail(NASCH_EINVAL, "two cars on cell %d", x[i]);
+        }
+        descents += r.descents;
     }
     if (N >= 2 && need_cyclic && descents != 1)
         return fail(NASCH_EINVAL, "positions are not in cyclic order (%lld descents)", (long long)descents);
