@@ -74,6 +74,17 @@ def test_errors_are_reported_not_raised_across_the_abi(lib):
     assert st == NS.EINVAL and b"vmax" in lib.nasch_last_error()
     st = lib.nasch_create(10, 5, 5, 1.5, 1, ctypes.byref(h))
     assert st == NS.EINVAL and b"p=" in lib.nasch_last_error()
+    # open roads: alpha and beta in [0, 1], grid layout only (checked before any device work)
+    prm = NS.Params()
+    lib.nasch_params_init(ctypes.byref(prm))
+    prm.L, prm.N, prm.vmax, prm.p = 1000, 10, 5, 0.1
+    for a, b in ((-0.5, 0.5), (0.5, 2.0), (float("nan"), 0.5)):
+        assert lib.nasch_create_open(ctypes.byref(prm), a, b, ctypes.byref(h)) == NS.EINVAL
+        assert b"alpha" in lib.nasch_last_error()
+    prm.layout = NS.LAYOUTS["agent"]
+    assert lib.nasch_create_open(ctypes.byref(prm), 0.5, 0.5, ctypes.byref(h)) == NS.EINVAL
+    assert b"grid layout" in lib.nasch_last_error()
+    assert lib.nasch_run_output(None, 10, 5, None, 0, None, 0, 0) == NS.EINVAL
 
 
 def test_no_gpu_fails_loudly(lib):
