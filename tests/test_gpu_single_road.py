@@ -254,7 +254,7 @@ def test_large_road_full_size(large_init):
         svT, _ = r.stats()
         assert len(svT) == s.T
     # the grid layout in both launch configurations the benchmark times:
-    # one step per launch (mask-step kernel) and the fused depth
+    # one step per launch (the one-step list kernel) and the fused depth
     order = np.argsort(xa, kind="stable")
     for kg in (1, WL.LARGE_ROAD_K["grid"]):
         with NS.Road(s.L, s.N, s.vmax, s.p, s.seed, layout="grid", k=kg) as g:
