@@ -10,13 +10,15 @@
 // (status word), and results leave by bulk stores.  Rule 2 makes every
 // scatter collision-free.  The first and last tiles take their halo across
 // the ring boundary (modular cell index, plain loads).
-//  - grid_tiled_kernel (k >= 2, or vmax > 16): 8192-cell spans,
-//    H = round_up(k vmax, 16);
-//    the span's cars become a sorted (position, velocity) list, k steps run
-//    on the list as in the agent form, and the list is scattered back.
 //  - grid_k1_kernel (k = 1, vmax <= 16): independent warps on 3040-cell
 //    tiles stepped in place; a warp car list sorted by cell, padded to whole
 //    groups of 32, gaps from the next entry.
+//  - grid_warp_kernel (the rest with H = round_up(k vmax, 16) <= 512):
+//    independent warps on 2048-cell spans; the span's cars become a sorted
+//    list, the k steps run on the list (grid_warp_steps) and the cars of the
+//    tile's own cells are scattered back.
+//  - grid_tiled_kernel (H > 512): the same on 8192-cell spans by a whole
+//    block.
 // Statistics of the cars that start a step in a tile's own cells are
 // reduced per warp (and block) and added to the per-step series.
 //
@@ -150,7 +152,7 @@ __global__ void __launch_bounds__(kGridThreads) grid_tiled_kernel(const GridStep
 //      followed by a dummy car in the padding after the span, up to a
 //      multiple of 32 entries and one more;
 //   3. with every car listed, the span is cleared to -1;
-//   4. the lanes take the list 32 cars at a time, two groups interleaved, so
+//   4. the lanes take the list 32 cars at a time, three groups interleaved, so
 //      every lane draws for the same number of cars; a car's leader is the
 //      next list entry, so its gap is the difference of the two indices
 //      less one; each car is scattered back into the span (in place).
@@ -161,8 +163,9 @@ __global__ void __launch_bounds__(kGridThreads) grid_tiled_kernel(const GridStep
 // (beyond the span) but moves only further right.  The last owned car sees
 // its leader, or the dummy at least vmax cells ahead.
 // Two buffers alternate: the tile being stepped and the next tile, whose
-// copy is issued once the tile before has been read by its store.  The rule-3 draw uses the counter-independent
-// parts of Philox computed on the host (SlowdownKey).
+// copy is issued once the tile before has been read by its store.  The
+// rule-3 draw uses the counter-independent parts of Philox computed on the
+// host (SlowdownKey).
 constexpr uint32_t kK1Words = 3;                         // occupancy words (32 cells each) per lane
 constexpr uint32_t kK1Halo = 16;                         // cells staged on each side: vmax <= 16
 constexpr uint32_t kK1Span = 1024u * kK1Words;           // staged cells
@@ -181,26 +184,56 @@ struct __align__(16) K1WarpSmem {
     uint64_t full[kK1Bufs];       // bulk-copy completion, one per buffer
 };
 
-// One car: rules 1-4.  e: its list entry (span index | velocity << 16),
-// lead: the leader's entry; returns the velocity used by the move and sets
-// the car's cell on the road.
-template <Draw D>
-__device__ __forceinline__ uint32_t k1_car(uint32_t e, uint32_t lead, int8_t *span, uint32_t base, uint32_t L,
-                                           uint32_t vmax, uint32_t thr, const SlowdownKey &sk, uint32_t &cell)
+// G groups of 32 listed cars (list: the first group's entries), rules 1-4,
+// with the draws of the G groups interleaved.  A car's entry is its span
+// index | velocity << 16 and its leader is the next entry.  W: the span
+// holds cell L - 1, so cells wrap and crossings are possible (warp-uniform;
+// false on every tile but the first and the last).  The statistics take the
+// cars on the tile's own cells.
+template <int G, Draw D, bool W>
+__device__ __forceinline__ void k1_groups(const uint32_t *list, uint32_t lane, int8_t *span, uint32_t base,
+                                          uint32_t L, uint32_t vmax, uint32_t thr, const SlowdownKey &sk,
+                                          uint32_t own, uint32_t &tsum, uint32_t &tcross)
 {
-    const uint32_t r = e & 0xFFFFu;
-    const uint32_t gap = (lead & 0xFFFFu) - r - 1u;                                      // empty cells ahead
-    uint32_t vel = min(min((e >> 16) + 1u, vmax), gap);                                 // rules 1, 2
-    cell = base + r;
-    if (cell >= L) cell -= L;
-    if (D == Draw::kAlways) {
-        vel -= vel != 0u ? 1u : 0u;                                                        // rule 3, p = 1
-    } else if (D == Draw::kPhilox) {
-        const uint32_t u = slowdown_word0(cell, sk);
-        vel -= (vel != 0u && u < thr) ? 1u : 0u;                                           // rule 3
+    uint32_t e[G], lead[G];
+#pragma unroll
+    for (int q = 0; q < G; ++q) {
+        e[q] = list[32 * q + lane];
+        lead[q] = list[32 * q + lane + 1];
     }
-    span[r + vel] = (int8_t)vel;                                                           // rule 4
-    return vel;
+#pragma unroll
+    for (int q = 0; q < G; ++q) {
+        const uint32_t r = e[q] & 0xFFFFu;
+        const uint32_t gap = (lead[q] & 0xFFFFu) - r - 1u;                                // empty cells ahead
+        uint32_t vel = min(min((e[q] >> 16) + 1u, vmax), gap);                            // rules 1, 2
+        uint32_t cell = base + r;
+        if (W && cell >= L) cell -= L;
+        if (D == Draw::kAlways) {
+            vel -= vel != 0u ? 1u : 0u;                                                    // rule 3, p = 1
+        } else if (D == Draw::kPhilox) {
+            const uint32_t u = slowdown_word0(cell, sk);
+            vel -= (vel != 0u && u < thr) ? 1u : 0u;                                       // rule 3
+        }
+        span[r + vel] = (int8_t)vel;                                                       // rule 4
+        const bool mine = r - kK1Halo < own;
+        tsum += mine ? vel : 0u;
+        if (W) tcross += (mine && cell + vel >= L) ? 1u : 0u;
+    }
+}
+
+// All `padded` listed cars (a multiple of 32), three groups at a time.
+template <Draw D, bool W>
+__device__ __forceinline__ void k1_cars(const uint32_t *list, uint32_t padded, uint32_t lane, int8_t *span,
+                                        uint32_t base, uint32_t L, uint32_t vmax, uint32_t thr,
+                                        const SlowdownKey &sk, uint32_t own, uint32_t &tsum, uint32_t &tcross)
+{
+    uint32_t gi = 0;
+    for (; gi + 96u <= padded; gi += 96u)
+        k1_groups<3, D, W>(list + gi, lane, span, base, L, vmax, thr, sk, own, tsum, tcross);
+    if (padded - gi == 64u)
+        k1_groups<2, D, W>(list + gi, lane, span, base, L, vmax, thr, sk, own, tsum, tcross);
+    else if (padded - gi == 32u)
+        k1_groups<1, D, W>(list + gi, lane, span, base, L, vmax, thr, sk, own, tsum, tcross);
 }
 
 template <Draw D>
@@ -320,24 +353,11 @@ __global__ void __launch_bounds__(32 * kK1Warps) grid_k1_kernel(const GridStep g
                 }
                 __syncwarp();
             }
-            // 4. the cars, 32 at a time, two groups interleaved
-            for (uint32_t gi = 0; gi < padded; gi += 64u) {
-                uint32_t cell0, cell1;
-                const uint32_t e0 = w.list[gi + lane], l0 = w.list[gi + lane + 1u];
-                if (gi + 32u < padded) {   // warp-uniform
-                    const uint32_t e1 = w.list[gi + 32u + lane], l1 = w.list[gi + 33u + lane];
-                    const uint32_t v0 = k1_car<D>(e0, l0, out, base, L, vmax, thr, sk, cell0);
-                    const uint32_t v1 = k1_car<D>(e1, l1, out, base, L, vmax, thr, sk, cell1);
-                    const bool own0 = (e0 & 0xFFFFu) - kK1Halo < own, own1 = (e1 & 0xFFFFu) - kK1Halo < own;
-                    tsum += (own0 ? v0 : 0u) + (own1 ? v1 : 0u);
-                    if (wraps) tcross += (own0 && cell0 + v0 >= L ? 1u : 0u) + (own1 && cell1 + v1 >= L ? 1u : 0u);
-                } else {
-                    const uint32_t v0 = k1_car<D>(e0, l0, out, base, L, vmax, thr, sk, cell0);
-                    const bool own0 = (e0 & 0xFFFFu) - kK1Halo < own;
-                    tsum += own0 ? v0 : 0u;
-                    if (wraps) tcross += own0 && cell0 + v0 >= L ? 1u : 0u;
-                }
-            }
+            // 4. the cars, 32 at a time, three groups interleaved
+            if (wraps)
+                k1_cars<D, true>(w.list, padded, lane, out, base, L, vmax, thr, sk, own, tsum, tcross);
+            else
+                k1_cars<D, false>(w.list, padded, lane, out, base, L, vmax, thr, sk, own, tsum, tcross);
             __syncwarp();   // the list is rewritten by the next pass
         }
         // 5. the result leaves by bulk store (or plain stores for a short last tile)
