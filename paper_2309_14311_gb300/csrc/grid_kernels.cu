@@ -148,14 +148,16 @@ __global__ void __launch_bounds__(kGridThreads) grid_tiled_kernel(const GridStep
 //   1. each lane turns its 32 * kK1Words cells into occupancy bits and counts
 //      its cars;
 //   2. a warp prefix sum gives each lane its slots in the car list: the
-//      span index and velocity of every car of the span in ascending order,
-//      followed by a dummy car in the padding after the span, up to a
-//      multiple of 32 entries and one more;
-//   3. with every car listed, the span is cleared to -1;
-//   4. the lanes take the list 32 cars at a time, three groups interleaved, so
-//      every lane draws for the same number of cars; a car's leader is the
-//      next list entry, so its gap is the difference of the two indices
-//      less one; each car is scattered back into the span (in place).
+//      span index of every car of the span in ascending order, followed by
+//      dummy cars in the padding after the span, up to a multiple of 32
+//      entries and one more;
+//   3. the lanes take the list 32 cars at a time, three groups interleaved,
+//      so every lane draws for the same number of cars; a car's leader is
+//      the next list entry, so its gap is the difference of the two indices
+//      less one.  Each car reads its velocity from its cell, empties the
+//      cell and writes its new velocity at its new cell (in place): no other
+//      car writes a car's cell in the same step, since the car behind stops
+//      before it and every destination is an empty cell or the car's own.
 // Only the cars the tile owns are counted in the statistics; the others
 // (halo cars, the dummy) are stepped with the rest and their results fall
 // outside the cells written back: a car in the left halo may move into the
@@ -173,39 +175,43 @@ constexpr uint32_t kK1Cells = kK1Span - 2u * kK1Halo;    // cells written per wa
 constexpr uint32_t kK1Buf = kK1Span + 32u;               // + padding: the dummy car's and halo cars' moves
 constexpr uint32_t kK1ListCap = 112u * kK1Words / 32u * 32u;   // cars per pass; a denser tile is done in passes
 constexpr uint32_t kK1ListLen = kK1ListCap + 32u;        // + padding to whole groups and one leader
-constexpr uint32_t kK1Dummy = kK1Span;                   // span index of the dummy car (padding), velocity 0
+constexpr uint32_t kK1Dummy = kK1Span;                   // span index of the dummy cars (padding)
 constexpr uint32_t kK1Bufs = 2;
+constexpr int8_t kEmptyCell = -1;
 constexpr int kK1Warps = 4;                              // warps per block
 static_assert(kK1ListCap % 32u == 0u, "whole groups");
 
 struct __align__(16) K1WarpSmem {
     int8_t buf[kK1Bufs][kK1Buf];
-    uint32_t list[kK1ListLen];    // span index | velocity << 16
+    uint16_t list[kK1ListLen];    // span index of each listed car
     uint64_t full[kK1Bufs];       // bulk-copy completion, one per buffer
 };
 
 // G groups of 32 listed cars (list: the first group's entries), rules 1-4,
 // with the draws of the G groups interleaved.  A car's entry is its span
-// index | velocity << 16 and its leader is the next entry.  W: the span
-// holds cell L - 1, so cells wrap and crossings are possible (warp-uniform;
-// false on every tile but the first and the last).  The statistics take the
-// cars on the tile's own cells.
+// index and its leader is the next entry; its velocity is read from `span`
+// and its result written to `out` (the same buffer when stepping in place).
+// W: the span holds cell L - 1, so cells wrap and crossings are possible
+// (warp-uniform; false on every tile but the first and the last).  The
+// statistics take the cars on the tile's own cells.
 template <int G, Draw D, bool W>
-__device__ __forceinline__ void k1_groups(const uint32_t *list, uint32_t lane, int8_t *span, uint32_t base,
-                                          uint32_t L, uint32_t vmax, uint32_t thr, const SlowdownKey &sk,
-                                          uint32_t own, uint32_t &tsum, uint32_t &tcross)
+__device__ __forceinline__ void k1_groups(const uint16_t *list, uint32_t lane, const int8_t *span, int8_t *out,
+                                          uint32_t base, uint32_t L, uint32_t vmax, uint32_t thr,
+                                          const SlowdownKey &sk, uint32_t own, uint32_t &tsum, uint32_t &tcross)
 {
-    uint32_t e[G], lead[G];
+    uint32_t rr[G], lead[G], v0[G];
 #pragma unroll
     for (int q = 0; q < G; ++q) {
-        e[q] = list[32 * q + lane];
+        rr[q] = list[32 * q + lane];
         lead[q] = list[32 * q + lane + 1];
     }
 #pragma unroll
+    for (int q = 0; q < G; ++q) v0[q] = (uint8_t)span[rr[q]];   // every read before any write of the groups
+#pragma unroll
     for (int q = 0; q < G; ++q) {
-        const uint32_t r = e[q] & 0xFFFFu;
-        const uint32_t gap = (lead[q] & 0xFFFFu) - r - 1u;                                // empty cells ahead
-        uint32_t vel = min(min((e[q] >> 16) + 1u, vmax), gap);                            // rules 1, 2
+        const uint32_t r = rr[q];
+        const uint32_t gap = lead[q] - r - 1u;                                            // empty cells ahead
+        uint32_t vel = min(min(v0[q] + 1u, vmax), gap);                                   // rules 1, 2
         uint32_t cell = base + r;
         if (W && cell >= L) cell -= L;
         if (D == Draw::kAlways) {
@@ -214,7 +220,8 @@ __device__ __forceinline__ void k1_groups(const uint32_t *list, uint32_t lane, i
             const uint32_t u = slowdown_word0(cell, sk);
             vel -= (vel != 0u && u < thr) ? 1u : 0u;                                       // rule 3
         }
-        span[r + vel] = (int8_t)vel;                                                       // rule 4
+        out[r] = kEmptyCell;                                                              // rule 4
+        out[r + vel] = (int8_t)vel;
         const bool mine = r - kK1Halo < own;
         tsum += mine ? vel : 0u;
         if (W) tcross += (mine && cell + vel >= L) ? 1u : 0u;
@@ -223,17 +230,17 @@ __device__ __forceinline__ void k1_groups(const uint32_t *list, uint32_t lane, i
 
 // All `padded` listed cars (a multiple of 32), three groups at a time.
 template <Draw D, bool W>
-__device__ __forceinline__ void k1_cars(const uint32_t *list, uint32_t padded, uint32_t lane, int8_t *span,
-                                        uint32_t base, uint32_t L, uint32_t vmax, uint32_t thr,
+__device__ __forceinline__ void k1_cars(const uint16_t *list, uint32_t padded, uint32_t lane, const int8_t *span,
+                                        int8_t *out, uint32_t base, uint32_t L, uint32_t vmax, uint32_t thr,
                                         const SlowdownKey &sk, uint32_t own, uint32_t &tsum, uint32_t &tcross)
 {
     uint32_t gi = 0;
     for (; gi + 96u <= padded; gi += 96u)
-        k1_groups<3, D, W>(list + gi, lane, span, base, L, vmax, thr, sk, own, tsum, tcross);
+        k1_groups<3, D, W>(list + gi, lane, span, out, base, L, vmax, thr, sk, own, tsum, tcross);
     if (padded - gi == 64u)
-        k1_groups<2, D, W>(list + gi, lane, span, base, L, vmax, thr, sk, own, tsum, tcross);
+        k1_groups<2, D, W>(list + gi, lane, span, out, base, L, vmax, thr, sk, own, tsum, tcross);
     else if (padded - gi == 32u)
-        k1_groups<1, D, W>(list + gi, lane, span, base, L, vmax, thr, sk, own, tsum, tcross);
+        k1_groups<1, D, W>(list + gi, lane, span, out, base, L, vmax, thr, sk, own, tsum, tcross);
 }
 
 template <Draw D>
@@ -250,6 +257,7 @@ __global__ void __launch_bounds__(32 * kK1Warps) grid_k1_kernel(const GridStep g
         for (uint32_t b = 0; b < kK1Bufs; ++b) mbar_init(&w.full[b], 1);
         fence_mbar_init();
     }
+    for (uint32_t b = 0; b < kK1Bufs; ++b) w.buf[b][kK1Span + lane] = kEmptyCell;   // the dummies' cells
     __syncthreads();
 
     auto bulk_ok = [&](uint32_t t) {
@@ -322,7 +330,6 @@ __global__ void __launch_bounds__(32 * kK1Warps) grid_k1_kernel(const GridStep g
 #pragma unroll
             for (uint32_t k = 0; k < 2u * kK1Words; ++k) reinterpret_cast<uint4 *>(out)[lane + 32u * k] = kEmpty4;
         }
-        auto entry = [&](uint32_t r) { return r | (uint32_t)(uint8_t)span[r] << 16; };
         for (uint32_t chunk = 0; chunk == 0u || chunk < total; chunk += kK1ListCap) {
             const uint32_t count = total > chunk ? min(kK1ListCap, total - chunk) : 0u;
             const uint32_t padded = (count + 31u) & ~31u;
@@ -330,22 +337,21 @@ __global__ void __launch_bounds__(32 * kK1Warps) grid_k1_kernel(const GridStep g
             if (!dense) {
 #pragma unroll
                 for (uint32_t j = 0; j < kK1Words; ++j)
-                    for (uint32_t mm = m[j]; mm; mm &= mm - 1u) w.list[pos++] = entry(c0 + 32u * j + __clz(__brev(mm)));
+                    for (uint32_t mm = m[j]; mm; mm &= mm - 1u)
+                        w.list[pos++] = (uint16_t)(c0 + 32u * j + __clz(__brev(mm)));
             } else {   // ranks chunk .. chunk + count (the last one: the pass's leader entry)
 #pragma unroll
                 for (uint32_t j = 0; j < kK1Words; ++j)
                     for (uint32_t mm = m[j]; mm; mm &= mm - 1u, ++pos)
-                        if (pos - chunk <= count) w.list[pos - chunk] = entry(c0 + 32u * j + __clz(__brev(mm)));
+                        if (pos - chunk <= count) w.list[pos - chunk] = (uint16_t)(c0 + 32u * j + __clz(__brev(mm)));
             }
             // dummies after the last car, and the leader of the last group
             // (a pass before the last is a whole number of groups, its leader entry a car)
-            if (chunk + count == total && lane <= padded - count) w.list[count + lane] = kK1Dummy;
+            if (chunk + count == total && lane <= padded - count) w.list[count + lane] = (uint16_t)kK1Dummy;
             __syncwarp();
             if (!dense) {
-                // 3. every car is listed: clear the span, and copy the next tile
-                // into the other buffer once the store of the tile before has read it
-#pragma unroll
-                for (uint32_t k = 0; k < 2u * kK1Words; ++k) reinterpret_cast<uint4 *>(span)[lane + 32u * k] = kEmpty4;
+                // every car is listed: copy the next tile into the other
+                // buffer once the store of the tile before has read it
                 if (lane == 0) {
                     bulk_wait_read_all();
                     const uint32_t nx = tile + nw;
@@ -353,14 +359,14 @@ __global__ void __launch_bounds__(32 * kK1Warps) grid_k1_kernel(const GridStep g
                 }
                 __syncwarp();
             }
-            // 4. the cars, 32 at a time, three groups interleaved
+            // 3. the cars, 32 at a time, three groups interleaved
             if (wraps)
-                k1_cars<D, true>(w.list, padded, lane, out, base, L, vmax, thr, sk, own, tsum, tcross);
+                k1_cars<D, true>(w.list, padded, lane, span, out, base, L, vmax, thr, sk, own, tsum, tcross);
             else
-                k1_cars<D, false>(w.list, padded, lane, out, base, L, vmax, thr, sk, own, tsum, tcross);
+                k1_cars<D, false>(w.list, padded, lane, span, out, base, L, vmax, thr, sk, own, tsum, tcross);
             __syncwarp();   // the list is rewritten by the next pass
         }
-        // 5. the result leaves by bulk store (or plain stores for a short last tile)
+        // 4. the result leaves by bulk store (or plain stores for a short last tile)
         fence_proxy_async();
         __syncwarp();
         if (own == kK1Cells) {
