@@ -418,7 +418,7 @@ struct __align__(16) KwWarpSmem {
 
 template <Draw D>
 __global__ void __launch_bounds__(32 * kKwWarps) grid_warp_kernel(const GridStep g, const uint32_t H,
-                                                                  const uint32_t n_tiles)
+                                                                  const uint32_t n_tiles, const SlowdownKey sk)
 {
     __shared__ KwWarpSmem s_w[kKwWarps];
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
@@ -473,7 +473,7 @@ __global__ void __launch_bounds__(32 * kKwWarps) grid_warp_kernel(const GridStep
         }
         __syncwarp();
         grid_warp_steps<D>(
-            g.rc, span, w.pos, w.vel, H, own, base, g.step0, ksteps,
+            g.rc, FoldedDraws{sk, {}}, span, w.pos, w.vel, H, own, base, g.step0, ksteps,
             [&]() {   // the next tile goes into the other buffer once the store of the tile before has read it
                 if (lane == 0) {
                     bulk_wait_read_all();
@@ -576,7 +576,8 @@ cudaError_t launch_kw_variant(const GridStep &g, uint32_t H, uint32_t n_tiles, c
     }
     const uint32_t need = (n_tiles + (uint32_t)kKwWarps - 1u) / (uint32_t)kKwWarps;
     const int grid = (int)((uint32_t)n < need ? (uint32_t)n : need);
-    grid_warp_kernel<D><<<grid, 32 * kKwWarps, 0, s>>>(g, H, n_tiles);
+    const SlowdownKey sk = make_slowdown_key(g.step0, g.rc.road, g.rc.key0, g.rc.key1);
+    grid_warp_kernel<D><<<grid, 32 * kKwWarps, 0, s>>>(g, H, n_tiles, sk);
     return cudaGetLastError();
 }
 

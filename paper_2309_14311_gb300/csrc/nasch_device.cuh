@@ -57,11 +57,13 @@ __device__ __forceinline__ uint32_t philox_word0(uint32_t c0, uint32_t c1, uint3
 // and round 3 xors a constant into word 2.  The key schedule is folded in
 // as well.  slowdown_word0(cell, make_slowdown_key(...)) equals
 // philox_word0(cell, step, road, kTagSlowdown, k0, k1) for every cell.
+// Only x2b and x3 depend on the step (slowdown_step_words).
 struct SlowdownKey {
     uint32_t k1_0;     // round 1: word 2 = hi(A * cell) ^ k1_0
     uint32_t x2a;      // round 2: word 0 = hi(B * word 2) ^ x2a
     uint32_t x2b;      // round 2: word 2 = round-1 word 3 ^ x2b
     uint32_t x3;       // round 3: word 2 = hi(A * word 0) ^ x3
+    uint32_t h0;       // round-1 output word 0 = h0 ^ step
     uint32_t k0[10];   // key word 0 of each round
     uint32_t k1[10];   // key word 1 of each round
 };
@@ -74,7 +76,8 @@ __host__ __device__ inline SlowdownKey make_slowdown_key(uint32_t step, uint32_t
         s.k1[r] = k1 + (uint32_t)r * kWeylB;
     }
     const uint64_t pb1 = (uint64_t)kMulB * road;                       // round 1, word 2's product
-    const uint32_t u0 = (uint32_t)(pb1 >> 32) ^ step ^ s.k0[0];       // round-1 output word 0
+    s.h0 = (uint32_t)(pb1 >> 32) ^ s.k0[0];
+    const uint32_t u0 = s.h0 ^ step;                                   // round-1 output word 0
     const uint32_t u1 = (uint32_t)pb1;                                 // round-1 output word 1
     const uint64_t pa2 = (uint64_t)kMulA * u0;                         // round 2, word 0's product
     s.k1_0 = s.k1[0];
@@ -84,7 +87,18 @@ __host__ __device__ inline SlowdownKey make_slowdown_key(uint32_t step, uint32_t
     return s;
 }
 
-__host__ __device__ __forceinline__ uint32_t slowdown_word0(uint32_t cell, const SlowdownKey &s)
+// x2b and x3 of `s` for another step (the rest of the key is the same).
+struct StepWords {
+    uint32_t x2b, x3;
+};
+__host__ __device__ __forceinline__ StepWords slowdown_step_words(const SlowdownKey &s, uint32_t step)
+{
+    const uint64_t pa2 = (uint64_t)kMulA * (s.h0 ^ step);
+    return StepWords{(uint32_t)(pa2 >> 32) ^ s.k1[1], (uint32_t)pa2 ^ s.k1[2]};
+}
+
+// The draw with the step words given apart from the key.
+__host__ __device__ __forceinline__ uint32_t slowdown_word0_at(uint32_t cell, const SlowdownKey &s, StepWords sw)
 {
     uint64_t pa = (uint64_t)kMulA * cell;                              // round 1
     uint32_t c2 = (uint32_t)(pa >> 32) ^ s.k1_0;
@@ -92,11 +106,11 @@ __host__ __device__ __forceinline__ uint32_t slowdown_word0(uint32_t cell, const
     uint64_t pb = (uint64_t)kMulB * c2;                                // round 2
     uint32_t c0 = (uint32_t)(pb >> 32) ^ s.x2a;
     uint32_t c1 = (uint32_t)pb;
-    c2 = c3 ^ s.x2b;
+    c2 = c3 ^ sw.x2b;
     pa = (uint64_t)kMulA * c0;                                         // round 3
     pb = (uint64_t)kMulB * c2;
     c0 = (uint32_t)(pb >> 32) ^ c1 ^ s.k0[2];
-    c2 = (uint32_t)(pa >> 32) ^ s.x3;
+    c2 = (uint32_t)(pa >> 32) ^ sw.x3;
     c1 = (uint32_t)pb;
     c3 = (uint32_t)pa;
 #pragma unroll
@@ -111,6 +125,11 @@ __host__ __device__ __forceinline__ uint32_t slowdown_word0(uint32_t cell, const
         c2 = n2;
     }
     return (uint32_t)(((uint64_t)kMulB * c2) >> 32) ^ c1 ^ s.k0[9];   // round 10, word 0
+}
+
+__host__ __device__ __forceinline__ uint32_t slowdown_word0(uint32_t cell, const SlowdownKey &s)
+{
+    return slowdown_word0_at(cell, s, StepWords{s.x2b, s.x3});
 }
 
 // Parameters every step kernel shares.

@@ -250,7 +250,7 @@ struct GridTileGeom {
 // in cell order (position, velocity) and clears the span, runs the k steps
 // on the list, and scatters the cars that end in the tile's own cells back
 // into the span.  A car's leader is the next list entry; the lanes take the
-// list 32 cars at a time in ascending order, two groups at once, and every
+// list 32 cars at a time in ascending order, three groups at once, and every
 // lane reads (its car and the leader) before any lane writes, so each car
 // sees its leader's start-of-step position (the later groups have not moved
 // yet).  After the last car come dummy cars far beyond the span, so the last
@@ -259,16 +259,91 @@ struct GridTileGeom {
 // cells a step, which keeps it in the right halo.  Statistics count the cars
 // whose cell at the start of a step is one of the tile's own.
 
+// Rule-3 draws for grid_warp_steps.  FoldedDraws: the key of the road
+// computed on the host (a kernel parameter), with the two step words
+// recomputed per step.  PlainDraws: Philox from the road's constants, for
+// code that has no folded key at hand.
+struct FoldedDraws {
+    const SlowdownKey &sk;
+    StepWords sw;
+    __device__ __forceinline__ void at_step(uint32_t step) { sw = slowdown_step_words(sk, step); }
+    __device__ __forceinline__ uint32_t operator()(uint32_t cell) const { return slowdown_word0_at(cell, sk, sw); }
+};
+struct PlainDraws {
+    const RoadConst &rc;
+    uint32_t step;
+    __device__ __forceinline__ void at_step(uint32_t s) { step = s; }
+    __device__ __forceinline__ uint32_t operator()(uint32_t cell) const
+    {
+        return philox_word0(cell, step, rc.road, kTagSlowdown, rc.key0, rc.key1);
+    }
+};
+
+// One step of G groups of 32 list entries from i0 (= first group + lane),
+// their draws interleaved.  Every lane reads its cars and their leaders
+// before any lane writes.  W: cells may wrap past L - 1 (warp-uniform).
+template <int G, Draw D, bool W, class Draws>
+__device__ __forceinline__ void warp_list_groups(uint16_t *pos, uint8_t *vel, uint32_t i0, const Draws &draws,
+                                                 uint32_t L, uint32_t vmax, uint32_t thr, uint32_t base, uint32_t H,
+                                                 uint32_t own, uint32_t &tsum, uint32_t &tcross)
+{
+    uint32_t x[G], lead[G], v[G];
+#pragma unroll
+    for (int q = 0; q < G; ++q) {
+        const uint32_t i = i0 + 32u * (uint32_t)q;
+        x[q] = pos[i];
+        lead[q] = pos[i + 1u];
+        v[q] = vel[i];
+    }
+    __syncwarp();   // every lane has read before any lane writes
+#pragma unroll
+    for (int q = 0; q < G; ++q) {
+        uint32_t vq = min(min(v[q] + 1u, vmax), lead[q] - x[q] - 1u);              // rules 1, 2
+        uint32_t cell = base + x[q];
+        if (W && cell >= L) cell -= L;
+        if (D == Draw::kAlways) {
+            vq -= vq != 0u ? 1u : 0u;                                              // rule 3, p = 1
+        } else if (D == Draw::kPhilox) {
+            const uint32_t u = draws(cell);
+            vq -= (vq != 0u && u < thr) ? 1u : 0u;                                 // rule 3
+        }
+        const uint32_t i = i0 + 32u * (uint32_t)q;
+        pos[i] = (uint16_t)(x[q] + vq);                                            // rule 4
+        vel[i] = (uint8_t)vq;
+        const bool mine = x[q] - H < own;
+        tsum += mine ? vq : 0u;
+        if (W) tcross += (mine && cell + vq >= L) ? 1u : 0u;
+    }
+}
+
+// One step of the whole list (`padded` entries, whole groups) in ascending
+// order, three groups at a time: a group's leaders belong to later groups,
+// which have not moved yet.
+template <Draw D, bool W, class Draws>
+__device__ __forceinline__ void warp_list_step(uint16_t *pos, uint8_t *vel, uint32_t padded, uint32_t lane,
+                                               const Draws &draws, uint32_t L, uint32_t vmax, uint32_t thr,
+                                               uint32_t base, uint32_t H, uint32_t own, uint32_t &tsum,
+                                               uint32_t &tcross)
+{
+    uint32_t gi = 0;
+    for (; gi + 96u <= padded; gi += 96u)
+        warp_list_groups<3, D, W>(pos, vel, gi + lane, draws, L, vmax, thr, base, H, own, tsum, tcross);
+    if (padded - gi == 64u)
+        warp_list_groups<2, D, W>(pos, vel, gi + lane, draws, L, vmax, thr, base, H, own, tsum, tcross);
+    else if (padded - gi == 32u)
+        warp_list_groups<1, D, W>(pos, vel, gi + lane, draws, L, vmax, thr, base, H, own, tsum, tcross);
+}
+
 // Fused steps of one warp-tile.  span: kKwBuf bytes of shared memory holding
 // the staged cells (span index 0 = road cell `base`); on return its cells
 // [H, H + own) hold the result.  pos / vel: kKwList entries of shared memory.
-// after_list() is called by every lane once the span has been read (it may
-// be reused from then on); add(s, sum, cross) by lane 0 with step s's
-// statistics of this warp-tile.
-template <Draw D, class AfterList, class Add>
-__device__ __forceinline__ void grid_warp_steps(const RoadConst &rc, int8_t *span, uint16_t *pos, uint8_t *vel,
-                                                uint32_t H, uint32_t own, uint32_t base, uint32_t step0, int ksteps,
-                                                AfterList after_list, Add add)
+// draws: FoldedDraws or PlainDraws of the road.  after_list() is called by
+// every lane once the span has been read (it may be reused from then on);
+// add(s, sum, cross) by lane 0 with step s's statistics of this warp-tile.
+template <Draw D, class Draws, class AfterList, class Add>
+__device__ __forceinline__ void grid_warp_steps(const RoadConst &rc, Draws draws, int8_t *span, uint16_t *pos,
+                                                uint8_t *vel, uint32_t H, uint32_t own, uint32_t base,
+                                                uint32_t step0, int ksteps, AfterList after_list, Add add)
 {
     constexpr uint32_t kWords = kKwSpan / 1024u;          // occupancy words per lane
     const uint32_t lane = threadIdx.x & 31u;
@@ -311,51 +386,12 @@ __device__ __forceinline__ void grid_warp_steps(const RoadConst &rc, int8_t *spa
     const bool wraps = base + kKwSpan + (uint32_t)ksteps * vmax > L;   // crossings possible
     // 2. k steps on the list
     for (int s = 0; s < ksteps; ++s) {
-        const uint32_t step = step0 + (uint32_t)s;
+        draws.at_step(step0 + (uint32_t)s);
         uint32_t tsum = 0, tcross = 0;
-        for (uint32_t gi = 0; gi < padded; gi += 64u) {
-            const bool two = gi + 32u < padded;   // warp-uniform
-            const uint32_t i0 = gi + lane, i1 = i0 + 32u;
-            const uint32_t x0 = pos[i0], l0 = pos[i0 + 1u];
-            uint32_t v0 = vel[i0];
-            uint32_t x1 = 0, l1 = 0, v1 = 0;
-            if (two) {
-                x1 = pos[i1];
-                l1 = pos[i1 + 1u];
-                v1 = vel[i1];
-            }
-            __syncwarp();   // every lane has read before any lane writes
-            v0 = min(min(v0 + 1u, vmax), l0 - x0 - 1u);                  // rules 1, 2
-            uint32_t cell0 = base + x0;
-            if (cell0 >= L) cell0 -= L;
-            if (D == Draw::kAlways) {
-                v0 -= v0 != 0u ? 1u : 0u;                                  // rule 3, p = 1
-            } else if (D == Draw::kPhilox) {
-                const uint32_t u0 = philox_word0(cell0, step, rc.road, kTagSlowdown, rc.key0, rc.key1);
-                v0 -= (v0 != 0u && u0 < thr) ? 1u : 0u;                    // rule 3
-            }
-            pos[i0] = (uint16_t)(x0 + v0);                                 // rule 4
-            vel[i0] = (uint8_t)v0;
-            const bool own0 = x0 - H < own;
-            tsum += own0 ? v0 : 0u;
-            if (wraps) tcross += own0 && cell0 + v0 >= L ? 1u : 0u;
-            if (two) {
-                v1 = min(min(v1 + 1u, vmax), l1 - x1 - 1u);
-                uint32_t cell1 = base + x1;
-                if (cell1 >= L) cell1 -= L;
-                if (D == Draw::kAlways) {
-                    v1 -= v1 != 0u ? 1u : 0u;
-                } else if (D == Draw::kPhilox) {
-                    const uint32_t u1 = philox_word0(cell1, step, rc.road, kTagSlowdown, rc.key0, rc.key1);
-                    v1 -= (v1 != 0u && u1 < thr) ? 1u : 0u;
-                }
-                pos[i1] = (uint16_t)(x1 + v1);
-                vel[i1] = (uint8_t)v1;
-                const bool own1 = x1 - H < own;
-                tsum += own1 ? v1 : 0u;
-                if (wraps) tcross += own1 && cell1 + v1 >= L ? 1u : 0u;
-            }
-        }
+        if (wraps)
+            warp_list_step<D, true>(pos, vel, padded, lane, draws, L, vmax, thr, base, H, own, tsum, tcross);
+        else
+            warp_list_step<D, false>(pos, vel, padded, lane, draws, L, vmax, thr, base, H, own, tsum, tcross);
         tsum = __reduce_add_sync(0xFFFFFFFFu, tsum);
         tcross = __reduce_add_sync(0xFFFFFFFFu, tcross);
         if (lane == 0) add(s, tsum, tcross);
