@@ -164,10 +164,10 @@ def kernel_source_hash(kernel: str) -> str:
 # sources when it was captured: a changed kernel reports null until it is
 # captured again.
 NCU_TRAFFIC: dict[str, dict] = {
-    "agent_tiled_k16": {"source_hash": "f348db7d4b9b86f6", "captured_bytes": 167957248 + 122387712,
-                        "scale": 4, "bytes_per_launch": 4 * (167957248 + 122387712)},
-    "grid_k1": {"source_hash": "acb9760453662904", "captured_bytes": 268562944 + 219382272,
-                "scale": 8, "bytes_per_launch": 8 * (268562944 + 219382272)},
+    "agent_tiled_k16": {"source_hash": "32d20f5b09e34095", "captured_bytes": 167913472 + 122408192,
+                        "scale": 4, "bytes_per_launch": 4 * (167913472 + 122408192)},
+    "grid_k1": {"source_hash": "76b9733b0ad84f20", "captured_bytes": 268520960 + 219900416,
+                "scale": 8, "bytes_per_launch": 8 * (268520960 + 219900416)},
 }
 
 
