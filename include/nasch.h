@@ -131,10 +131,12 @@ int nasch_create_open(const nasch_params *prm, double alpha, double beta, nasch_
 
 /* Replace the state: N cars (N must equal the handle's N) at positions
  * x_host[0..N-1] (distinct, in [0, L), in cyclic order: a rotation of an
- * increasing sequence) with velocities v_host[0..N-1] <= vmax; the next
- * step run is `step`.  Statistics kept so far are dropped.  Copies the host
- * arrays to the device on the handle's stream and returns once the copy is
- * complete. */
+ * increasing sequence; a grid road takes any order) with velocities
+ * v_host[0..N-1] <= vmax; the next step run is `step`.  Statistics kept so
+ * far are dropped.  Copies the host arrays to the device on the handle's
+ * stream, checks them there and returns once the check is complete.  A
+ * state that breaks a rule is NASCH_EINVAL (the message names the first bad
+ * car, or the shared cell) and leaves the road's state as it was. */
 int nasch_set_state(nasch_handle h, const int32_t *x_host, const uint8_t *v_host, int64_t N,
                     uint64_t step);
 

@@ -11,14 +11,13 @@
 #include <cstring>
 #include <new>
 #include <string>
-#include <atomic>
-#include <thread>
 #include <vector>
 
 #include "nasch.h"
 #include "kernels.h"
 #include "road_output.h"
 #include "runtime_internal.h"
+#include "state_check.h"
 
 namespace nasch {
 
@@ -120,74 +119,6 @@ int floyd_init_host(int64_t L, int64_t N, uint64_t seed, uint32_t road, int32_t 
     return n == N ? NASCH_OK : fail(NASCH_EINVAL, "floyd: internal count mismatch");
 }
 
-// Positions must be distinct, in [0, L), and a rotation of an increasing
-// sequence (the cars' cyclic order on the ring).
-int validate_state(int64_t L, int64_t N, int vmax, const int32_t *x, const uint8_t *v, bool need_cyclic)
-{
-    // One pass over the cars, split over the host's cores: each chunk finds
-    // its first bad car (a cell outside the road, a velocity above vmax, the
-    // same cell as the next car) and counts the descents of x (the ring
-    // order allows exactly one).  The first bad car of the lowest chunk is
-    // reported.
-    struct Part {
-        int64_t bad = -1;   // index of the first bad car
-        int kind = 0;       // 1 cell, 2 velocity, 3 same cell as the next
-        int64_t descents = 0;
-    };
-    const int64_t chunk = int64_t(1) << 22;
-    const int64_t n_parts = N == 0 ? 0 : (N + chunk - 1) / chunk;
-    std::vector<Part> parts((size_t)n_parts);
-    auto work = [&](int64_t part) {
-        Part &r = parts[(size_t)part];
-        const int64_t a = part * chunk, b = std::min(N, a + chunk);
-        for (int64_t i = a; i < b; ++i) {
-            const int32_t xi = x[i];
-            const int32_t nx = i + 1 < N ? x[i + 1] : x[0];
-            int kind = 0;
-            if (xi < 0 || xi >= L) kind = 1;
-            else if (v[i] > vmax) kind = 2;
-            else if (N >= 2 && nx == xi) kind = 3;
-            if (kind) {
-                r.bad = i;
-                r.kind = kind;
-                return;
-            }
-            r.descents += (N >= 2 && nx < xi) ? 1 : 0;
-        }
-    };
-    const int64_t workers = std::min<int64_t>(n_parts, std::max(1u, std::thread::hardware_concurrency()));
-    if (workers <= 1) {
-        for (int64_t q = 0; q < n_parts; ++q) work(q);
-    } else {
-        std::atomic<int64_t> next{0};
-        std::vector<std::thread> pool;
-        for (int64_t t = 0; t < workers; ++t)
-            pool.emplace_back([&]() {
-                for (int64_t q = next.fetch_add(1); q < n_parts; q = next.fetch_add(1)) work(q);
-            });
-        for (auto &th : pool) th.join();
-    }
-    int64_t descents = 0;
-    for (const Part &r : parts) {
-        if (r.bad >= 0) {
-            const int64_t i = r.bad;
-            if (r.kind == 1) return fail(NASCH_EINVAL, "x[%lld]=%d outside [0, L)", (long long)i, x[i]);
-            if (r.kind == 2) return fail(NASCH_EINVAL, "v[%lld]=%d above vmax=%d", (long long)i, v[i], vmax);
-            return fail(NASCH_EINVAL, "two cars on cell %d", x[i]);
-        }
-        descents += r.descents;
-    }
-    if (N >= 2 && need_cyclic && descents != 1)
-        return fail(NASCH_EINVAL, "positions are not in cyclic order (%lld descents)", (long long)descents);
-    if (N >= 2 && !need_cyclic) {
-        std::vector<int32_t> s(x, x + N);
-        std::sort(s.begin(), s.end());
-        for (int64_t i = 1; i < N; ++i)
-            if (s[i] == s[i - 1]) return fail(NASCH_EINVAL, "two cars on cell %d", s[i]);
-    }
-    return NASCH_OK;
-}
-
 int device_info(int *device, int *sms)
 {
     cudaError_t e = cudaGetDevice(device);
@@ -214,6 +145,7 @@ struct nasch_road {
     int blocks = 1;
     int tile = 0;                       // agent warp-tile span or grid tile cells
     unsigned int *d_status = nullptr;   // kernels set bits here when a bounded wait runs out
+    unsigned long long *d_check = nullptr;   // nasch_set_state's device checks (3 words), made on first use
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     int32_t *x[2] = {nullptr, nullptr};
@@ -277,6 +209,7 @@ void free_road(nasch_road *h)
     cudaFree(h->d_sum);
     cudaFree(h->d_cross);
     cudaFree(h->d_status);
+    cudaFree(h->d_check);
     if (h->io_stream) cudaStreamSynchronize(h->io_stream);
     for (int i = 0; i < 2; ++i) {
         cudaFree(h->stage[i]);
@@ -348,6 +281,88 @@ int upload_state(nasch_road *h, const int32_t *x, const uint8_t *v)
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(e, "upload state");
     return NASCH_OK;
+}
+
+// The message for car i, which the device check found bad (a cell outside
+// the road, a velocity above vmax, or the next car's cell, in that order).
+int bad_car(int64_t L, int64_t N, int vmax, const int32_t *x, const uint8_t *v, int64_t i)
+{
+    if (x[i] < 0 || x[i] >= L) return fail(NASCH_EINVAL, "x[%lld]=%d outside [0, L)", (long long)i, x[i]);
+    if (v[i] > vmax) return fail(NASCH_EINVAL, "v[%lld]=%d above vmax=%d", (long long)i, v[i], vmax);
+    (void)N;
+    return fail(NASCH_EINVAL, "two cars on cell %d", x[i]);
+}
+
+// nasch_set_state's upload: the state goes into the buffers the next launch
+// would write, is checked there on the device, and becomes the road's state
+// only if it is valid, so a rejected state leaves the road as it was.
+// Agent roads: positions inside the road, velocities up to vmax, no car on
+// the next car's cell, and one descent round the ring (cyclic order).  Grid
+// roads: the same per car, then the cars are scattered and the occupied
+// cells counted (a shared cell leaves fewer than N).  The caller has
+// synchronised the stream.
+int upload_checked(nasch_road *h, int64_t N, const int32_t *x, const uint8_t *v)
+{
+    const int nxt = h->cur ^ 1;
+    cudaError_t e = cudaSuccess;
+    if (!h->d_check) e = cudaMalloc(&h->d_check, 3 * sizeof(unsigned long long));
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(check words)");
+    unsigned long long res[3] = {~0ull, 0ull, 0ull};   // first bad car, descents, occupied cells
+    e = cudaMemcpyAsync(h->d_check, res, sizeof(res), cudaMemcpyHostToDevice, h->stream);
+    int32_t *dx = nullptr;
+    uint8_t *dv = nullptr;
+    if (h->layout == NASCH_LAYOUT_AGENT) {
+        dx = h->x[nxt];
+        dv = h->v[nxt];
+    } else if (N > 0) {
+        if (e == cudaSuccess) e = cudaMallocAsync(&dx, (size_t)N * 4, h->stream);
+        if (e == cudaSuccess) e = cudaMallocAsync(&dv, (size_t)N, h->stream);
+    }
+    if (e == cudaSuccess && N > 0) e = cudaMemcpyAsync(dx, x, (size_t)N * 4, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess && N > 0) e = cudaMemcpyAsync(dv, v, (size_t)N, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess)
+        e = launch_check_cars(dx, dv, (uint32_t)N, (uint32_t)h->L, (uint32_t)h->vmax, h->d_check, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(res, h->d_check, sizeof(res), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    int st = NASCH_OK;
+    if (e != cudaSuccess) {
+        st = cuda_fail(e, "upload and check state");
+    } else if (res[0] < (unsigned long long)N) {
+        st = bad_car(h->L, N, h->vmax, x, v, (int64_t)res[0]);
+    } else if (h->layout == NASCH_LAYOUT_AGENT) {
+        if (N >= 2 && res[1] != 1)
+            st = fail(NASCH_EINVAL, "positions are not in cyclic order (%llu descents)", res[1]);
+    } else {
+        // every car is on the road: scatter them and count the occupied cells
+        e = cudaMemsetAsync(h->cells[nxt], 0xFF, (size_t)h->L, h->stream);
+        if (e == cudaSuccess) e = launch_scatter_agent_to_grid(dx, dv, (uint32_t)N, h->cells[nxt], h->stream);
+        if (e == cudaSuccess) e = launch_count_cars(h->cells[nxt], (uint32_t)h->L, h->d_check + 2, h->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&res[2], h->d_check + 2, 8, cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) {
+            st = cuda_fail(e, "scatter and count state");
+        } else if (res[2] != (unsigned long long)N) {   // a shared cell: name it
+            std::vector<int32_t> sorted(x, x + N);
+            std::sort(sorted.begin(), sorted.end());
+            int32_t cell = sorted[0];
+            for (int64_t i = 1; i < N; ++i)
+                if (sorted[i] == sorted[i - 1]) {
+                    cell = sorted[i];
+                    break;
+                }
+            st = fail(NASCH_EINVAL, "two cars on cell %d", cell);
+        }
+    }
+    if (h->layout != NASCH_LAYOUT_AGENT) {
+        if (dx) cudaFreeAsync(dx, h->stream);
+        if (dv) cudaFreeAsync(dv, h->stream);
+        if (st == NASCH_OK) {
+            e = cudaStreamSynchronize(h->stream);
+            if (e != cudaSuccess) st = cuda_fail(e, "upload state");
+        }
+    }
+    if (st == NASCH_OK) h->cur = nxt;
+    return st;
 }
 
 int choose_layout(const nasch_params *prm)
@@ -624,17 +639,11 @@ int nasch_set_state(nasch_handle h, const int32_t *x_host, const uint8_t *v_host
         return fail(NASCH_EINVAL, "N=%lld: must equal the handle's N=%lld (a ring) or lie in 0..L (an open road)",
                     (long long)N, (long long)h->N);
     if (N > 0 && (!x_host || !v_host)) return fail(NASCH_EINVAL, "NULL state array");
-    int st = validate_state(h->L, N, h->vmax, x_host, v_host, h->layout == NASCH_LAYOUT_AGENT);
-    if (st) return st;
     cudaError_t e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
-    const int64_t n_before = h->N;
+    const int st = upload_checked(h, N, x_host, v_host);
+    if (st) return st;
     h->N = N;
-    st = upload_state(h, x_host, v_host);
-    if (st) {
-        h->N = n_before;
-        return st;
-    }
     h->step = step;
     h->stats_first = step;
     return NASCH_OK;

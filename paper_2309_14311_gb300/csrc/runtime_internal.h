@@ -26,7 +26,6 @@ void clear_error();
 
 uint64_t slow_threshold(double p);
 int validate_params(const nasch_params *prm);
-int validate_state(int64_t L, int64_t N, int vmax, const int32_t *x, const uint8_t *v, bool need_cyclic);
 int floyd_init_host(int64_t L, int64_t N, uint64_t seed, uint32_t road, int32_t *x);
 int device_info(int *device, int *sms);
 

@@ -206,17 +206,46 @@ def test_resume_from_state_is_bit_exact(layout, tile):
 
 
 def test_set_state_rejects_bad_states():
+    """Bad states are refused (checked on the device) and leave the road as
+    it was."""
     with NS.Road(100, 3, 5, 0.1, 1, layout="agent") as r:
-        for x, v in [([1, 1, 5], [0, 0, 0]), ([1, 5, 200], [0, 0, 0]), ([1, 5, 9], [0, 6, 0]),
-                     ([5, 1, 9, ], [0, 0, 0][:3])]:
+        x0, v0 = (a.copy() for a in r.read_state())
+        for x, v, msg in [([1, 1, 5], [0, 0, 0], "two cars on cell 1"), ([1, 5, 200], [0, 0, 0], "x[2]=200"),
+                          ([1, 5, 9], [0, 6, 0], "v[1]=6"), ([5, 1, 9], [0, 0, 0], "cyclic order"),
+                          ([-3, 5, 9], [0, 0, 0], "x[0]=-3"), ([9, 5, 9], [0, 0, 0], "two cars on cell 9")]:
             with pytest.raises(NS.NaschError) as e:
                 r.set_state(np.array(x), np.array(v), 0)
-            assert e.value.status == NS.EINVAL
+            assert e.value.status == NS.EINVAL and msg in str(e.value), (x, v, str(e.value))
+            x1, v1 = r.read_state()
+            assert np.array_equal(x1, x0) and np.array_equal(v1, v0)
         with pytest.raises(NS.NaschError):
             r.set_state(np.array([1, 2]), np.array([0, 0]), 0)   # wrong N
         r.set_state(np.array([9, 1, 5]), np.array([1, 2, 3]), 0)   # rotation of sorted: fine
         with pytest.raises(NS.NaschError):
             r.stats(0, 5)   # nothing run yet
+
+
+def test_grid_set_state_checks():
+    """A grid road takes the cars in any order; a cell shared by two cars
+    that are not neighbours in the array is found by counting the occupied
+    cells after the scatter.  Refused states leave the road as it was."""
+    with NS.Road(100, 4, 5, 0.1, 1, layout="grid") as r:
+        before = r.read_grid().copy()
+        for x, v, msg in [([1, 5, 9, 5], [0, 0, 0, 0], "two cars on cell 5"),
+                          ([3, 3, 7, 9], [0, 0, 0, 0], "two cars on cell 3"),
+                          ([2, 50, 100, 7], [0, 0, 0, 0], "x[2]=100"),
+                          ([1, 5, 9, 20], [0, 6, 0, 0], "v[1]=6")]:
+            with pytest.raises(NS.NaschError) as e:
+                r.set_state(np.array(x, np.int32), np.array(v, np.uint8), 0)
+            assert e.value.status == NS.EINVAL and msg in str(e.value), (x, str(e.value))
+            assert np.array_equal(r.read_grid(), before)
+        r.set_state(np.array([9, 1, 5, 20], np.int32), np.array([1, 2, 3, 0], np.uint8), 7)
+        want = np.full(100, -1, np.int8)
+        want[[9, 1, 5, 20]] = [1, 2, 3, 0]
+        assert np.array_equal(r.read_grid(), want)
+        r.run(3)
+        orc = O.grid_run(want, 5, 0.1, 1, 0, 7, 3)
+        assert np.array_equal(r.read_grid(), orc[0])
 
 
 @pytest.fixture(scope="module")
