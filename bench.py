@@ -166,8 +166,8 @@ def kernel_source_hash(kernel: str) -> str:
 NCU_TRAFFIC: dict[str, dict] = {
     "agent_tiled_k16": {"source_hash": "32d20f5b09e34095", "captured_bytes": 167913472 + 122408192,
                         "scale": 4, "bytes_per_launch": 4 * (167913472 + 122408192)},
-    "grid_k1": {"source_hash": "76b9733b0ad84f20", "captured_bytes": 268520960 + 219900416,
-                "scale": 8, "bytes_per_launch": 8 * (268520960 + 219900416)},
+    "grid_k1": {"source_hash": "b9b95de8ce96a985", "captured_bytes": 268517120 + 220308736,
+                "scale": 8, "bytes_per_launch": 8 * (268517120 + 220308736)},
 }
 
 

@@ -26,6 +26,7 @@
 // in shared memory and runs any number of steps in one launch.
 #include <atomic>
 
+#include "road_output.h"
 #include "tile_device.cuh"
 
 namespace nasch {
@@ -168,6 +169,11 @@ __global__ void __launch_bounds__(kGridThreads) grid_tiled_kernel(const GridStep
 // copy is issued once the tile before has been read by its store.  The
 // rule-3 draw uses the counter-independent parts of Philox computed on the
 // host (SlowdownKey).
+// Open (an open road, cells 0..L-1): cells off the road read as empty, a
+// closed exit is a car standing on cell L (seen by the car behind it, never
+// written back), cars that pass cell L - 1 leave and are counted as
+// crossings, and after the step a car enters cell 0 at rest if `entry` and
+// the cell is empty.  The host decides the exit and the entry of the step.
 constexpr uint32_t kK1Words = 3;                         // occupancy words (32 cells each) per lane
 constexpr uint32_t kK1Halo = 16;                         // cells staged on each side: vmax <= 16
 constexpr uint32_t kK1Span = 1024u * kK1Words;           // staged cells
@@ -243,9 +249,10 @@ __device__ __forceinline__ void k1_cars(const uint16_t *list, uint32_t padded, u
         k1_groups<1, D, W>(list + gi, lane, span, out, base, L, vmax, thr, sk, own, tsum, tcross);
 }
 
-template <Draw D>
+template <Draw D, bool Open>
 __global__ void __launch_bounds__(32 * kK1Warps) grid_k1_kernel(const GridStep g, const uint32_t n_tiles,
-                                                                const SlowdownKey sk)
+                                                                const SlowdownKey sk, const int exit_open,
+                                                                const int entry)
 {
     __shared__ K1WarpSmem s_w[kK1Warps];
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
@@ -279,7 +286,8 @@ __global__ void __launch_bounds__(32 * kK1Warps) grid_k1_kernel(const GridStep g
         int8_t *span = w.buf[bi];
         const uint32_t t0 = tile * kK1Cells;
         const uint32_t own = min(kK1Cells, L - t0);
-        const uint32_t base = t0 >= kK1Halo ? t0 - kK1Halo : t0 + L - kK1Halo;   // road cell of span index 0
+        // road cell of span index 0 (an open road: modulo 2^32, before the road on tile 0)
+        const uint32_t base = Open ? t0 - kK1Halo : (t0 >= kK1Halo ? t0 - kK1Halo : t0 + L - kK1Halo);
         bool ok = true;
         if (bulk_ok(tile)) {
             if (lane == 0) ok = mbar_wait_bounded(&w.full[bi], (parity >> bi) & 1u);
@@ -287,8 +295,17 @@ __global__ void __launch_bounds__(32 * kK1Warps) grid_k1_kernel(const GridStep g
         } else {
             for (uint32_t i = lane; i < kK1Span; i += 32u) {
                 uint32_t c = base + i;
-                if (c >= L) c -= L;
-                span[i] = g.c_in[c];
+                if (Open) {
+                    span[i] = c < L ? g.c_in[c] : kEmptyCell;
+                } else {
+                    if (c >= L) c -= L;
+                    span[i] = g.c_in[c];
+                }
+            }
+            if (Open && !exit_open) {   // a closed exit: a car on cell L, if the span holds it
+                __syncwarp();
+                const uint32_t e = L - base;
+                if (lane == 0 && e < kK1Span) span[e] = 0;
             }
         }
         if (!__all_sync(0xFFFFFFFFu, ok)) {
@@ -365,6 +382,10 @@ __global__ void __launch_bounds__(32 * kK1Warps) grid_k1_kernel(const GridStep g
             else
                 k1_cars<D, false>(w.list, padded, lane, span, out, base, L, vmax, thr, sk, own, tsum, tcross);
             __syncwarp();   // the list is rewritten by the next pass
+        }
+        if (Open && entry && tile == 0) {   // a car enters cell 0 at rest
+            __syncwarp();
+            if (lane == 0 && out[kK1Halo] < 0) out[kK1Halo] = 0;
         }
         // 4. the result leaves by bulk store (or plain stores for a short last tile)
         fence_proxy_async();
@@ -530,8 +551,9 @@ GridTileGeom make_geom(int ksteps, uint32_t vmax, uint32_t L)
 // two stages, two outputs, and the car list (uint16 position + uint8 velocity)
 size_t grid_tiled_smem(const GridTileGeom &geo) { return 4u * (size_t)geo.padded + 3u * (size_t)kGridListCap; }
 
-template <Draw D>
-cudaError_t launch_k1_variant(const GridStep &g, uint32_t n_tiles, cudaStream_t s)
+template <Draw D, bool Open>
+cudaError_t launch_k1_variant(const GridStep &g, uint32_t n_tiles, cudaStream_t s, bool exit_open = false,
+                              bool entry = false)
 {
     // blocks per SM from the occupancy calculator, once per device
     static std::atomic<int> per_sm[kMaxDevices];
@@ -544,7 +566,7 @@ cudaError_t launch_k1_variant(const GridStep &g, uint32_t n_tiles, cudaStream_t 
         int sms = 0, b = 0;
         e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return e;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, grid_k1_kernel<D>, 32 * kK1Warps, 0);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, grid_k1_kernel<D, Open>, 32 * kK1Warps, 0);
         if (e != cudaSuccess) return e;
         n = sms * (b > 0 ? b : 1);
         per_sm[dev].store(n);
@@ -552,7 +574,7 @@ cudaError_t launch_k1_variant(const GridStep &g, uint32_t n_tiles, cudaStream_t 
     const uint32_t need = (n_tiles + (uint32_t)kK1Warps - 1u) / (uint32_t)kK1Warps;
     const int grid = (int)((uint32_t)n < need ? (uint32_t)n : need);
     const SlowdownKey sk = make_slowdown_key(g.step0, g.rc.road, g.rc.key0, g.rc.key1);
-    grid_k1_kernel<D><<<grid, 32 * kK1Warps, 0, s>>>(g, n_tiles, sk);
+    grid_k1_kernel<D, Open><<<grid, 32 * kK1Warps, 0, s>>>(g, n_tiles, sk, exit_open ? 1 : 0, entry ? 1 : 0);
     return cudaGetLastError();
 }
 
@@ -617,9 +639,9 @@ cudaError_t launch_grid_tiled(const GridStep &g, int blocks, cudaStream_t s)
     if (2u * geo.halo >= (uint32_t)kGridSpan || g.rc.L < (uint32_t)kGridSpan) return cudaErrorInvalidValue;
     if (g.ksteps == 1 && g.rc.vmax <= 16u) {
         const uint32_t n_tiles = (g.rc.L + kK1Cells - 1u) / kK1Cells;
-        if (g.rc.thr == 0) return launch_k1_variant<Draw::kNever>(g, n_tiles, s);
-        if (g.rc.thr > 0xFFFFFFFFull) return launch_k1_variant<Draw::kAlways>(g, n_tiles, s);
-        return launch_k1_variant<Draw::kPhilox>(g, n_tiles, s);
+        if (g.rc.thr == 0) return launch_k1_variant<Draw::kNever, false>(g, n_tiles, s);
+        if (g.rc.thr > 0xFFFFFFFFull) return launch_k1_variant<Draw::kAlways, false>(g, n_tiles, s);
+        return launch_k1_variant<Draw::kPhilox, false>(g, n_tiles, s);
     }
     if (geo.halo <= kKwMaxHalo) {
         const uint32_t n_tiles = (g.rc.L + (kKwSpan - 2u * geo.halo) - 1u) / (kKwSpan - 2u * geo.halo);
@@ -632,6 +654,15 @@ cudaError_t launch_grid_tiled(const GridStep &g, int blocks, cudaStream_t s)
     if (g.rc.thr == 0) return launch_grid_variant<Draw::kNever>(g, geo, grid, smem, s);
     if (g.rc.thr > 0xFFFFFFFFull) return launch_grid_variant<Draw::kAlways>(g, geo, grid, smem, s);
     return launch_grid_variant<Draw::kPhilox>(g, geo, grid, smem, s);
+}
+
+cudaError_t launch_grid_k1_open(const GridStep &g, bool exit_open, bool entry, cudaStream_t s)
+{
+    if (g.ksteps != 1 || g.rc.vmax > kK1Halo || g.rc.L == 0) return cudaErrorInvalidValue;
+    const uint32_t n_tiles = (g.rc.L + kK1Cells - 1u) / kK1Cells;
+    if (g.rc.thr == 0) return launch_k1_variant<Draw::kNever, true>(g, n_tiles, s, exit_open, entry);
+    if (g.rc.thr > 0xFFFFFFFFull) return launch_k1_variant<Draw::kAlways, true>(g, n_tiles, s, exit_open, entry);
+    return launch_k1_variant<Draw::kPhilox, true>(g, n_tiles, s, exit_open, entry);
 }
 
 cudaError_t launch_grid_ring(const GridStep &g, cudaStream_t s)

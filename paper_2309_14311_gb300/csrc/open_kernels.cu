@@ -10,11 +10,14 @@
 // The exit and entry draws of a step are decided on the host (Philox tags 2
 // and 3); the kernel gets the two outcomes.
 //
-// One step per launch.  Every warp works alone on tiles of kKwSpan - 2H
-// cells, H = round_up(vmax, 16): it stages the tile with H cells on each
-// side (cells off the road read as empty; a closed exit as a car standing
-// on cell L), steps the span by the list method (grid_warp_steps, as the
-// ring's fused kernels), lets a car enter on cell 0, and writes the tile.
+// One step per launch.  For vmax <= 16 the ring's one-step kernel runs the
+// open road (grid_k1_kernel in its open form: bulk copies, stepped in
+// place).  For larger vmax this kernel does: every warp works alone on
+// tiles of kKwSpan - 2H cells, H = round_up(vmax, 16); it stages the tile
+// with H cells on each side (cells off the road read as empty; a closed
+// exit as a car standing on cell L), steps the span by the list method
+// (grid_warp_steps, as the ring's fused kernels), lets a car enter on cell
+// 0, and writes the tile.
 #include <atomic>
 
 #include "road_output.h"
@@ -117,6 +120,7 @@ cudaError_t launch_open_variant(const GridStep &g, uint32_t H, uint32_t n_tiles,
 cudaError_t launch_grid_open(const GridStep &g, bool exit_open, bool entry, cudaStream_t s)
 {
     if (g.ksteps != 1 || g.rc.vmax > 127u || g.rc.L == 0) return cudaErrorInvalidValue;
+    if (g.rc.vmax <= 16u) return launch_grid_k1_open(g, exit_open, entry, s);   // bulk copies, stepped in place
     const uint32_t H = grid_halo(1, g.rc.vmax) < 16u ? 16u : grid_halo(1, g.rc.vmax);
     const uint32_t C = kKwSpan - 2u * H;
     const uint32_t n_tiles = (g.rc.L + C - 1u) / C;
