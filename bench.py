@@ -157,7 +157,8 @@ def kernel_source_hash(kernel: str) -> str:
 
 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
-# one ncu --set full capture of the small profiling case (bench.py --profile),
+# one ncu capture of the small profiling case (bench.py --profile; --set full,
+# or the two DRAM counters alone),
 # scaled to a launch of the large road by the units it processes (x4 cars for
 # the agent kernel, x8 cells for the grid kernel; the traffic of these
 # streaming kernels grows in proportion).  Keyed by the hash of the kernel's
@@ -166,8 +167,8 @@ def kernel_source_hash(kernel: str) -> str:
 NCU_TRAFFIC: dict[str, dict] = {
     "agent_tiled_k16": {"source_hash": "32d20f5b09e34095", "captured_bytes": 167913472 + 122408192,
                         "scale": 4, "bytes_per_launch": 4 * (167913472 + 122408192)},
-    "grid_k1": {"source_hash": "b9b95de8ce96a985", "captured_bytes": 268517120 + 220308736,
-                "scale": 8, "bytes_per_launch": 8 * (268517120 + 220308736)},
+    "grid_k1": {"source_hash": "c047250434e161c6", "captured_bytes": 268561408 + 219080192,
+                "scale": 8, "bytes_per_launch": 8 * (268561408 + 219080192)},
 }
 
 

@@ -198,8 +198,8 @@ struct __align__(16) K1WarpSmem {
 // index and its leader is the next entry; its velocity is read from `span`
 // and its result written to `out` (the same buffer when stepping in place).
 // W: the span holds cell L - 1, so cells wrap and crossings are possible
-// (warp-uniform; false on every tile but the first and the last).  The
-// statistics take the cars on the tile's own cells.
+// (warp-uniform; on a ring false on every tile but the first and the last).
+// The statistics take the cars on the tile's own cells.
 template <int G, Draw D, bool W>
 __device__ __forceinline__ void k1_groups(const uint16_t *list, uint32_t lane, const int8_t *span, int8_t *out,
                                           uint32_t base, uint32_t L, uint32_t vmax, uint32_t thr,
