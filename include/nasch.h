@@ -258,9 +258,13 @@ int nasch_batch_road_layout(nasch_batch b, int64_t i, int32_t *layout);
 void nasch_batch_destroy(nasch_batch b);
 
 /* Tuning of the automatic choices (process-wide; the autotuner sets these):
- * rho_star - density below which AUTO picks the agent layout (default 0.2,
- * the state-byte crossover 10 rho = 2); k_agent, k_grid - fused steps per
- * launch of tiled roads (0 leaves a value unchanged). */
+ * rho_star - density below which AUTO picks the agent layout (default 1:
+ * with fused steps the agent step is the faster one at every density; a
+ * road or batch whose AUTO roads would need more than half of the free
+ * device memory at rho_star uses 0.2 instead, the density where the agent
+ * state (10 bytes per car) and the grid state (2 per cell) are equal);
+ * k_agent, k_grid - fused steps per launch of tiled roads (0 leaves a value
+ * unchanged). */
 int nasch_set_tuning(double rho_star, int32_t k_agent, int32_t k_grid);
 int nasch_get_tuning(double *rho_star, int32_t *k_agent, int32_t *k_grid);
 

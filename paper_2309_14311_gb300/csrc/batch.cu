@@ -29,7 +29,12 @@ namespace nasch {
 namespace {
 
 std::mutex g_tuning_mu;
-double g_rho_star = 0.2;   // state bytes: agent 10 per car, grid 2 per cell -> equal at density 0.2
+// AUTO picks the agent layout below this density.  With fused steps both
+// layouts are bound by the step's arithmetic, not by HBM, and the agent step
+// is the cheaper one at every density measured, so the default is 1;
+// auto_rho_star falls back to kBytesRhoStar when memory is short.
+double g_rho_star = 1.0;
+constexpr double kBytesRhoStar = 0.2;   // state bytes equal: agent 10 per car, grid 2 per cell
 int g_k_agent = 8;
 int g_k_grid = 8;
 constexpr int kRingK = 8;   // steps per item of whole-ring roads
@@ -38,6 +43,27 @@ constexpr int64_t kGraphChunk = 2048;   // super-steps per captured graph
 uint32_t round_up(uint32_t a, uint32_t m) { return (a + m - 1u) / m * m; }
 
 }  // namespace
+
+double auto_rho_star(const nasch_params *roads, int64_t n)
+{
+    double rho;
+    {
+        std::lock_guard<std::mutex> g(g_tuning_mu);
+        rho = g_rho_star;
+    }
+    if (rho <= kBytesRhoStar) return rho;
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+        cudaGetLastError();
+        return kBytesRhoStar;
+    }
+    double bytes = 0.0;   // state of the AUTO roads at rho (two buffers each)
+    for (int64_t i = 0; i < n; ++i) {
+        if (roads[i].layout != NASCH_LAYOUT_AUTO) continue;
+        bytes += (double)roads[i].N < rho * (double)roads[i].L ? 10.0 * (double)roads[i].N : 2.0 * (double)roads[i].L;
+    }
+    return bytes <= 0.5 * (double)free_b ? rho : kBytesRhoStar;
+}
 
 void get_tuning_values(double *rho_star, int *k_agent, int *k_grid)
 {
@@ -219,11 +245,9 @@ int nasch_submit(const nasch_params *roads, int64_t n_roads, const int64_t *step
     *out = nullptr;
     if (n_roads <= 0 || !roads || !steps) return fail(NASCH_EINVAL, "no roads");
     if (n_roads > (int64_t)0x7FFFFFFF) return fail(NASCH_EINVAL, "too many roads");
-    double rho_star;
     int k_agent, k_grid;
     {
         std::lock_guard<std::mutex> g(g_tuning_mu);
-        rho_star = g_rho_star;
         k_agent = g_k_agent;
         k_grid = g_k_grid;
     }
@@ -254,6 +278,7 @@ int nasch_submit(const nasch_params *roads, int64_t n_roads, const int64_t *step
     }
 
     // ---------------------------------------------------------------- plan
+    const double rho_star = auto_rho_star(roads, n_roads);
     b->roads.resize((size_t)n_roads);
     b->layout.resize((size_t)n_roads);
     b->super.resize((size_t)n_roads);

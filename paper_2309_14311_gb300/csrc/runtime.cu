@@ -368,9 +368,8 @@ int upload_checked(nasch_road *h, int64_t N, const int32_t *x, const uint8_t *v)
 int choose_layout(const nasch_params *prm)
 {
     if (prm->layout != NASCH_LAYOUT_AUTO) return prm->layout;
-    // State bytes per step: agent 10 per car (read + write x and v), grid 2
-    // per cell; equal at density 0.2.
-    return (double)prm->N < 0.2 * (double)prm->L ? NASCH_LAYOUT_AGENT : NASCH_LAYOUT_GRID;
+    // the agent layout below the tuned density (see auto_rho_star)
+    return (double)prm->N < auto_rho_star(prm, 1) * (double)prm->L ? NASCH_LAYOUT_AGENT : NASCH_LAYOUT_GRID;
 }
 
 // Enqueue `steps` steps on the handle's stream (validated by the caller).

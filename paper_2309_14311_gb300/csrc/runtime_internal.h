@@ -28,5 +28,10 @@ uint64_t slow_threshold(double p);
 int validate_params(const nasch_params *prm);
 int floyd_init_host(int64_t L, int64_t N, uint64_t seed, uint32_t road, int32_t *x);
 int device_info(int *device, int *sms);
+// The density below which the AUTO roads of a job (one road, or a batch)
+// take the agent layout: the tuned value, or the state-byte crossover 0.2
+// when those roads would need more than half of the free device memory at
+// the tuned value.
+double auto_rho_star(const nasch_params *roads, int64_t n);
 
 }  // namespace nasch

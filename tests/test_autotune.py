@@ -26,10 +26,11 @@ def test_tuning_run_applies_its_choice():
     from paper_2309_14311_gb300 import build
     from paper_2309_14311_gb300 import nasch as NS
     build.build()
+    prev = NS.get_tuning()
     res = AT.tune(L=1 << 20, steps=16)
     assert res["k_agent"] in AT.K_CANDIDATES and res["k_grid"] in AT.K_CANDIDATES
     assert 0.0 <= res["rho_star"] <= 1.0
     AT.apply(res)
     rho, ka, kg = NS.get_tuning()
     assert (rho, ka, kg) == (pytest.approx(res["rho_star"]), res["k_agent"], res["k_grid"])
-    NS.set_tuning(0.2, 8, 8)
+    NS.set_tuning(*prev)

@@ -157,12 +157,23 @@ def _invariants(b, i, r):
     return cells
 
 
-def test_fundamental_diagram_full_size():
+@pytest.fixture
+def byte_crossover():
+    """Automatic layout at the state-byte crossover (agent below density
+    0.2, grid above), so a sweep runs in both layouts."""
+    prev = NS.get_tuning()
+    NS.set_tuning(0.2, 0, 0)
+    yield
+    NS.set_tuning(*prev)
+
+
+def test_fundamental_diagram_full_size(byte_crossover):
     """The sweep at full size: one replica per (density, p), L = 10^6, T =
-    12000, in the layouts the batch picks.  Every road: invariants, and the
-    same cells and statistics when every road is forced into the other
-    layout.  Every fourth road: light-cone windows of 40 cars after the 12000
-    steps against the oracle run from the same start."""
+    12000, in the layouts the batch picks at the state-byte crossover.  Every
+    road: invariants, and the same cells and statistics when every road is
+    forced into the other layout.  Every fourth road: light-cone windows of
+    40 cars after the 12000 steps against the oracle run from the same
+    start."""
     roads = WL.fundamental_diagram_roads(replicas=1)
     T = WL.FD_T
     with NS.Batch(roads, [T] * len(roads)) as b:

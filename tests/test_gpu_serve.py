@@ -39,7 +39,8 @@ def mixed_requests(n, seed=0):
 
 
 def alone(r):
-    lay = "agent" if r["N"] < 0.2 * r["L"] else "grid"
+    rho_star = NS.get_tuning()[0]   # the server's automatic layout choice
+    lay = "agent" if r["N"] < rho_star * r["L"] else "grid"
     with NS.Road(r["L"], r["N"], r["vmax"], r["p"], r["seed"], r["road_id"], layout=lay) as road:
         road.run(r["T"])
         sv, cr = road.stats()
