@@ -147,12 +147,39 @@ KERNEL_SOURCES = {
 }
 
 
+def source_tokens(text: str) -> str:
+    """C/C++/CUDA source with its comments removed and every run of
+    whitespace made one space: what a compiler sees, so that an edit of a
+    comment or of the layout leaves it unchanged.  String and character
+    literals are kept as they are."""
+    out, i, n = [], 0, len(text)
+    while i < n:
+        c = text[i]
+        if c in "\"'":                              # literal: copy up to its closing quote
+            j = i + 1
+            while j < n and text[j] != c:
+                j += 2 if text[j] == "\\" else 1
+            out.append(text[i:j + 1])
+            i = j + 1
+        elif text.startswith("//", i):                # line comment
+            j = text.find("\n", i)
+            i = n if j < 0 else j
+        elif text.startswith("/*", i):                # block comment
+            j = text.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+            out.append(" ")
+        else:
+            out.append(c)
+            i += 1
+    return " ".join("".join(out).split())
+
+
 def kernel_source_hash(kernel: str) -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2309_14311_gb300", "csrc")
     for fn in KERNEL_SOURCES[kernel]:
-        with open(os.path.join(csrc, fn), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(csrc, fn), encoding="utf-8") as f:
+            h.update(source_tokens(f.read()).encode())
     return h.hexdigest()[:16]
 
 
@@ -162,12 +189,12 @@ def kernel_source_hash(kernel: str) -> str:
 # scaled to a launch of the large road by the units it processes (x4 cars for
 # the agent kernel, x8 cells for the grid kernel; the traffic of these
 # streaming kernels grows in proportion).  Keyed by the hash of the kernel's
-# sources when it was captured: a changed kernel reports null until it is
-# captured again.
+# sources (comments and layout aside) when it was captured: a changed kernel
+# reports null until it is captured again.
 NCU_TRAFFIC: dict[str, dict] = {
-    "agent_tiled_k16": {"source_hash": "32d20f5b09e34095", "captured_bytes": 167913472 + 122408192,
+    "agent_tiled_k16": {"source_hash": "539ea9d742b86ed2", "captured_bytes": 167913472 + 122408192,
                         "scale": 4, "bytes_per_launch": 4 * (167913472 + 122408192)},
-    "grid_k1": {"source_hash": "c047250434e161c6", "captured_bytes": 268561408 + 219080192,
+    "grid_k1": {"source_hash": "9b3a0fb2f4c9080f", "captured_bytes": 268561408 + 219080192,
                 "scale": 8, "bytes_per_launch": 8 * (268561408 + 219080192)},
 }
 
