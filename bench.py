@@ -663,45 +663,22 @@ def run_workload(args):
                    plain_vehicle_updates_per_s=pwork / plain,
                    speedup=(work / inf.run_seconds) / (pwork / plain))
     elif args.workload == "fundamental-diagram":
+        from paper_2309_14311_gb300 import fundamental as FD
         roads = WL.fundamental_diagram_roads(replicas=args.replicas, L=args.fd_L, vmax=args.fd_vmax)
         T = WL.FD_T
+        window = T - WL.FD_WARMUP
         t0 = time.perf_counter()
         with NS.Batch(roads, [T] * len(roads), stream=stream) as b:
             b.wait()
             inf = b.info()
-            table = {}
-            for i, r in enumerate(roads):
-                sv, _ = b.stats_sum(i, WL.FD_WARMUP, T - WL.FD_WARMUP)
-                key = (r["N"], r["p"])
-                table.setdefault(key, []).append(sv)
+            sums = [FD.ReplicaSum(r["L"], r["N"], r["p"], r["vmax"], b.stats_sum(i, WL.FD_WARMUP, window)[0], window)
+                    for i, r in enumerate(roads)]
         wall = time.perf_counter() - t0
-        rows = []
-        L = args.fd_L
-        for (N, p), sums in sorted(table.items()):
-            steps = T - WL.FD_WARMUP
-            J = np.array([s / (L * steps) for s in sums])  # time-averaged flux per replica
-            v = np.array([s / (N * steps) for s in sums])  # time-averaged mean velocity
-            se = float(J.std(ddof=1) / np.sqrt(len(J))) if len(J) > 1 else 0.0
-            row = {"rho": N / L, "p": p, "J": float(J.mean()), "J_sd": float(J.std(ddof=1)) if len(J) > 1 else 0.0,
-                   "J_ci95": 1.96 * se, "v": float(v.mean()), "replicas": len(J)}
-            rho = N / L
-            theory = None
-            if p == 0.0:
-                theory = min(args.fd_vmax * rho, 1 - rho)   # deterministic steady state
-            elif args.fd_vmax == 1:
-                theory = WL.flux_vmax1(rho, p)
-            if theory is not None:
-                row["J_theory"] = theory
-                row["J_minus_theory"] = row["J"] - theory
-            rows.append(row)
+        rows = FD.fd_table(sums)
         work = sum(r["N"] for r in roads) * T
-        checked = [r for r in rows if "J_theory" in r]
-        out.update(roads=len(roads), L=L, T=T, warmup=WL.FD_WARMUP, vmax=args.fd_vmax, vehicle_updates=work,
-                   batched_gpu_seconds=inf.run_seconds, wall_seconds=wall,
-                   vehicle_updates_per_s=work / inf.run_seconds,
-                   theory_rows=len(checked),
-                   max_abs_J_minus_theory=max((abs(r["J_minus_theory"]) for r in checked), default=None),
-                   table=rows)
+        out.update(roads=len(roads), L=args.fd_L, T=T, warmup=WL.FD_WARMUP, vmax=args.fd_vmax,
+                   vehicle_updates=work, batched_gpu_seconds=inf.run_seconds, wall_seconds=wall,
+                   vehicle_updates_per_s=work / inf.run_seconds, **FD.summary(rows), table=rows)
     elif args.workload == "serve":
         from paper_2309_14311_gb300 import serve as SV
         rows = WL.request_stream()[: args.serve_requests]

@@ -323,8 +323,9 @@ int nasch_server_drain(nasch_server s, int64_t timeout_ms);
 /* Take up to cap finished requests' results (each is returned once). */
 int nasch_server_poll(nasch_server s, nasch_request_result *out, int64_t cap, int64_t *n_out);
 /* Copy a finished request's per-step statistics (cap_steps >= its steps) and,
- * with keep_state, its final state in cell order (cap_cars >= N); any output
- * may be NULL. */
+ * with keep_state, its final state (cap_cars >= N): an agent road's cars in
+ * their cyclic order, as nasch_read_state gives them; a grid road's cars in
+ * increasing cell order.  Any output may be NULL. */
 int nasch_server_result(nasch_server s, uint64_t request_id, uint64_t *sum_v_host, uint64_t *crossings_host,
                         int64_t cap_steps, int32_t *x_host, uint8_t *v_host, int64_t cap_cars);
 /* Forget a finished, polled request (frees its host copies). */
@@ -346,9 +347,10 @@ void nasch_server_destroy(nasch_server s);
  * the caller synchronises before reading x_dev.  It calls no allocating
  * routine: its scratch bit map is a fixed 2 MiB array in the library's device
  * memory, held by every GPU that loads the library until the process exits,
- * so L is limited to 2^24 cells (a longer road is NASCH_EINVAL).  The first
- * call on a device looks up that array's device address with the device
- * current; make that first call before any stream capture.  All calls share
+ * so L is limited to 2^24 cells (a longer road is NASCH_EINVAL).  Every
+ * call looks up that array's device address with the calling thread's
+ * device current (the first call on a device also loads the library's
+ * device code there); make that first call before any stream capture.  All calls share
  * the array and the bits of the previous call stay in it (each call clears
  * the part it uses first), so calls whose work overlaps on the GPU race and
  * give wrong positions: issue them on one stream, or synchronise between

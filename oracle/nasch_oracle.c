@@ -220,6 +220,44 @@ int oracle_agent_run(int64_t L, int64_t N, int32_t vmax, uint64_t thr, uint64_t 
 }
 
 /* ------------------------------------------------------------------------ */
+/* One synchronous step of the agent form with the rule-3 outcome given      */
+/* instead of drawn: slow[i] != 0 means car i's Bernoulli trial succeeded    */
+/* (r < p).  Rules 1-4 as in oracle_agent_run (Handout, "The                 */
+/* Nagel-Schreckenberg traffic model"); a car that is stopped after rule 2   */
+/* stays stopped whatever its trial.  This is the model's one-step           */
+/* transition for one outcome of the N independent trials, so enumerating    */
+/* all 2^N outcomes (each with probability p^k (1-p)^(N-k)) gives the whole  */
+/* one-step distribution.  `count` independent states of N cars each are     */
+/* stepped: state s is x[s*N .. s*N+N-1], v[...], slow[...] (cars in cyclic  */
+/* order, distinct cells in [0, L)); results go to x_out and v_out.          */
+/* ------------------------------------------------------------------------ */
+int oracle_agent_step_masked(int64_t L, int64_t N, int32_t vmax, int64_t count, const int32_t *x,
+                             const uint8_t *v, const uint8_t *slow, int32_t *x_out, uint8_t *v_out)
+{
+    if (L < 1 || L > ((int64_t)1 << 31) || N < 1 || N > L || vmax < 0 || vmax > 127 || count < 0)
+        return ORACLE_EINVAL;
+    for (int64_t s = 0; s < count; ++s) {
+        const int32_t *xs = x + s * N;
+        const uint8_t *vs = v + s * N;
+        const uint8_t *ms = slow + s * N;
+        for (int64_t i = 0; i < N; ++i) {
+            int64_t xi = xs[i];
+            int64_t d = (int64_t)xs[(i + 1) % N] - xi;   /* headway */
+            if (d <= 0) d += L;                          /* ring; alone: d = L */
+            int64_t vel = (int64_t)vs[i] + 1;            /* rule 1 */
+            if (vel > vmax) vel = vmax;
+            if (vel > d - 1) vel = d - 1;                /* rule 2 */
+            if (vel > 0 && ms[i]) vel -= 1;              /* rule 3 */
+            int64_t nx = xi + vel;                       /* rule 4 */
+            if (nx >= L) nx -= L;
+            x_out[s * N + i] = (int32_t)nx;
+            v_out[s * N + i] = (uint8_t)vel;
+        }
+    }
+    return ORACLE_OK;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Grid representation: one int8 per cell, -1 empty, otherwise the velocity  */
 /* of the car on it.  The gap is found by scanning forward over empty cells  */
 /* (at most the accelerated velocity); the successor grid starts all empty   */

@@ -82,6 +82,8 @@ def _load(openmp: bool) -> ctypes.CDLL:
         lib.oracle_agent_segment.restype = ctypes.c_int
         lib.oracle_grid_segment.argtypes = [i64, i64, i64, i32, u64, u64, u32, u64, i64, P]
         lib.oracle_grid_segment.restype = ctypes.c_int
+        lib.oracle_agent_step_masked.argtypes = [i64, i64, i32, i64, P, P, P, P, P]
+        lib.oracle_agent_step_masked.restype = ctypes.c_int
         lib.oracle_set_threads.argtypes = [ctypes.c_int]
         lib.oracle_set_threads.restype = ctypes.c_int
         _LIBS[openmp] = lib
@@ -146,6 +148,23 @@ def agent_run(L, x, v, vmax, p, seed, road=0, step0=0, T=1, *, openmp=False, thr
                                         _ptr(x), _ptr(v), _ptr(sv), _ptr(cr))
     _check(st, "agent_run")
     return x, v, sv, cr
+
+
+def agent_step_masked(L, x, v, slow, vmax):
+    """One step of the agent form with the rule-3 outcome given per car
+    (``slow`` nonzero: the car's Bernoulli trial succeeded) instead of drawn.
+    ``x``, ``v``, ``slow``: arrays of shape (count, N), one independent
+    state per row, cars in cyclic order.  Returns (x', v') of that shape."""
+    x = np.ascontiguousarray(x, dtype=np.int32)
+    v = np.ascontiguousarray(v, dtype=np.uint8)
+    slow = np.ascontiguousarray(slow, dtype=np.uint8)
+    assert x.ndim == 2 and x.shape == v.shape == slow.shape
+    count, N = x.shape
+    xo = np.zeros_like(x)
+    vo = np.zeros_like(v)
+    _check(_load(False).oracle_agent_step_masked(L, N, vmax, count, _ptr(x), _ptr(v), _ptr(slow), _ptr(xo),
+                                                 _ptr(vo)), "agent_step_masked")
+    return xo, vo
 
 
 def grid_run(cells, vmax, p, seed, road=0, step0=0, T=1, *, openmp=False, thr=None):

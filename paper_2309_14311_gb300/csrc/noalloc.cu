@@ -11,9 +11,6 @@
 // the library holds until the process exits.
 #include <cuda_runtime.h>
 
-#include <mutex>
-#include <vector>
-
 #include "nasch.h"
 #include "nasch_device.cuh"
 #include "runtime_internal.h"
@@ -27,22 +24,17 @@ constexpr size_t kNoAllocWords = (size_t)(kNoAllocMaxCells / 64);     // 2 MiB o
 // One bit per cell of the road being initialised.  Shared by every call.
 static __device__ __align__(256) unsigned long long g_floyd_scratch[kNoAllocWords];
 
-std::mutex g_scratch_mu;
-std::vector<unsigned long long *> g_scratch_addr;   // device address of the array, per device
-
 // Host code cannot use the array's name as a device address; look the
-// address up once per device (with that device current).
-int scratch_address(int device, unsigned long long **out)
+// address up with the calling thread's device current.  This is done on
+// every call rather than cached: a context that is torn down and made again
+// (cudaDeviceReset, or a framework resetting the device) reloads the
+// library's device code, and a cached address would then be stale.
+int scratch_address(unsigned long long **out)
 {
-    std::lock_guard<std::mutex> g(g_scratch_mu);
-    if ((int)g_scratch_addr.size() <= device) g_scratch_addr.resize((size_t)device + 1, nullptr);
-    if (!g_scratch_addr[(size_t)device]) {
-        void *p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_floyd_scratch);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(Floyd scratch)");
-        g_scratch_addr[(size_t)device] = static_cast<unsigned long long *>(p);
-    }
-    *out = g_scratch_addr[(size_t)device];
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_floyd_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(Floyd scratch)");
+    *out = static_cast<unsigned long long *>(p);
     return NASCH_OK;
 }
 
@@ -141,16 +133,13 @@ extern "C" int nasch_floyd_init_device_noalloc(int64_t L, int64_t N, uint64_t se
     if (N < 0 || N > L) return fail(NASCH_EINVAL, "N=%lld outside 0..L=%lld", (long long)N, (long long)L);
     if (N > 0 && !x_dev) return fail(NASCH_EINVAL, "x_dev is NULL");
     if (N == 0) return NASCH_OK;
-    int device = 0;
-    cudaError_t e = cudaGetDevice(&device);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
     unsigned long long *bm = nullptr;
-    int st = scratch_address(device, &bm);
+    int st = scratch_address(&bm);
     if (st) return st;
     const cudaStream_t s = static_cast<cudaStream_t>(stream);
     const uint32_t words = (uint32_t)((L + 63) / 64);
     // the array keeps the previous call's bits: clear the part this road uses
-    e = cudaMemsetAsync(bm, 0, (size_t)words * sizeof(unsigned long long), s);
+    cudaError_t e = cudaMemsetAsync(bm, 0, (size_t)words * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return cuda_fail(e, "clear Floyd scratch");
     floyd_bits_single_kernel<<<1, 1, 0, s>>>((uint64_t)L, (uint64_t)N, (uint32_t)seed, (uint32_t)(seed >> 32), road_id,
                                              bm);

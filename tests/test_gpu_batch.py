@@ -201,6 +201,24 @@ def test_fundamental_diagram_full_size(byte_crossover):
         assert np.array_equal(cells[i][wx], wv.astype(np.int8)), (i, "window")
 
 
+def test_fundamental_diagram_full_length_roads_match_oracle(byte_crossover):
+    """Four roads of the sweep at full size (L = 10^6, T = 12000 steps), one
+    per p, at densities next to the critical density 1/(vmax+1) and above
+    it, in the layouts the sweep's batch picks (agent below density 0.2, grid
+    above): the final state and every step's statistics against the oracle
+    run in full from the same Floyd start."""
+    picks = [(10, 0), (11, 1), (40, 2), (63, 3)]     # (density index, p index)
+    per = len(WL.FD_PS)
+    roads = [WL.fundamental_diagram_roads(replicas=1)[i * per + j] for i, j in picks]
+    T = WL.FD_T
+    with NS.Batch(roads, [T] * len(roads)) as b:
+        b.wait()
+        layouts = [b.layout(i) for i in range(len(roads))]
+        assert NS.LAYOUT_AGENT in layouts and NS.LAYOUT_GRID in layouts
+        for i, r in enumerate(roads):
+            check_road(b, i, dict(r, T=T))
+
+
 @pytest.mark.parametrize("layout", ["agent", "grid"])
 def test_reference_case_thousand_seeds(layout):
     """The handout's reference case (200 cars on 1000 cells, p = 0.13, vmax =
@@ -212,6 +230,26 @@ def test_reference_case_thousand_seeds(layout):
         b.wait()
         for i, r in enumerate(roads):
             check_road(b, i, dict(r, T=s.T))
+
+
+def test_stats_sum_equals_summed_series_and_oracle():
+    """nasch_batch_stats_sum over windows of a road's steps equals the sum
+    of the per-step series nasch_batch_stats returns and the sum of the
+    oracle's series (the fundamental diagram's time averages come from it)."""
+    rs = MIXED[:7]
+    with NS.Batch([_params(r) for r in rs], [r["T"] for r in rs]) as b:
+        b.wait()
+        for i, r in enumerate(rs):
+            _, _, osv, ocr = oracle_road(r)
+            sv, cr = b.stats(i)
+            T = r["T"]
+            for first, count in ((0, T), (0, 0), (T // 3, T - T // 3), (1, max(T - 2, 0)), (T - 1, 1)):
+                a, c = b.stats_sum(i, first, count)
+                assert a == int(sv[first:first + count].sum()) == int(osv[first:first + count].sum()), (i, first)
+                assert c == int(cr[first:first + count].sum()) == int(ocr[first:first + count].sum()), (i, first)
+        with pytest.raises(NS.NaschError) as e:
+            b.stats_sum(0, 1, rs[0]["T"])          # one step past the end
+        assert e.value.status == NS.EINVAL
 
 
 def test_wait_timeout_and_cancel():

@@ -1,14 +1,16 @@
 """GPU tests of the serving loop (continuous batching under a memory budget).
 
 Requests arriving while others run are admitted into the same launches; each
-request's per-step statistics and final state must equal the same road run
-alone through the single-road API (bit-exact; its draws are keyed by its
-own seed and road id).  The budget bounds what is resident; requests that
-can never fit are refused; cancelled requests report so.
+request's per-step statistics and final state must equal the oracle run of
+the same road from its Floyd start and the same road run alone through the
+single-road API (bit-exact; its draws are keyed by its own seed and road
+id).  The budget bounds what is resident; requests that can never fit are
+refused; cancelled requests report so.
 """
 import numpy as np
 import pytest
 
+from oracle import oracle as O
 from paper_2309_14311_gb300 import nasch as NS
 from paper_2309_14311_gb300 import serve as SV
 from paper_2309_14311_gb300 import workloads as WL
@@ -48,7 +50,16 @@ def alone(r):
         return sv.copy(), cr.copy(), x.copy(), v.copy()
 
 
-def test_requests_in_the_mix_equal_alone():
+def oracle_request(r):
+    """The request's road run by the oracle: Floyd start of (seed, road id),
+    v = 0, T steps.  Returns the per-step series and the final cells."""
+    x0 = O.floyd_init(r["L"], r["N"], r["seed"], r["road_id"])
+    ox, ov, osv, ocr = O.agent_run(r["L"], x0, np.zeros(r["N"], np.uint8), r["vmax"], r["p"], r["seed"],
+                                   r["road_id"], 0, r["T"], openmp=True)
+    return osv, ocr, O.agent_to_grid(r["L"], ox, ov)
+
+
+def test_requests_in_the_mix_equal_oracle_and_alone():
     reqs = mixed_requests(48)
     with NS.Server(memory_budget=1 << 30, steps_per_tick=4, max_resident=16, keep_state=True) as srv:
         # submit in waves while earlier requests are running
@@ -63,6 +74,9 @@ def test_requests_in_the_mix_equal_alone():
         for i, r in enumerate(reqs):
             assert results[i]["status"] == NS.OK
             sv, cr, x, v = srv.result(i, with_state=True)
+            osv, ocr, ocells = oracle_request(r)
+            assert np.array_equal(sv, osv) and np.array_equal(cr, ocr), (i, "series against the oracle")
+            assert np.array_equal(O.agent_to_grid(r["L"], x, v), ocells), (i, "state against the oracle")
             asv, acr, ax, av = alone(r)
             assert np.array_equal(sv, asv) and np.array_equal(cr, acr), i
             assert np.array_equal(x, ax) and np.array_equal(v, av), i
@@ -100,8 +114,24 @@ def test_cancel_queued_and_running():
         assert res[1]["status"] == NS.ECANCELED and res[2]["status"] == NS.ECANCELED
 
 
-def test_poisson_driver_small_stream():
+def test_poisson_driver_small_stream_matches_oracle():
+    """The smallest requests of the seed-11 stream, served by the Poisson
+    driver; every served result equals the oracle run of its road."""
     rows = [r for r in WL.request_stream() if r["N"] * r["T"] < 3e7][:40]
-    out = SV.run_poisson(rows, rate=200.0, memory_budget=2 << 30, steps_per_tick=8)
+    checked = []
+
+    def check(srv, res):
+        i = res["request_id"]
+        assert res["status"] == NS.OK, i
+        r = dict(WL.road_params(rows[i]), T=rows[i]["T"])
+        sv, cr, x, v = srv.result(i, with_state=True)
+        osv, ocr, ocells = oracle_request(r)
+        assert np.array_equal(sv, osv) and np.array_equal(cr, ocr), (i, "series")
+        assert np.array_equal(O.agent_to_grid(r["L"], x, v), ocells), (i, "state")
+        checked.append(i)
+
+    out = SV.run_poisson(rows, rate=200.0, memory_budget=2 << 30, steps_per_tick=8, keep_state=True,
+                         on_result=check)
     assert out["completed"] == len(rows)
+    assert sorted(checked) == list(range(len(rows)))
     assert out["latency_p99_s"] >= out["latency_p50_s"] > 0
