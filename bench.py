@@ -191,12 +191,7 @@ def kernel_source_hash(kernel: str) -> str:
 # streaming kernels grows in proportion).  Keyed by the hash of the kernel's
 # sources (comments and layout aside) when it was captured: a changed kernel
 # reports null until it is captured again.
-NCU_TRAFFIC: dict[str, dict] = {
-    "agent_tiled_k16": {"source_hash": "539ea9d742b86ed2", "captured_bytes": 167913472 + 122408192,
-                        "scale": 4, "bytes_per_launch": 4 * (167913472 + 122408192)},
-    "grid_k1": {"source_hash": "9b3a0fb2f4c9080f", "captured_bytes": 268561408 + 219080192,
-                "scale": 8, "bytes_per_launch": 8 * (268561408 + 219080192)},
-}
+NCU_TRAFFIC: dict[str, dict] = {}
 
 
 def traffic_for(kernel: str):
@@ -266,24 +261,46 @@ def run_reference(args):
 
 
 # --------------------------------------------------------------------------- GPU arm
-# Algorithmic integer operations of one car-step on this instruction set:
-# Philox4x32-10 word 0 = 10 rounds of two 32x32->64 products and two 3-input
-# xors, less the first round's product of the per-launch constant counter
-# word and the last round's three unused outputs (37); rules 1-4 with the
-# per-step statistics: accelerate 1, gap 2, brake 1, slowdown 2, move 2,
-# statistics 2 (10).  Total 47.
+# The agent step is bound by the SM's heavy integer-multiply pipe
+# (fmaheavy), which runs Philox4x32-10's 32x32->64 products.  Per SM it
+# takes 4 schedulers x 16 lanes = 64 lane-slots per clock; a 32x32->64
+# product (IMAD.WIDE) occupies two slots, a high half alone one (the ncu
+# pipe counters fit this: busy cycles = 2 x wide + 1 x narrow instructions,
+# per 16 lanes).  Algorithmic work of one car-step: word 0 of Philox with
+# counter (cell, step, road, 0) needs 16 wide products (rounds 1-9, less the
+# product of the launch-constant road word in round 1 and of the
+# step-constant word 0 in round 2) and one high half (round 10) = 33
+# lane-slots; the rules, the move and the statistics need none.
+HEAVY_SLOTS_PER_CAR_STEP = 33
+HEAVY_SLOTS_PER_SM_CLOCK = 64
+# Algorithmic integer instructions of one car-step (issue view, kept beside
+# it): Philox word 0 = 37 (two products and two 3-input xors per round, less
+# the constant products and the last round's unused outputs), rules 1-4 with
+# the statistics = 10.
 ALU_OPS_PER_CAR_STEP = 47
+
+
+def sm_clock_mhz() -> float:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f).get("sm_max_mhz", 2070.0))
+    except Exception:
+        return 2070.0
+
+
+def heavy_pipe_peak(props) -> tuple[float, str]:
+    """Heavy-multiply-pipe ceiling in lane-slots per second: SMs x 64 slots
+    per clock x the maximum SM clock."""
+    mhz = sm_clock_mhz()
+    return (props.multi_processor_count * HEAVY_SLOTS_PER_SM_CLOCK * mhz * 1e6,
+            f"{props.multi_processor_count} SMs x {HEAVY_SLOTS_PER_SM_CLOCK} fmaheavy lane-slots per clock x "
+            f"{mhz:.0f} MHz")
 
 
 def issue_peak_ops(props) -> tuple[float, str]:
     """Integer issue ceiling: SMs x 4 schedulers x 32 lanes x max SM clock
     (one instruction per lane per clock)."""
-    mhz = 2070.0
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            mhz = float(json.load(f).get("sm_max_mhz", mhz))
-    except Exception:
-        pass
+    mhz = sm_clock_mhz()
     return props.multi_processor_count * 128 * mhz * 1e6, f"{props.multi_processor_count} SMs x 128 lanes x {mhz:.0f} MHz"
 
 
@@ -356,12 +373,19 @@ def run_ours(args):
     kernel_name = f"{layout}_tiled_k{info.k}"
     car_steps_per_launch = spec.N * info.k
     if layout == "agent":
+        heavy_peak, heavy_how = heavy_pipe_peak(props)
+        achieved = HEAVY_SLOTS_PER_CAR_STEP * car_steps_per_launch / launch_s
         ops_peak, ops_how = issue_peak_ops(props)
         achieved_ops = ALU_OPS_PER_CAR_STEP * car_steps_per_launch / launch_s
-        roofline = {"bound": "alu", "achieved": achieved_ops / 1e12, "peak": ops_peak / 1e12, "unit": "Tops/s",
-                    "frac": achieved_ops / ops_peak, "traffic": traffic_for(kernel_name), "kernel": kernel_name,
-                    "peak_source": f"derived: {ops_how}, one integer instruction per lane per clock",
-                    "algorithmic_ops_per_car_step": ALU_OPS_PER_CAR_STEP,
+        roofline = {"bound": "alu", "pipe": "fmaheavy", "achieved": achieved / 1e12, "peak": heavy_peak / 1e12,
+                    "unit": "T fmaheavy lane-slots/s", "frac": achieved / heavy_peak,
+                    "traffic": traffic_for(kernel_name), "kernel": kernel_name,
+                    "peak_source": f"derived: {heavy_how} (a 32x32->64 product takes two slots)",
+                    "algorithmic_slots_per_car_step": HEAVY_SLOTS_PER_CAR_STEP,
+                    "car_steps_per_s_ceiling": heavy_peak / HEAVY_SLOTS_PER_CAR_STEP,
+                    "issue_view": {"achieved_tops": achieved_ops / 1e12, "peak_tops": ops_peak / 1e12,
+                                   "frac": achieved_ops / ops_peak, "ops_per_car_step": ALU_OPS_PER_CAR_STEP,
+                                   "peak_source": f"derived: {ops_how}, one instruction per lane per clock"},
                     "algorithmic_bytes_per_launch": AGENT_BYTES_PER_CAR * spec.N,
                     "hbm_gbs": AGENT_BYTES_PER_CAR * spec.N / launch_s / 1e9, "launch_ms": launch_s * 1e3}
     else:
@@ -419,6 +443,8 @@ def run_ours(args):
     # ---------------------------------------------------------------- batched vs plain, and served
     batch_res = run_batch_vs_plain(args, NS, stream, torch) if not args.no_batch else None
     serve_res = run_served(args, NS, batch_res) if (not args.no_serve and batch_res) else None
+    saturated = (run_serve_vs_batch(args, NS, stream, WL.request_stream()[: args.serve_requests])
+                 if not args.no_serve else None)
 
     # ---------------------------------------------------------------- oracle on the host cores (rank 0, N = 1)
     cpu = None
@@ -457,6 +483,7 @@ def run_ours(args):
                     "h2d_bytes_per_step": spec.N * 5, "d2h_bytes_per_step": spec.N * 5 + chunk * 16},
             "batched_vs_plain": batch_res,
             "served": serve_res,
+            "served_saturated_vs_batched": saturated,
             "gpu_launches": gpu_launches,
             "clocks": clocks,
             "cpu_baseline": cpu,
@@ -519,6 +546,29 @@ def run_served(args, NS, batch_res):
     return out
 
 
+def run_serve_vs_batch(args, NS, stream, rows):
+    """The same requests batched (one nasch_submit job) and served all at
+    once (saturated continuous batching): GPU rates of both and the served
+    fraction of the batched rate, with the server's GPU-busy fraction."""
+    from paper_2309_14311_gb300 import serve as SV
+    roads = [WL.road_params(r) for r in rows]
+    steps = [r["T"] for r in rows]
+    work = sum(r["N"] * r["T"] for r in rows)
+    with NS.Batch(roads, steps, stream=stream) as b:
+        b.wait()
+        batched_s = b.info().run_seconds
+    out = SV.run_poisson(rows, rate=float("inf"), memory_budget=args.serve_budget_gb << 30,
+                         steps_per_tick=args.serve_steps_per_tick, time_limit_s=args.serve_time_limit,
+                         stream_series=True)
+    served = out["vehicle_updates_per_s"]
+    return {"requests": len(rows), "vehicle_updates": work, "batched_vehicle_updates_per_s": work / batched_s,
+            "served_vehicle_updates_per_s": served, "served_over_batched": served / (work / batched_s),
+            "served_gpu_busy_fraction": out["gpu_busy_fraction"], "served_span_s": out["span_s"],
+            "ticks": out["ticks"], "streamed_steps": out["streamed_steps"],
+            "all_steps": sum(steps), "sample": f"the first {len(rows)} requests of the seed-11 stream, all queued at "
+                                               f"once"}
+
+
 class _Null:
     def __enter__(self):
         return self
@@ -542,6 +592,9 @@ def run_workload(args):
     serve                the seed-11 request stream (first --serve-requests),
                          Poisson arrivals at --serve-load x capacity, 40 GB
                          budget; p50/p99 latency and aggregate rate;
+    serve-vs-batch       the first --serve-requests requests batched in one
+                         job and served all at once (series streamed back):
+                         the served rate as a fraction of the batched one;
     snapshots            output while running: a 2^28-cell road (2^24 cars)
                          run for --other-steps steps with no output, with
                          snapshots of its cells every 50 and every 10 steps
@@ -679,6 +732,9 @@ def run_workload(args):
         out.update(roads=len(roads), L=args.fd_L, T=T, warmup=WL.FD_WARMUP, vmax=args.fd_vmax,
                    vehicle_updates=work, batched_gpu_seconds=inf.run_seconds, wall_seconds=wall,
                    vehicle_updates_per_s=work / inf.run_seconds, **FD.summary(rows), table=rows)
+    elif args.workload == "serve-vs-batch":
+        rows = WL.request_stream()[: args.serve_requests]
+        out.update(run_serve_vs_batch(args, NS, stream, rows))
     elif args.workload == "serve":
         from paper_2309_14311_gb300 import serve as SV
         rows = WL.request_stream()[: args.serve_requests]
@@ -739,8 +795,8 @@ def main(argv=None):
     ap.add_argument("--cpu-steps", type=int, default=10)
     ap.add_argument("--ref-steps-per-step", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["large-road", "ensemble", "fundamental-diagram", "serve", "k-sweep",
-                                           "snapshots", "open-road"],
+    ap.add_argument("--workload", choices=["large-road", "ensemble", "fundamental-diagram", "serve", "serve-vs-batch",
+                                           "k-sweep", "snapshots", "open-road"],
                     default="large-road", help="large-road is the benchmark line; the others print their own line")
     ap.add_argument("--sweep-k", default="1,2,4,8,16,32", help="fusion depths of the k-sweep workload")
     ap.add_argument("--roads", type=int, default=4096)

@@ -274,19 +274,28 @@ int nasch_get_tuning(double *rho_star, int32_t *k_agent, int32_t *k_grid);
  * each scheduling round admits queued requests, oldest first, while their
  * state and statistics fit the device-memory budget, and enqueues one tick
  * of launches over every resident road, each continuing from its own step -
- * requests admitted later run in the same launches as earlier ones.
- * Finished requests return their per-step statistics (and, with keep_state,
- * their final state) to the host and their memory to the budget.  A
- * request's result equals the same road run alone.
+ * requests admitted later run in the same launches as earlier ones.  A tick
+ * is at least steps_per_tick super-step launches, and more (up to
+ * max_steps_per_tick) while the resident roads are too few to keep the GPU
+ * busy for target_tick_ms per tick; up to ticks_in_flight ticks are queued
+ * on the GPU at once, so the host plans the next while the GPU runs.  The
+ * per-step statistics of a running request can be streamed back as its
+ * steps finish (nasch_server_poll_series).  Finished requests return their
+ * per-step statistics (and, with keep_state, their final state) to the host
+ * and their memory to the budget.  A request's result equals the same road
+ * run alone.
  * ------------------------------------------------------------------------ */
 typedef struct nasch_server_s *nasch_server;
 
 typedef struct nasch_server_config {
     int64_t memory_budget;   /* device bytes for resident roads (one slab, allocated at create) */
-    int32_t steps_per_tick;  /* super-step launches per scheduling round (default 8) */
+    int32_t steps_per_tick;  /* fewest super-step launches per scheduling round (default 8) */
     int32_t max_resident;    /* most roads resident at once (default 4096) */
     int32_t keep_state;      /* nonzero: also copy each request's final state back */
     void *stream;            /* cudaStream_t; NULL = one owned by the server */
+    int32_t max_steps_per_tick; /* most super-step launches per round (default 256; >= steps_per_tick) */
+    int32_t ticks_in_flight;    /* ticks queued on the GPU at once, 1..4 (default 3) */
+    double target_tick_ms;      /* GPU time a tick aims at (default 4; 0: always steps_per_tick) */
 } nasch_server_config;
 
 typedef struct nasch_request_result {
@@ -307,9 +316,23 @@ typedef struct nasch_server_info {
     int64_t vehicle_steps_done;
     int32_t blocks;
     double now;              /* seconds since the server was created (host clock) */
+    double gpu_busy_seconds; /* GPU time of the finished ticks (first launch to last, per tick) */
+    int32_t last_tick_super_steps;  /* launches in the latest tick */
+    int32_t pad;
 } nasch_server_info;
 
-/* Defaults: 40 GiB budget, 8 launches per tick, 4096 resident roads. */
+/* One piece of a request's per-step series (nasch_server_poll_series):
+ * steps first_step .. first_step+count-1 of request request_id, stored at
+ * sum_v_host[offset ..] and crossings_host[offset ..]. */
+typedef struct nasch_series_chunk {
+    uint64_t request_id;
+    int64_t first_step;
+    int64_t count;
+    int64_t offset;
+} nasch_series_chunk;
+
+/* Defaults: 40 GiB budget, 8 to 256 launches per tick aiming at 4 ms of GPU
+ * time, 3 ticks in flight, 4096 resident roads. */
 void nasch_server_config_init(nasch_server_config *cfg);
 int nasch_server_create(const nasch_server_config *cfg, nasch_server *out);
 /* Queue one request (thread-safe).  NASCH_ENOMEM if it could never fit the budget. */
@@ -328,6 +351,19 @@ int nasch_server_poll(nasch_server s, nasch_request_result *out, int64_t cap, in
  * increasing cell order.  Any output may be NULL. */
 int nasch_server_result(nasch_server s, uint64_t request_id, uint64_t *sum_v_host, uint64_t *crossings_host,
                         int64_t cap_steps, int32_t *x_host, uint8_t *v_host, int64_t cap_cars);
+/* Stream the per-step statistics of admitted requests as their steps finish:
+ * copies, for each request with steps that the GPU has finished and that
+ * were not returned before, those steps' sum_v and crossings into
+ * sum_v_host / crossings_host (one chunk per request, in order, at most
+ * cap_steps steps in all) and describes each chunk in chunks[0..*n_chunks).
+ * A request's chunks come in step order and, put together, are its whole
+ * series; the last one may come after the request has finished (poll it
+ * with nasch_server_poll as usual, and call this before releasing it).
+ * Either output array may be NULL; cap_chunks or cap_steps 0 returns
+ * nothing.  Reads what finished ticks wrote, on a stream of its own, and
+ * does not wait for running ticks. */
+int nasch_server_poll_series(nasch_server s, nasch_series_chunk *chunks, int64_t cap_chunks, uint64_t *sum_v_host,
+                             uint64_t *crossings_host, int64_t cap_steps, int64_t *n_chunks);
 /* Forget a finished, polled request (frees its host copies). */
 int nasch_server_release(nasch_server s, uint64_t request_id);
 /* Cancel a queued or running request; it finishes with NASCH_ECANCELED. */

@@ -4,6 +4,8 @@
 //
 // Tiled kernel.  A warp-tile is 512 consecutive cars held in registers, 16
 // per lane, and every warp works alone (no block barrier in the step loop).
+// A tile that cannot reach cell L-1 within the launch (all but the few
+// near the ring's wrap point) steps without modular cell arithmetic.
 // Car i's next state depends on car i+1's position only, so after k fused
 // steps the first 512 - round_up(k, 16) cars of the tile are exact and the
 // rest (the look-ahead halo) is discarded; warp-tiles overlap by the halo.
@@ -25,8 +27,9 @@ namespace {
 
 // Persistent grid of independent warps; warp w takes warp-tiles w, w + W, ...
 template <int R, Draw D>
-__global__ void __launch_bounds__(kAgentThreads) agent_tiled_kernel(const AgentStep a, const uint32_t owned,
-                                                                    const uint32_t n_tiles)
+__global__ void __launch_bounds__(kAgentThreads, kAgentBlocksPerSm) agent_tiled_kernel(const AgentStep a,
+                                                                                       const uint32_t owned,
+                                                                                       const uint32_t n_tiles)
 {
     __shared__ unsigned long long s_sum[kMaxFusedSteps];
     __shared__ unsigned long long s_cross[kMaxFusedSteps];

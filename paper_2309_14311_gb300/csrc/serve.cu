@@ -9,14 +9,23 @@
 //      statistics fit the device-memory budget (a first-fit allocator over
 //      one slab of that size) and a slot is free; new roads get their Floyd
 //      start on the GPU;
-//   3. enqueues one tick: up to steps_per_tick launches of the super-step
-//      kernel over the items of every resident road, each road continuing
-//      from its own super-step, so a request admitted now runs in the same
-//      launches as requests admitted earlier.
-// At most two ticks are in flight, so planning the next tick overlaps the
-// GPU running the current one.  A request's result is identical to the
-// same road run alone: its draws are keyed by its own seed and road id,
-// never by its slot or by what else is resident.
+//   3. enqueues one tick: M launches of the super-step kernel over the items
+//      of every resident road, each road continuing from its own super-step,
+//      so a request admitted now runs in the same launches as requests
+//      admitted earlier.  M is steps_per_tick, or more (up to
+//      max_steps_per_tick) when the resident roads are too few to keep the
+//      GPU busy for target_tick_ms: the tick's work is estimated from the
+//      roads' cars and the rate the last finished ticks ran at.
+// Up to ticks_in_flight ticks are queued at once; each has its own host
+// staging buffers, reused only after that tick has finished, so planning
+// the next tick overlaps the GPU running the earlier ones.  Every tick is
+// timed by a pair of events (the GPU's busy time).  When a tick finishes,
+// the steps it completed become readable: nasch_server_poll_series copies
+// them from the device on a stream of its own (the kernels that wrote them
+// have finished), or from the host copy once the request has retired.
+// A request's result is identical to the same road run alone: its draws
+// are keyed by its own seed and road id, never by its slot or by what else
+// is resident.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -102,17 +111,37 @@ struct Request {
     int slot = -1;
     int64_t last_tick = -1;   // sequence number of the last tick that ran it
     bool canceled = false;
+    bool retired = false;     // results copied back, device memory released
     int status = NASCH_OK;
     double submit_t = 0, admit_t = 0, done_t = 0;
     std::vector<uint64_t> sum_v, crossings;
     std::vector<int32_t> x;
     std::vector<uint8_t> v;
+    // streamed series: steps whose statistics are final (ticks finished),
+    // steps already returned by nasch_server_poll_series, and the steps
+    // completed by each tick still in flight, oldest first
+    int64_t ready = 0, sent = 0;
+    std::deque<std::pair<int64_t, int64_t>> marks;   // (tick sequence, steps done after it)
+};
+
+// Host staging of one tick in flight; reused only after that tick finished.
+struct TickBuf {
+    BatchRoadDev *h_slots = nullptr;     // pinned: slot descriptors
+    BatchRoadDev *h_new = nullptr;       // pinned: descriptors of roads initialised this round
+    uint64_t **h_new_bm = nullptr;       // pinned: their Floyd bit maps
+    BatchItem *h_items = nullptr;        // pinned: work-list
+    BatchItem *d_items = nullptr;        // device work-list
+    uint32_t *d_counters = nullptr;      // device work-list cursors, one per launch
 };
 
 struct Tick {
     int64_t seq = 0;
-    cudaEvent_t ev = nullptr;
+    int64_t vehicle_steps = 0;           // work of the tick (cars x steps)
+    int32_t launches = 0;
+    cudaEvent_t ev0 = nullptr, ev = nullptr;   // timing events around the tick's launches
 };
+
+constexpr int kMaxTicksInFlight = 4;
 
 }  // namespace
 }  // namespace nasch
@@ -123,6 +152,7 @@ struct nasch_server_s {
     nasch_server_config cfg{};
     int device = 0, sms = 1;
     cudaStream_t stream = nullptr;
+    cudaStream_t copy_stream = nullptr;  // reads of finished series
     bool own_stream = false;
     double rho_star = 0.2;
     int k_agent = 8, k_grid = 8;
@@ -131,15 +161,11 @@ struct nasch_server_s {
     int max_slots = 0;
     std::vector<int> free_slots;
     BatchRoadDev *d_slots = nullptr;
-    BatchRoadDev *h_slots[2] = {nullptr, nullptr};   // pinned staging of slot descriptors, one per tick in flight
     BatchRoadDev *d_new = nullptr;       // descriptors of roads initialised this round
     uint64_t **d_new_bm = nullptr;
-    BatchRoadDev *h_new[2] = {nullptr, nullptr};
-    uint64_t **h_new_bm[2] = {nullptr, nullptr};
-    BatchItem *d_items[2] = {nullptr, nullptr};
-    BatchItem *h_items[2] = {nullptr, nullptr};
+    TickBuf bufs[kMaxTicksInFlight];
+    int depth = 2;                       // ticks in flight
     int64_t items_cap = 0;
-    uint32_t *d_counters[2] = {nullptr, nullptr};
     uint32_t *h_cancel = nullptr, *d_cancel = nullptr;
     uint32_t padded = 0;
     int blocks = 1;
@@ -149,8 +175,12 @@ struct nasch_server_s {
     std::vector<Tick> spare_ticks;
     std::unordered_map<uint64_t, Request *> by_id;
     std::vector<Request *> completed;    // not yet polled
+    std::vector<Request *> streaming;    // admitted, series not yet fully returned, in admission order
     int64_t tick_seq = 0, harvested_seq = -1;
     int64_t n_done = 0, vehicle_steps_done = 0;
+    double gpu_busy = 0.0;
+    double rate = 0.0;                   // vehicle-steps per GPU second of the last finished ticks
+    int32_t last_launches = 0;
     std::chrono::steady_clock::time_point t0;
     std::mutex mu;
 
@@ -174,28 +204,39 @@ size_t request_bytes(const Request &r)
     return b;
 }
 
+void free_tick_buf(TickBuf &b)
+{
+    cudaFree(b.d_items);
+    cudaFree(b.d_counters);
+    if (b.h_items) cudaFreeHost(b.h_items);
+    if (b.h_slots) cudaFreeHost(b.h_slots);
+    if (b.h_new) cudaFreeHost(b.h_new);
+    if (b.h_new_bm) cudaFreeHost(b.h_new_bm);
+    b = TickBuf{};
+}
+
 void destroy_server(nasch_server s)
 {
     if (!s) return;
     if (s->stream) cudaStreamSynchronize(s->stream);
-    for (auto &t : s->inflight) cudaEventDestroy(t.ev);
-    for (auto &t : s->spare_ticks) cudaEventDestroy(t.ev);
+    if (s->copy_stream) cudaStreamSynchronize(s->copy_stream);
+    for (auto &t : s->inflight) {
+        cudaEventDestroy(t.ev0);
+        cudaEventDestroy(t.ev);
+    }
+    for (auto &t : s->spare_ticks) {
+        cudaEventDestroy(t.ev0);
+        cudaEventDestroy(t.ev);
+    }
     cudaFree(s->slab);
     cudaFree(s->d_slots);
     cudaFree(s->d_new);
     cudaFree(s->d_new_bm);
-    for (int i = 0; i < 2; ++i) {
-        cudaFree(s->d_items[i]);
-        cudaFree(s->d_counters[i]);
-        if (s->h_items[i]) cudaFreeHost(s->h_items[i]);
-        if (s->h_new[i]) cudaFreeHost(s->h_new[i]);
-        if (s->h_new_bm[i]) cudaFreeHost(s->h_new_bm[i]);
-    }
-    for (int i = 0; i < 2; ++i)
-        if (s->h_slots[i]) cudaFreeHost(s->h_slots[i]);
+    for (auto &b : s->bufs) free_tick_buf(b);
     if (s->h_cancel) cudaFreeHost(s->h_cancel);
     // every request not yet released (queued, resident or finished) is in by_id
     for (auto &kv : s->by_id) delete kv.second;
+    if (s->copy_stream) cudaStreamDestroy(s->copy_stream);
     if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
     delete s;
 }
@@ -204,7 +245,11 @@ void destroy_server(nasch_server s)
 int retire(nasch_server s, Request *r)
 {
     cudaError_t e = cudaSuccess;
-    if (!r->canceled && r->T > 0) {
+    // a request that ran no tick (no steps, or no cars) retires in the round
+    // that admitted it: its zeroed series and its start state were written by
+    // work on the server's stream that no finished tick covers yet
+    if (r->super == 0 && !r->canceled) e = cudaStreamSynchronize(s->stream);
+    if (e == cudaSuccess && !r->canceled && r->T > 0) {
         r->sum_v.resize((size_t)r->T);
         r->crossings.resize((size_t)r->T);
         e = cudaMemcpy(r->sum_v.data(), r->rd.sum_v, (size_t)r->T * 8, cudaMemcpyDeviceToHost);
@@ -235,6 +280,9 @@ int retire(nasch_server s, Request *r)
     if (r->slot >= 0) s->free_slots.push_back(r->slot);
     r->slot = -1;
     r->bytes = 0;
+    r->retired = true;
+    r->marks.clear();
+    r->ready = r->canceled ? r->sent : r->T;   // the whole series is on the host now
     r->done_t = s->now();
     r->status = r->canceled ? NASCH_ECANCELED : NASCH_OK;
     if (!r->canceled) s->vehicle_steps_done += (int64_t)r->rd.N * r->T;
@@ -261,6 +309,16 @@ int retire_ready(nasch_server s)
     return st;
 }
 
+// Steps whose statistics the ticks finished up to `seq` made final.
+void advance_series(nasch_server s, int64_t seq)
+{
+    for (auto *r : s->resident)
+        while (!r->marks.empty() && r->marks.front().first <= seq) {
+            r->ready = std::max(r->ready, r->marks.front().second);
+            r->marks.pop_front();
+        }
+}
+
 // Observe finished ticks (blocking on the oldest if `block`).
 int harvest(nasch_server s, bool block)
 {
@@ -269,7 +327,16 @@ int harvest(nasch_server s, bool block)
         cudaError_t q = block ? cudaEventSynchronize(t.ev) : cudaEventQuery(t.ev);
         if (q == cudaErrorNotReady) break;
         if (q != cudaSuccess) return cuda_fail(q, "tick completion");
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, t.ev0, t.ev) == cudaSuccess && ms > 0.f) {
+            s->gpu_busy += ms * 1e-3;
+            const double r = (double)t.vehicle_steps / (ms * 1e-3);
+            s->rate = s->rate > 0.0 ? 0.5 * (s->rate + r) : r;
+        } else {
+            cudaGetLastError();
+        }
         s->harvested_seq = t.seq;
+        advance_series(s, t.seq);
         s->spare_ticks.push_back(t);
         s->inflight.pop_front();
         block = false;
@@ -288,13 +355,14 @@ int ensure_items(nasch_server s, int64_t need)
         if (st) return st;
     }
     const int64_t cap = std::max<int64_t>(need, 2 * s->items_cap);
-    for (int i = 0; i < 2; ++i) {
-        cudaFree(s->d_items[i]);
-        if (s->h_items[i]) cudaFreeHost(s->h_items[i]);
-        s->d_items[i] = nullptr;
-        s->h_items[i] = nullptr;
-        cudaError_t e = cudaMalloc(&s->d_items[i], (size_t)cap * sizeof(BatchItem));
-        if (e == cudaSuccess) e = cudaHostAlloc((void **)&s->h_items[i], (size_t)cap * sizeof(BatchItem), 0);
+    for (int i = 0; i < s->depth; ++i) {
+        TickBuf &b = s->bufs[i];
+        cudaFree(b.d_items);
+        if (b.h_items) cudaFreeHost(b.h_items);
+        b.d_items = nullptr;
+        b.h_items = nullptr;
+        cudaError_t e = cudaMalloc(&b.d_items, (size_t)cap * sizeof(BatchItem));
+        if (e == cudaSuccess) e = cudaHostAlloc((void **)&b.h_items, (size_t)cap * sizeof(BatchItem), 0);
         if (e != cudaSuccess) return cuda_fail(e, "work-list buffers");
     }
     s->items_cap = cap;
@@ -303,8 +371,9 @@ int ensure_items(nasch_server s, int64_t need)
 
 // Admit queued requests (oldest first) while memory and slots allow, and
 // enqueue their initial state.
-int admit(nasch_server s, int buf)
+int admit(nasch_server s, TickBuf &buf, bool *staged)
 {
+    *staged = false;
     std::vector<Request *> fresh;
     while (!s->queue.empty()) {
         Request *r = s->queue.front();
@@ -312,6 +381,7 @@ int admit(nasch_server s, int buf)
             s->queue.pop_front();
             r->status = NASCH_ECANCELED;
             r->done_t = s->now();
+            r->retired = true;
             s->completed.push_back(r);
             ++s->n_done;
             continue;
@@ -363,19 +433,21 @@ int admit(nasch_server s, int buf)
             e = cudaMemsetAsync(static_cast<char *>(s->slab) + bm_off, 0, bm_bytes, s->stream);
         if (e != cudaSuccess) return cuda_fail(e, "admit request");
         s->resident.push_back(r);
+        s->streaming.push_back(r);
         if (r->rd.N > 0) fresh.push_back(r);
-        if (r->super == 0) r->last_tick = s->harvested_seq;   // nothing to run: retire at once
+        if (r->super == 0) r->last_tick = s->harvested_seq;   // nothing to run (no steps or no cars): retire at once
     }
     if (!fresh.empty()) {
         for (size_t i = 0; i < fresh.size(); ++i) {
-            s->h_new[buf][i] = fresh[i]->rd;
-            s->h_new_bm[buf][i] = reinterpret_cast<uint64_t *>(static_cast<char *>(s->slab) + fresh[i]->bm_off);
+            buf.h_new[i] = fresh[i]->rd;
+            buf.h_new_bm[i] = reinterpret_cast<uint64_t *>(static_cast<char *>(s->slab) + fresh[i]->bm_off);
         }
-        cudaError_t e = cudaMemcpyAsync(s->d_new, s->h_new[buf], fresh.size() * sizeof(BatchRoadDev),
+        cudaError_t e = cudaMemcpyAsync(s->d_new, buf.h_new, fresh.size() * sizeof(BatchRoadDev),
                                         cudaMemcpyHostToDevice, s->stream);
         if (e == cudaSuccess)
-            e = cudaMemcpyAsync(s->d_new_bm, s->h_new_bm[buf], fresh.size() * sizeof(uint64_t *),
+            e = cudaMemcpyAsync(s->d_new_bm, buf.h_new_bm, fresh.size() * sizeof(uint64_t *),
                                 cudaMemcpyHostToDevice, s->stream);
+        *staged = true;
         if (e == cudaSuccess) e = launch_batch_floyd(s->d_new, (uint32_t)fresh.size(), s->d_new_bm, s->sms, s->stream);
         if (e != cudaSuccess) return cuda_fail(e, "initialise admitted roads");
         // the bit maps were only needed by the initialisation, which the stream
@@ -388,8 +460,23 @@ int admit(nasch_server s, int buf)
     return retire_ready(s);
 }
 
+// Launches of the next tick: steps_per_tick, or more while the resident
+// work per launch is too small to keep the GPU busy for target_tick_ms.
+int64_t tick_launches(nasch_server s, const std::vector<Request *> &act)
+{
+    const int64_t longest = act.front()->super - act.front()->done_super;
+    int64_t M = s->cfg.steps_per_tick;
+    if (s->cfg.target_tick_ms > 0.0 && s->rate > 0.0) {
+        double per_launch = 0.0;   // cars x steps of one launch over every active road
+        for (auto *r : act) per_launch += (double)r->rd.N * (double)r->rd.k;
+        const double want = s->cfg.target_tick_ms * 1e-3 * s->rate / std::max(per_launch, 1.0);
+        if (want > (double)M) M = (int64_t)std::min<double>(want, (double)s->cfg.max_steps_per_tick);
+    }
+    return std::min<int64_t>(M, longest);
+}
+
 // Plan and enqueue one tick over the resident roads.
-int enqueue_tick(nasch_server s, int buf)
+int enqueue_tick(nasch_server s, TickBuf &buf)
 {
     std::vector<Request *> act;
     for (auto *r : s->resident)
@@ -398,63 +485,88 @@ int enqueue_tick(nasch_server s, int buf)
     std::stable_sort(act.begin(), act.end(), [](const Request *a, const Request *b) {
         return a->super - a->done_super > b->super - b->done_super;
     });
-    const int64_t M = std::min<int64_t>(s->cfg.steps_per_tick, act.front()->super - act.front()->done_super);
+    const int64_t M = tick_launches(s, act);
     int64_t total = 0;
     for (auto *r : act) total += r->n_items;
     int st = ensure_items(s, total);
     if (st) return st;
     // work-list (roads by remaining super-steps, longest first) and prefix counts
     std::vector<uint32_t> active((size_t)M, 0);
-    int64_t k = 0;
+    int64_t k = 0, work = 0;
     for (auto *r : act) {
-        for (int64_t t = 0; t < r->n_items; ++t) s->h_items[buf][k++] = BatchItem{(uint32_t)r->slot, (uint32_t)t};
+        for (int64_t t = 0; t < r->n_items; ++t) buf.h_items[k++] = BatchItem{(uint32_t)r->slot, (uint32_t)t};
         const int64_t runs = std::min<int64_t>(M, r->super - r->done_super);
         for (int64_t j = 0; j < runs; ++j) active[(size_t)j] = (uint32_t)k;
         r->rd.sbase = (uint32_t)r->done_super;
+        const int64_t steps_before = std::min<int64_t>(r->T, r->done_super * (int64_t)r->rd.k);
+        const int64_t steps_after = std::min<int64_t>(r->T, (r->done_super + runs) * (int64_t)r->rd.k);
+        work += (int64_t)r->rd.N * (steps_after - steps_before);
     }
     // every resident road's descriptor, in one copy of the slots up to the
     // highest in use (the others are never listed); the staging copy must stay
-    // unchanged until this asynchronous copy has run: ticks alternate between
-    // two staging buffers, and a buffer is reused only after the tick that
-    // used it has finished
+    // unchanged until this asynchronous copy has run, so each tick in flight
+    // has its own staging buffers
     int top = 0;
     for (auto *r : s->resident) {
-        s->h_slots[buf][r->slot] = r->rd;
+        buf.h_slots[r->slot] = r->rd;
         top = std::max(top, r->slot + 1);
     }
-    cudaError_t e = cudaMemcpyAsync(s->d_items[buf], s->h_items[buf], (size_t)total * sizeof(BatchItem),
-                                    cudaMemcpyHostToDevice, s->stream);
+    Tick t;
+    cudaError_t e = cudaSuccess;
+    if (!s->spare_ticks.empty()) {
+        t = s->spare_ticks.back();
+        s->spare_ticks.pop_back();
+    } else {
+        e = cudaEventCreate(&t.ev0);
+        if (e == cudaSuccess) e = cudaEventCreate(&t.ev);
+    }
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(s->d_slots, s->h_slots[buf], (size_t)top * sizeof(BatchRoadDev), cudaMemcpyHostToDevice,
+        e = cudaMemcpyAsync(buf.d_items, buf.h_items, (size_t)total * sizeof(BatchItem), cudaMemcpyHostToDevice,
                             s->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(s->d_counters[buf], 0, sizeof(uint32_t) * (size_t)M, s->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(s->d_slots, buf.h_slots, (size_t)top * sizeof(BatchRoadDev), cudaMemcpyHostToDevice,
+                            s->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(buf.d_counters, 0, sizeof(uint32_t) * (size_t)M, s->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(t.ev0, s->stream);
     for (int64_t j = 0; j < M && e == cudaSuccess; ++j) {
         BatchLaunch bl;
         bl.roads = s->d_slots;
-        bl.items = s->d_items[buf];
+        bl.items = buf.d_items;
         bl.n_items = active[(size_t)j];
         bl.super_step = (uint32_t)j;
-        bl.counter = s->d_counters[buf] + j;
+        bl.counter = buf.d_counters + j;
         bl.cancel = s->d_cancel;
         bl.padded = s->padded;
         e = launch_batch_super_step(bl, (int)std::min<int64_t>(s->blocks, std::max<uint32_t>(bl.n_items, 1u)), s->stream);
     }
-    Tick t;
-    if (!s->spare_ticks.empty()) {
-        t = s->spare_ticks.back();
-        s->spare_ticks.pop_back();
-    } else if (e == cudaSuccess) {
-        e = cudaEventCreateWithFlags(&t.ev, cudaEventDisableTiming);
-    }
     t.seq = s->tick_seq++;
+    t.vehicle_steps = work;
+    t.launches = (int32_t)M;
     if (e == cudaSuccess) e = cudaEventRecord(t.ev, s->stream);
-    if (e != cudaSuccess) return cuda_fail(e, "enqueue tick");
+    if (e != cudaSuccess) {
+        if (t.ev0) cudaEventDestroy(t.ev0);
+        if (t.ev) cudaEventDestroy(t.ev);
+        return cuda_fail(e, "enqueue tick");
+    }
     s->inflight.push_back(t);
+    s->last_launches = (int32_t)M;
     for (auto *r : act) {
         r->done_super += std::min<int64_t>(M, r->super - r->done_super);
         r->last_tick = t.seq;
+        r->marks.emplace_back(t.seq, std::min<int64_t>(r->T, r->done_super * (int64_t)r->rd.k));
     }
     return NASCH_OK;
+}
+
+int alloc_tick_buf(nasch_server s, TickBuf &b)
+{
+    const size_t n = (size_t)s->max_slots;
+    cudaError_t e = cudaHostAlloc((void **)&b.h_slots, sizeof(BatchRoadDev) * n, 0);
+    if (e == cudaSuccess) e = cudaHostAlloc((void **)&b.h_new, sizeof(BatchRoadDev) * n, 0);
+    if (e == cudaSuccess) e = cudaHostAlloc((void **)&b.h_new_bm, sizeof(uint64_t *) * n, 0);
+    if (e == cudaSuccess)
+        e = cudaMalloc(&b.d_counters, sizeof(uint32_t) * (size_t)std::max(s->cfg.max_steps_per_tick, s->cfg.steps_per_tick));
+    return e == cudaSuccess ? NASCH_OK : cuda_fail(e, "tick staging buffers");
 }
 
 }  // namespace
@@ -468,6 +580,9 @@ void nasch_server_config_init(nasch_server_config *cfg)
     cfg->memory_budget = int64_t(40) << 30;
     cfg->steps_per_tick = 8;
     cfg->max_resident = 4096;
+    cfg->max_steps_per_tick = 256;
+    cfg->ticks_in_flight = 3;
+    cfg->target_tick_ms = 4.0;
 }
 
 int nasch_server_create(const nasch_server_config *cfg, nasch_server *out)
@@ -477,10 +592,18 @@ int nasch_server_create(const nasch_server_config *cfg, nasch_server *out)
     *out = nullptr;
     if (cfg->memory_budget < (1 << 20)) return fail(NASCH_EINVAL, "memory budget below 1 MiB");
     if (cfg->steps_per_tick < 1 || cfg->steps_per_tick > 4096) return fail(NASCH_EINVAL, "steps_per_tick outside 1..4096");
+    if (cfg->max_steps_per_tick < 0 || cfg->max_steps_per_tick > 4096)
+        return fail(NASCH_EINVAL, "max_steps_per_tick outside 0..4096");
     if (cfg->max_resident < 1 || cfg->max_resident > (1 << 20)) return fail(NASCH_EINVAL, "max_resident outside 1..2^20");
+    if (cfg->ticks_in_flight < 0 || cfg->ticks_in_flight > kMaxTicksInFlight)
+        return fail(NASCH_EINVAL, "ticks_in_flight outside 1..%d", kMaxTicksInFlight);
+    if (!(cfg->target_tick_ms >= 0.0 && cfg->target_tick_ms <= 1e4))
+        return fail(NASCH_EINVAL, "target_tick_ms outside 0..10000");
     nasch_server s = new (std::nothrow) nasch_server_s();
     if (!s) return fail(NASCH_ENOMEM, "host allocation");
     s->cfg = *cfg;
+    if (s->cfg.max_steps_per_tick < s->cfg.steps_per_tick) s->cfg.max_steps_per_tick = s->cfg.steps_per_tick;
+    s->depth = s->cfg.ticks_in_flight > 0 ? s->cfg.ticks_in_flight : 3;
     s->t0 = std::chrono::steady_clock::now();
     get_tuning_values(&s->rho_star, &s->k_agent, &s->k_grid);
     int st = device_info(&s->device, &s->sms);
@@ -501,17 +624,11 @@ int nasch_server_create(const nasch_server_config *cfg, nasch_server *out)
     }
     s->max_slots = cfg->max_resident;
     s->padded = (uint32_t)kGridSpan;
-    e = cudaMalloc(&s->slab, (size_t)cfg->memory_budget);
+    e = cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMalloc(&s->slab, (size_t)cfg->memory_budget);
     if (e == cudaSuccess) e = cudaMalloc(&s->d_slots, sizeof(BatchRoadDev) * (size_t)s->max_slots);
-    for (int i = 0; i < 2 && e == cudaSuccess; ++i)
-        e = cudaHostAlloc((void **)&s->h_slots[i], sizeof(BatchRoadDev) * (size_t)s->max_slots, 0);
     if (e == cudaSuccess) e = cudaMalloc(&s->d_new, sizeof(BatchRoadDev) * (size_t)s->max_slots);
     if (e == cudaSuccess) e = cudaMalloc(&s->d_new_bm, sizeof(uint64_t *) * (size_t)s->max_slots);
-    for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
-        e = cudaHostAlloc((void **)&s->h_new[i], sizeof(BatchRoadDev) * (size_t)s->max_slots, 0);
-        if (e == cudaSuccess) e = cudaHostAlloc((void **)&s->h_new_bm[i], sizeof(uint64_t *) * (size_t)s->max_slots, 0);
-        if (e == cudaSuccess) e = cudaMalloc(&s->d_counters[i], sizeof(uint32_t) * (size_t)cfg->steps_per_tick);
-    }
     if (e == cudaSuccess) e = cudaHostAlloc((void **)&s->h_cancel, sizeof(uint32_t), cudaHostAllocMapped);
     if (e == cudaSuccess) {
         *s->h_cancel = 0;
@@ -523,6 +640,11 @@ int nasch_server_create(const nasch_server_config *cfg, nasch_server *out)
                                                      (long long)cfg->memory_budget)
                                               : cuda_fail(e, "server allocation");
     }
+    for (int i = 0; i < s->depth; ++i)
+        if ((st = alloc_tick_buf(s, s->bufs[i]))) {
+            destroy_server(s);
+            return st;
+        }
     s->alloc.reset((size_t)cfg->memory_budget);
     for (int i = s->max_slots - 1; i >= 0; --i) s->free_slots.push_back(i);
     s->blocks = s->sms * batch_blocks_per_sm(s->padded);
@@ -570,15 +692,23 @@ int nasch_server_step(nasch_server s, int64_t *pending)
     std::lock_guard<std::mutex> g(s->mu);
     int st = harvest(s, false);
     if (st) return st;
-    if (s->inflight.size() >= 2) {
+    if ((int)s->inflight.size() >= s->depth) {
         st = harvest(s, true);
         if (st) return st;
     }
-    const int buf = (int)(s->tick_seq & 1);
-    st = admit(s, buf);
+    TickBuf &buf = s->bufs[s->tick_seq % s->depth];
+    bool staged = false;
+    const int64_t seq_before = s->tick_seq;
+    st = admit(s, buf, &staged);
     if (st) return st;
     st = enqueue_tick(s, buf);
     if (st) return st;
+    if (staged && s->tick_seq == seq_before) {
+        // no tick took this staging buffer, so the next round reuses it: let
+        // its copies run first
+        const cudaError_t e = cudaStreamSynchronize(s->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    }
     if (s->inflight.empty() && !s->resident.empty()) st = retire_ready(s);
     if (pending) *pending = (int64_t)(s->queue.size() + s->resident.size());
     return st;
@@ -629,6 +759,52 @@ int nasch_server_poll(nasch_server s, nasch_request_result *out, int64_t cap, in
     return NASCH_OK;
 }
 
+int nasch_server_poll_series(nasch_server s, nasch_series_chunk *chunks, int64_t cap_chunks, uint64_t *sum_v_host,
+                             uint64_t *crossings_host, int64_t cap_steps, int64_t *n_chunks)
+{
+    clear_error();
+    if (!s || !n_chunks || (cap_chunks > 0 && !chunks) || cap_chunks < 0 || cap_steps < 0)
+        return fail(NASCH_EINVAL, "NULL or negative argument");
+    std::lock_guard<std::mutex> g(s->mu);
+    int st = harvest(s, false);   // make the ticks that have finished count
+    if (st) return st;
+    int64_t n = 0, used = 0;
+    cudaError_t e = cudaSuccess;
+    std::vector<Request *> keep;
+    keep.reserve(s->streaming.size());
+    for (auto *r : s->streaming) {
+        const int64_t avail = r->ready - r->sent;
+        if (avail > 0 && n < cap_chunks && used < cap_steps && e == cudaSuccess) {
+            const int64_t cnt = std::min<int64_t>(avail, cap_steps - used);
+            const int64_t first = r->sent;
+            if (r->retired) {   // the series is on the host
+                if (sum_v_host) std::copy(r->sum_v.begin() + first, r->sum_v.begin() + first + cnt, sum_v_host + used);
+                if (crossings_host)
+                    std::copy(r->crossings.begin() + first, r->crossings.begin() + first + cnt, crossings_host + used);
+            } else {            // steps written by finished ticks: read them from the device
+                if (sum_v_host)
+                    e = cudaMemcpyAsync(sum_v_host + used, r->rd.sum_v + first, (size_t)cnt * 8, cudaMemcpyDeviceToHost,
+                                        s->copy_stream);
+                if (e == cudaSuccess && crossings_host)
+                    e = cudaMemcpyAsync(crossings_host + used, r->rd.crossings + first, (size_t)cnt * 8,
+                                        cudaMemcpyDeviceToHost, s->copy_stream);
+            }
+            if (e == cudaSuccess) {
+                chunks[n++] = nasch_series_chunk{r->id, first, cnt, used};
+                used += cnt;
+                r->sent += cnt;
+            }
+        }
+        // a request leaves the list once all of its series has been returned
+        // (or it was cancelled and retired)
+        if (!(r->retired && (r->sent >= r->T || r->canceled))) keep.push_back(r);
+    }
+    s->streaming.swap(keep);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->copy_stream);
+    *n_chunks = n;
+    return e == cudaSuccess ? NASCH_OK : cuda_fail(e, "copy streamed series");
+}
+
 int nasch_server_result(nasch_server s, uint64_t request_id, uint64_t *sum_v_host, uint64_t *crossings_host,
                         int64_t cap_steps, int32_t *x_host, uint8_t *v_host, int64_t cap_cars)
 {
@@ -663,6 +839,8 @@ int nasch_server_release(nasch_server s, uint64_t request_id)
     if (r->done_t == 0) return fail(NASCH_EBUSY, "request %llu has not finished", (unsigned long long)request_id);
     for (auto *c : s->completed)
         if (c == r) return fail(NASCH_EBUSY, "request %llu has not been polled", (unsigned long long)request_id);
+    // a series not yet streamed is dropped with the request
+    s->streaming.erase(std::remove(s->streaming.begin(), s->streaming.end(), r), s->streaming.end());
     s->by_id.erase(it);
     delete r;
     return NASCH_OK;
@@ -685,6 +863,7 @@ int nasch_server_get_info(nasch_server s, nasch_server_info *info)
     clear_error();
     if (!s || !info) return fail(NASCH_EINVAL, "NULL argument");
     std::lock_guard<std::mutex> g(s->mu);
+    std::memset(info, 0, sizeof(*info));
     info->queued = (int64_t)s->queue.size();
     info->resident = (int64_t)s->resident.size();
     info->completed = s->n_done;
@@ -693,6 +872,8 @@ int nasch_server_get_info(nasch_server s, nasch_server_info *info)
     info->vehicle_steps_done = s->vehicle_steps_done;
     info->blocks = s->blocks;
     info->now = s->now();
+    info->gpu_busy_seconds = s->gpu_busy;
+    info->last_tick_super_steps = s->last_launches;
     return NASCH_OK;
 }
 

@@ -63,6 +63,68 @@ enum class Draw { kNever, kAlways, kPhilox };
 
 __host__ __device__ __forceinline__ Draw draw_mode(uint64_t thr) { return thr == 0 ? Draw::kNever : (thr > 0xFFFFFFFFull ? Draw::kAlways : Draw::kPhilox); }
 
+// The k fused steps of one warp-tile held in registers (32 lanes x R cars).
+// kInterior: no car of the tile can reach cell L-1 within the launch (the
+// tile does not wrap round the ring and its last car, moving at most vmax a
+// step, stays below L), so every leader in the tile lies ahead of its car in
+// plain cell order, no car crosses L-1 -> 0, and the step needs no modular
+// arithmetic and no crossing count.  The tile's last car takes the next
+// lane's first car as leader, and lane 31's last car is halo whose result is
+// discarded; its velocity stays <= vmax, which keeps its moves inside the
+// bound the interior test assumes.
+template <int R, Draw D, bool kFull, bool kInterior>
+__device__ __forceinline__ void agent_tile_steps(const AgentStep &a, uint32_t (&x)[R], uint32_t (&v)[R],
+                                                 uint32_t n_own, unsigned long long *s_sum,
+                                                 unsigned long long *s_cross)
+{
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t L = a.rc.L;
+    const uint32_t Lm1 = L - 1u;
+    const uint32_t vmax = a.rc.vmax;
+    const uint32_t thr = (uint32_t)a.rc.thr;
+    for (int s = 0; s < a.ksteps; ++s) {
+        const uint32_t step = a.step0 + (uint32_t)s;
+        // leader of the lane's last car: the next lane's first car (start-of-step)
+        const uint32_t lead_last = __shfl_down_sync(0xFFFFFFFFu, x[0], 1);
+        uint32_t tsum = 0, tcross = 0;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const uint32_t xi = x[r];
+            const uint32_t lead = (r + 1 < R) ? x[r + 1] : lead_last;
+            // empty cells ahead: (lead - x - 1) mod L, or L - 1 if the car is
+            // its own leader; on the ring as the smaller of two unsigned values
+            const uint32_t d = lead - xi;
+            const uint32_t gap = kInterior ? d - 1u : min(d - 1u, d + Lm1);
+            uint32_t vel = min(min(v[r] + 1u, vmax), gap);            // rules 1, 2
+            if (D == Draw::kAlways) {
+                vel -= vel > 0u ? 1u : 0u;                              // rule 3, p = 1
+            } else if (D == Draw::kPhilox) {
+                const uint32_t u = philox_word0(xi, step, a.rc.road, kTagSlowdown, a.rc.key0, a.rc.key1);
+                vel -= (vel > 0u && u < thr) ? 1u : 0u;                 // rule 3
+            }
+            uint32_t nx = xi + vel;                                     // rule 4
+            bool wrap = false;
+            if (!kInterior) {
+                wrap = nx >= L;
+                nx = wrap ? nx - L : nx;
+            }
+            x[r] = nx;
+            v[r] = vel;
+            if (kFull || (uint32_t)r < n_own) {
+                tsum += vel;
+                if (!kInterior) tcross += wrap ? 1u : 0u;
+            }
+        }
+        if (kFull && n_own == 0u) tsum = tcross = 0u;   // halo lanes
+        tsum = __reduce_add_sync(0xFFFFFFFFu, tsum);
+        if (!kInterior) tcross = __reduce_add_sync(0xFFFFFFFFu, tcross);
+        if (lane == 0 && (tsum | tcross)) {
+            atomicAdd(&s_sum[s], (unsigned long long)tsum);
+            if (!kInterior) atomicAdd(&s_cross[s], (unsigned long long)tcross);
+        }
+    }
+}
+
 // One warp-tile: 32 lanes x R consecutive cars in registers.  kFull: the
 // tile lies inside [0, N) and every owned car of a lane is owned (lanes are
 // either all-owned or all-halo), so no per-car ownership test is needed.
@@ -73,10 +135,6 @@ __device__ __forceinline__ void agent_warp_tile(const AgentStep &a, uint32_t t0,
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t e0 = lane * R;
     const uint32_t N = a.N;
-    const uint32_t L = a.rc.L;
-    const uint32_t Lm1 = L - 1u;
-    const uint32_t vmax = a.rc.vmax;
-    const uint32_t thr = (uint32_t)a.rc.thr;
     uint32_t x[R], v[R];
     if (kFull) {
         load_cars_vec<R>(a.x_in, a.v_in, t0 + e0, x, v);
@@ -91,45 +149,19 @@ __device__ __forceinline__ void agent_warp_tile(const AgentStep &a, uint32_t t0,
     // cars of this lane that the tile owns (statistics and write-back)
     const uint32_t own_end = min(owned, N - t0);
     const uint32_t n_own = e0 >= own_end ? 0u : min((uint32_t)R, own_end - e0);
-
-    for (int s = 0; s < a.ksteps; ++s) {
-        const uint32_t step = a.step0 + (uint32_t)s;
-        // leader of the lane's last car: the next lane's first car (start-of-step)
-        const uint32_t lead_last = __shfl_down_sync(0xFFFFFFFFu, x[0], 1);
-        uint32_t tsum = 0, tcross = 0;
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const uint32_t xi = x[r];
-            const uint32_t lead = (r + 1 < R) ? x[r + 1] : lead_last;
-            // empty cells ahead on the ring: (lead - x - 1) mod L, or L - 1 if
-            // the car is its own leader; as the smaller of two unsigned values
-            const uint32_t d = lead - xi;
-            const uint32_t gap = min(d - 1u, d + Lm1);
-            uint32_t vel = min(min(v[r] + 1u, vmax), gap);            // rules 1, 2
-            if (D == Draw::kAlways) {
-                vel -= vel > 0u ? 1u : 0u;                              // rule 3, p = 1
-            } else if (D == Draw::kPhilox) {
-                const uint32_t u = philox_word0(xi, step, a.rc.road, kTagSlowdown, a.rc.key0, a.rc.key1);
-                vel -= (vel > 0u && u < thr) ? 1u : 0u;                 // rule 3
-            }
-            uint32_t nx = xi + vel;                                     // rule 4
-            const bool wrap = nx >= L;
-            nx = wrap ? nx - L : nx;
-            x[r] = nx;
-            v[r] = vel;
-            if (kFull || (uint32_t)r < n_own) {
-                tsum += vel;
-                tcross += wrap ? 1u : 0u;
-            }
-        }
-        if (kFull && n_own == 0u) tsum = tcross = 0u;   // halo lanes
-        tsum = __reduce_add_sync(0xFFFFFFFFu, tsum);
-        tcross = __reduce_add_sync(0xFFFFFFFFu, tcross);
-        if (lane == 0 && (tsum | tcross)) {
-            atomicAdd(&s_sum[s], (unsigned long long)tsum);
-            atomicAdd(&s_cross[s], (unsigned long long)tcross);
-        }
+    bool interior = false;
+    if (kFull) {
+        // cars in cyclic order: a tile that does not wrap round the ring has
+        // its first car at or below its last; its last car (halo) moves at
+        // most k * vmax cells in the launch (L + k * vmax < 2^32)
+        const uint32_t first = __shfl_sync(0xFFFFFFFFu, x[0], 0);
+        const uint32_t last = __shfl_sync(0xFFFFFFFFu, x[R - 1], 31);
+        interior = first <= last && last + (uint32_t)a.ksteps * a.rc.vmax < a.rc.L;
     }
+    if (interior)
+        agent_tile_steps<R, D, kFull, true>(a, x, v, n_own, s_sum, s_cross);
+    else
+        agent_tile_steps<R, D, kFull, false>(a, x, v, n_own, s_sum, s_cross);
 
     if (n_own == (uint32_t)R) {
         store_cars_vec<R>(a.x_out, a.v_out, t0 + e0, x, v);

@@ -118,6 +118,7 @@ def _declare(lib) -> None:
         "nasch_batch_road_layout": (ctypes.c_int, [H, i64, P]),
         "nasch_batch_destroy": (None, [H]),
         "nasch_set_tuning": (ctypes.c_int, [dbl, i32, i32]),
+        "nasch_server_poll_series": (ctypes.c_int, [H, P, i64, P, P, i64, P]),
         "nasch_floyd_init_device_noalloc": (ctypes.c_int, [i64, i64, u64, u32, P, P]),
         "nasch_selftest_bounded_wait": (ctypes.c_int, [i64, P]),
         "nasch_server_config_init": (None, [P]),
@@ -395,7 +396,9 @@ class Batch:
 
 class ServerConfig(ctypes.Structure):
     _fields_ = [("memory_budget", ctypes.c_int64), ("steps_per_tick", ctypes.c_int32),
-                ("max_resident", ctypes.c_int32), ("keep_state", ctypes.c_int32), ("stream", ctypes.c_void_p)]
+                ("max_resident", ctypes.c_int32), ("keep_state", ctypes.c_int32), ("stream", ctypes.c_void_p),
+                ("max_steps_per_tick", ctypes.c_int32), ("ticks_in_flight", ctypes.c_int32),
+                ("target_tick_ms", ctypes.c_double)]
 
 
 class RequestResult(ctypes.Structure):
@@ -407,18 +410,31 @@ class RequestResult(ctypes.Structure):
 class ServerInfo(ctypes.Structure):
     _fields_ = [("queued", ctypes.c_int64), ("resident", ctypes.c_int64), ("completed", ctypes.c_int64),
                 ("bytes_in_use", ctypes.c_int64), ("ticks", ctypes.c_int64), ("vehicle_steps_done", ctypes.c_int64),
-                ("blocks", ctypes.c_int32), ("now", ctypes.c_double)]
+                ("blocks", ctypes.c_int32), ("now", ctypes.c_double), ("gpu_busy_seconds", ctypes.c_double),
+                ("last_tick_super_steps", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
+class SeriesChunk(ctypes.Structure):
+    _fields_ = [("request_id", ctypes.c_uint64), ("first_step", ctypes.c_int64), ("count", ctypes.c_int64),
+                ("offset", ctypes.c_int64)]
 
 
 class Server:
     """Continuous-batching request loop (``nasch_server_*``)."""
 
     def __init__(self, memory_budget: int = 40 << 30, steps_per_tick: int = 8, max_resident: int = 4096,
-                 keep_state: bool = False, stream=None):
+                 keep_state: bool = False, stream=None, max_steps_per_tick: int | None = None,
+                 ticks_in_flight: int | None = None, target_tick_ms: float | None = None):
         lib = load()
         cfg = ServerConfig()
         lib.nasch_server_config_init(ctypes.byref(cfg))
         cfg.memory_budget, cfg.steps_per_tick, cfg.max_resident = int(memory_budget), int(steps_per_tick), int(max_resident)
+        if max_steps_per_tick is not None:
+            cfg.max_steps_per_tick = int(max_steps_per_tick)
+        if ticks_in_flight is not None:
+            cfg.ticks_in_flight = int(ticks_in_flight)
+        if target_tick_ms is not None:
+            cfg.target_tick_ms = float(target_tick_ms)
         cfg.keep_state = 1 if keep_state else 0
         cfg.stream = _stream_handle(stream)
         self._stream_ref = stream
@@ -473,6 +489,21 @@ class Server:
             return sv[:T], cr[:T], x[:N], v[:N]
         _check(load().nasch_server_result(self._h, int(request_id), _ptr(sv), _ptr(cr), len(sv), None, None, 0))
         return sv[:T], cr[:T]
+
+    def poll_series(self, cap_chunks: int = 4096, cap_steps: int = 1 << 20):
+        """Newly finished steps of admitted requests: a list of
+        (request_id, first_step, sum_v, crossings) with array copies."""
+        buf = getattr(self, "_series_buf", None)
+        if buf is None or len(buf[0]) < cap_chunks or len(buf[1]) < max(cap_steps, 1):
+            buf = ((SeriesChunk * cap_chunks)(), np.zeros(max(cap_steps, 1), dtype=np.uint64),
+                   np.zeros(max(cap_steps, 1), dtype=np.uint64))
+            self._series_buf = buf
+        chunks, sv, cr = buf
+        n = ctypes.c_int64()
+        _check(load().nasch_server_poll_series(self._h, chunks, cap_chunks, _ptr(sv), _ptr(cr), cap_steps,
+                                               ctypes.byref(n)))
+        return [(c.request_id, c.first_step, sv[c.offset:c.offset + c.count].copy(),
+                 cr[c.offset:c.offset + c.count].copy()) for c in chunks[: n.value]]
 
     def release(self, request_id: int) -> None:
         _check(load().nasch_server_release(self._h, int(request_id)))

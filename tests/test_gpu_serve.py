@@ -135,3 +135,63 @@ def test_poisson_driver_small_stream_matches_oracle():
     assert out["completed"] == len(rows)
     assert sorted(checked) == list(range(len(rows)))
     assert out["latency_p99_s"] >= out["latency_p50_s"] > 0
+
+
+def test_series_stream_while_requests_run():
+    """Streamed per-step series: chunks of a running request arrive before it
+    finishes, in step order; put together they equal the request's final
+    series and the oracle's, for a long and a short request and a request
+    with no steps."""
+    reqs = [dict(L=1_000_000, N=120_000, vmax=5, p=0.13, seed=4, road_id=70, T=3000),
+            dict(L=40_000, N=9_000, vmax=8, p=0.3, seed=5, road_id=71, T=200),
+            dict(L=5_000, N=100, vmax=5, p=0.2, seed=6, road_id=72, T=0)]
+    got = {i: [] for i in range(len(reqs))}
+    early = set()
+    finished = set()
+    with NS.Server(memory_budget=1 << 30, steps_per_tick=2, max_steps_per_tick=2, target_tick_ms=0,
+                   ticks_in_flight=2) as srv:
+        for i, r in enumerate(reqs):
+            srv.submit(WL.road_params(r), r["T"], i)
+        pending = 1
+        while pending or len(finished) < len(reqs):
+            pending = srv.step()
+            for rid, first, sv, cr in srv.poll_series(cap_chunks=64, cap_steps=1 << 16):
+                if rid not in finished:
+                    early.add(rid)
+                got[rid].append((first, sv, cr))
+            finished |= {res["request_id"] for res in srv.poll()}
+        for rid, first, sv, cr in srv.poll_series():
+            got[rid].append((first, sv, cr))
+        assert srv.poll_series() == []
+        for i, r in enumerate(reqs):
+            firsts = [c[0] for c in got[i]]
+            lens = [len(c[1]) for c in got[i]]
+            assert firsts == list(np.cumsum([0] + lens[:-1])), (i, "chunks in step order")
+            sv = np.concatenate([c[1] for c in got[i]]) if got[i] else np.zeros(0, np.uint64)
+            cr = np.concatenate([c[2] for c in got[i]]) if got[i] else np.zeros(0, np.uint64)
+            fsv, fcr = srv.result(i)
+            osv, ocr, _ = oracle_request(r)
+            assert np.array_equal(sv, fsv) and np.array_equal(cr, fcr), (i, "streamed = final")
+            assert np.array_equal(sv, osv) and np.array_equal(cr, ocr), (i, "streamed = oracle")
+        assert 0 in early, "the long request's first chunk came only after it finished"
+        assert len(got[0]) > 2
+
+
+def test_tick_grows_when_few_roads_are_resident():
+    """With one small road resident, a tick runs more launches than
+    steps_per_tick (up to max_steps_per_tick) to reach its GPU-time target;
+    the result is unchanged."""
+    r = dict(L=200_000, N=20_000, vmax=5, p=0.13, seed=9, road_id=80, T=20_000)
+    with NS.Server(memory_budget=1 << 30, steps_per_tick=2, max_steps_per_tick=64, target_tick_ms=5.0) as srv:
+        srv.submit(WL.road_params(r), r["T"], 0)
+        most = 0
+        while srv.step():
+            most = max(most, srv.info().last_tick_super_steps)
+        srv.drain(600000)
+        assert 2 < most <= 64
+        assert srv.info().gpu_busy_seconds > 0
+        (res,) = srv.poll()
+        sv, cr = srv.result(0)
+        osv, ocr, _ = oracle_request(r)
+        assert np.array_equal(sv, osv) and np.array_equal(cr, ocr)
+
