@@ -191,7 +191,12 @@ def kernel_source_hash(kernel: str) -> str:
 # streaming kernels grows in proportion).  Keyed by the hash of the kernel's
 # sources (comments and layout aside) when it was captured: a changed kernel
 # reports null until it is captured again.
-NCU_TRAFFIC: dict[str, dict] = {}
+NCU_TRAFFIC: dict[str, dict] = {
+    "agent_tiled_k16": {"source_hash": "7bc97511c34927ca", "captured_bytes": 167853312 + 122396416,
+                        "scale": 4, "bytes_per_launch": 4 * (167853312 + 122396416)},
+    "grid_k1": {"source_hash": "abef33d2fb2bfdd1", "captured_bytes": 268510720 + 219353344,
+                "scale": 8, "bytes_per_launch": 8 * (268510720 + 219353344)},
+}
 
 
 def traffic_for(kernel: str):
@@ -554,14 +559,17 @@ def run_serve_vs_batch(args, NS, stream, rows):
     roads = [WL.road_params(r) for r in rows]
     steps = [r["T"] for r in rows]
     work = sum(r["N"] * r["T"] for r in rows)
+    t0 = time.perf_counter()
     with NS.Batch(roads, steps, stream=stream) as b:
         b.wait()
         batched_s = b.info().run_seconds
+    batched_wall = time.perf_counter() - t0          # start states included, as for the served requests
     out = SV.run_poisson(rows, rate=float("inf"), memory_budget=args.serve_budget_gb << 30,
                          steps_per_tick=args.serve_steps_per_tick, time_limit_s=args.serve_time_limit,
                          stream_series=True)
     served = out["vehicle_updates_per_s"]
     return {"requests": len(rows), "vehicle_updates": work, "batched_vehicle_updates_per_s": work / batched_s,
+            "batched_with_start_states_vehicle_updates_per_s": work / batched_wall,
             "served_vehicle_updates_per_s": served, "served_over_batched": served / (work / batched_s),
             "served_gpu_busy_fraction": out["gpu_busy_fraction"], "served_span_s": out["span_s"],
             "ticks": out["ticks"], "streamed_steps": out["streamed_steps"],

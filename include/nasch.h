@@ -372,6 +372,29 @@ int nasch_server_get_info(nasch_server s, nasch_server_info *info);
 /* Wait for all work, then free the server.  NULL is a no-op. */
 void nasch_server_destroy(nasch_server s);
 
+/* One rank's share of a ring road split into contiguous cell ranges (the
+ * grid layout's 1-D domain decomposition; the paper's "Variations":
+ * distributed memory).  The rank owns the `owned` cells first_cell ..
+ * first_cell + owned - 1 (mod L) and holds them with `halo` cells on each
+ * side: seg_in_dev[i] (caller-owned device memory, int8 cells, -1 empty) is
+ * ring cell first_cell - halo + i (mod L) at global step step0, for i <
+ * owned + 2 * halo.  Enqueues k steps (rules 1-4, the rule-3 draw keyed by
+ * the ring cell as for the whole road) on `stream` (a cudaStream_t, NULL
+ * for the default stream) and writes the owned cells at step step0 + k to
+ * seg_out_dev[halo .. halo + owned - 1]; the halo parts of seg_out_dev are
+ * not written (refresh both halos from the ring neighbours before the next
+ * call).  Per step s < k, adds to sum_v_dev[s] and crossings_dev[s]
+ * (caller-owned device uint64 arrays, zeroed by the caller) the velocities
+ * and the crossings of the cars whose cell at the start of the step is
+ * owned, so the ranks' series add up to the whole road's.  Cell j at step
+ * t+1 depends only on cells j - vmax .. j + vmax at step t, so the result
+ * is exact when k * vmax <= halo.  Requires: halo a multiple of 16 with
+ * k * vmax <= halo <= 512; 1 <= k <= 64; 1 <= owned <= L; both buffers
+ * 16-byte aligned and not overlapping; anything else is NASCH_EINVAL. */
+int nasch_segment_run(const int8_t *seg_in_dev, int8_t *seg_out_dev, int64_t owned, int32_t halo,
+                      int64_t first_cell, int64_t L, int32_t vmax, double p, uint64_t seed, uint32_t road_id,
+                      uint64_t step0, int32_t k, uint64_t *sum_v_dev, uint64_t *crossings_dev, void *stream);
+
 /* Start positions of one road, computed on the GPU without allocating any
  * device memory.  The paper has no counterpart: this entry point exists for
  * callers that cannot allocate device memory - a process whose device memory

@@ -8,7 +8,9 @@
 //   2. admits queued requests, oldest first, while their state and
 //      statistics fit the device-memory budget (a first-fit allocator over
 //      one slab of that size) and a slot is free; new roads get their Floyd
-//      start on the GPU;
+//      start on the GPU, on a stream of their own, so that it overlaps the
+//      running ticks; a road joins the ticks once the host has seen its
+//      initialisation finish;
 //   3. enqueues one tick: M launches of the super-step kernel over the items
 //      of every resident road, each road continuing from its own super-step,
 //      so a request admitted now runs in the same launches as requests
@@ -112,6 +114,7 @@ struct Request {
     int64_t last_tick = -1;   // sequence number of the last tick that ran it
     bool canceled = false;
     bool retired = false;     // results copied back, device memory released
+    bool initialised = false; // its start state is on the device (initialisation observed finished)
     int status = NASCH_OK;
     double submit_t = 0, admit_t = 0, done_t = 0;
     std::vector<uint64_t> sum_v, crossings;
@@ -127,8 +130,6 @@ struct Request {
 // Host staging of one tick in flight; reused only after that tick finished.
 struct TickBuf {
     BatchRoadDev *h_slots = nullptr;     // pinned: slot descriptors
-    BatchRoadDev *h_new = nullptr;       // pinned: descriptors of roads initialised this round
-    uint64_t **h_new_bm = nullptr;       // pinned: their Floyd bit maps
     BatchItem *h_items = nullptr;        // pinned: work-list
     BatchItem *d_items = nullptr;        // device work-list
     uint32_t *d_counters = nullptr;      // device work-list cursors, one per launch
@@ -143,6 +144,18 @@ struct Tick {
 
 constexpr int kMaxTicksInFlight = 4;
 
+// One admission round's initialisation (Floyd start states), run on a
+// stream of its own so that it overlaps the ticks of the roads already
+// running; its staging buffers are reused only after its event completed.
+struct InitRound {
+    BatchRoadDev *h_new = nullptr, *d_new = nullptr;   // descriptors of the round's roads
+    uint64_t **h_bm = nullptr, **d_bm = nullptr;       // their Floyd bit maps
+    cudaEvent_t ev = nullptr;
+    bool busy = false;
+    std::vector<Request *> reqs;
+};
+constexpr int kInitRounds = 4;
+
 }  // namespace
 }  // namespace nasch
 
@@ -153,6 +166,7 @@ struct nasch_server_s {
     int device = 0, sms = 1;
     cudaStream_t stream = nullptr;
     cudaStream_t copy_stream = nullptr;  // reads of finished series
+    cudaStream_t init_stream = nullptr;  // start states of admitted roads
     bool own_stream = false;
     double rho_star = 0.2;
     int k_agent = 8, k_grid = 8;
@@ -161,8 +175,7 @@ struct nasch_server_s {
     int max_slots = 0;
     std::vector<int> free_slots;
     BatchRoadDev *d_slots = nullptr;
-    BatchRoadDev *d_new = nullptr;       // descriptors of roads initialised this round
-    uint64_t **d_new_bm = nullptr;
+    InitRound init[kInitRounds];
     TickBuf bufs[kMaxTicksInFlight];
     int depth = 2;                       // ticks in flight
     int64_t items_cap = 0;
@@ -210,8 +223,6 @@ void free_tick_buf(TickBuf &b)
     cudaFree(b.d_counters);
     if (b.h_items) cudaFreeHost(b.h_items);
     if (b.h_slots) cudaFreeHost(b.h_slots);
-    if (b.h_new) cudaFreeHost(b.h_new);
-    if (b.h_new_bm) cudaFreeHost(b.h_new_bm);
     b = TickBuf{};
 }
 
@@ -220,6 +231,7 @@ void destroy_server(nasch_server s)
     if (!s) return;
     if (s->stream) cudaStreamSynchronize(s->stream);
     if (s->copy_stream) cudaStreamSynchronize(s->copy_stream);
+    if (s->init_stream) cudaStreamSynchronize(s->init_stream);
     for (auto &t : s->inflight) {
         cudaEventDestroy(t.ev0);
         cudaEventDestroy(t.ev);
@@ -230,13 +242,19 @@ void destroy_server(nasch_server s)
     }
     cudaFree(s->slab);
     cudaFree(s->d_slots);
-    cudaFree(s->d_new);
-    cudaFree(s->d_new_bm);
+    for (auto &ir : s->init) {
+        if (ir.h_new) cudaFreeHost(ir.h_new);
+        if (ir.h_bm) cudaFreeHost(ir.h_bm);
+        cudaFree(ir.d_new);
+        cudaFree(ir.d_bm);
+        if (ir.ev) cudaEventDestroy(ir.ev);
+    }
     for (auto &b : s->bufs) free_tick_buf(b);
     if (s->h_cancel) cudaFreeHost(s->h_cancel);
     // every request not yet released (queued, resident or finished) is in by_id
     for (auto &kv : s->by_id) delete kv.second;
     if (s->copy_stream) cudaStreamDestroy(s->copy_stream);
+    if (s->init_stream) cudaStreamDestroy(s->init_stream);
     if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
     delete s;
 }
@@ -247,8 +265,8 @@ int retire(nasch_server s, Request *r)
     cudaError_t e = cudaSuccess;
     // a request that ran no tick (no steps, or no cars) retires in the round
     // that admitted it: its zeroed series and its start state were written by
-    // work on the server's stream that no finished tick covers yet
-    if (r->super == 0 && !r->canceled) e = cudaStreamSynchronize(s->stream);
+    // initialisation work that may still be running
+    if (r->super == 0 && !r->canceled) e = cudaStreamSynchronize(s->init_stream);
     if (e == cudaSuccess && !r->canceled && r->T > 0) {
         r->sum_v.resize((size_t)r->T);
         r->crossings.resize((size_t)r->T);
@@ -291,8 +309,8 @@ int retire(nasch_server s, Request *r)
     return NASCH_OK;
 }
 
-// Retire resident requests that are finished or cancelled and that no
-// unfinished tick still runs.
+// Retire resident requests that are finished or cancelled, whose
+// initialisation has finished and that no unfinished tick still runs.
 int retire_ready(nasch_server s)
 {
     std::vector<Request *> keep;
@@ -300,7 +318,7 @@ int retire_ready(nasch_server s)
     int st = NASCH_OK;
     for (auto *r : s->resident) {
         const bool over = r->canceled || r->done_super >= r->super;
-        if (over && r->last_tick <= s->harvested_seq && st == NASCH_OK)
+        if (over && r->initialised && r->last_tick <= s->harvested_seq && st == NASCH_OK)
             st = retire(s, r);
         else
             keep.push_back(r);
@@ -369,11 +387,33 @@ int ensure_items(nasch_server s, int64_t need)
     return NASCH_OK;
 }
 
-// Admit queued requests (oldest first) while memory and slots allow, and
-// enqueue their initial state.
-int admit(nasch_server s, TickBuf &buf, bool *staged)
+// Initialisation rounds whose work has finished: their roads may run.
+int poll_init(nasch_server s)
 {
-    *staged = false;
+    for (auto &ir : s->init) {
+        if (!ir.busy) continue;
+        const cudaError_t q = cudaEventQuery(ir.ev);
+        if (q == cudaErrorNotReady) continue;
+        if (q != cudaSuccess) return cuda_fail(q, "initialisation");
+        for (auto *r : ir.reqs) r->initialised = true;
+        ir.reqs.clear();
+        ir.busy = false;
+    }
+    return NASCH_OK;
+}
+
+// Admit queued requests (oldest first) while memory and slots allow, and
+// enqueue their initial state on the initialisation stream (one round; none
+// while every round's staging is still in use).
+int admit(nasch_server s)
+{
+    InitRound *round = nullptr;
+    for (auto &ir : s->init)
+        if (!ir.busy) {
+            round = &ir;
+            break;
+        }
+    if (!round) return NASCH_OK;
     std::vector<Request *> fresh;
     while (!s->queue.empty()) {
         Request *r = s->queue.front();
@@ -425,33 +465,41 @@ int admit(nasch_server s, TickBuf &buf, bool *staged)
         const size_t ss = align256((size_t)std::max<int64_t>(r->T, 1) * 8);
         r->rd.sum_v = reinterpret_cast<unsigned long long *>(base + o);
         r->rd.crossings = reinterpret_cast<unsigned long long *>(base + o + ss);
-        cudaError_t e = cudaMemsetAsync(base + o, 0, 2 * ss, s->stream);
-        if (e == cudaSuccess && r->layout == NASCH_LAYOUT_AGENT) e = cudaMemsetAsync(r->rd.v[0], 0, n, s->stream);
+        const cudaStream_t is = s->init_stream;
+        cudaError_t e = cudaMemsetAsync(base + o, 0, 2 * ss, is);
+        if (e == cudaSuccess && r->layout == NASCH_LAYOUT_AGENT) e = cudaMemsetAsync(r->rd.v[0], 0, n, is);
         if (e == cudaSuccess && r->layout == NASCH_LAYOUT_GRID)
-            e = cudaMemsetAsync(r->rd.cells[0], 0xFF, (size_t)r->rd.L, s->stream);
+            e = cudaMemsetAsync(r->rd.cells[0], 0xFF, (size_t)r->rd.L, is);
         if (e == cudaSuccess && r->rd.N > 0)
-            e = cudaMemsetAsync(static_cast<char *>(s->slab) + bm_off, 0, bm_bytes, s->stream);
+            e = cudaMemsetAsync(static_cast<char *>(s->slab) + bm_off, 0, bm_bytes, is);
         if (e != cudaSuccess) return cuda_fail(e, "admit request");
         s->resident.push_back(r);
         s->streaming.push_back(r);
-        if (r->rd.N > 0) fresh.push_back(r);
+        if (r->rd.N > 0)
+            fresh.push_back(r);
+        else
+            r->initialised = true;   // nothing to place (and nothing to run)
         if (r->super == 0) r->last_tick = s->harvested_seq;   // nothing to run (no steps or no cars): retire at once
     }
     if (!fresh.empty()) {
+        InitRound &ir = *round;
         for (size_t i = 0; i < fresh.size(); ++i) {
-            buf.h_new[i] = fresh[i]->rd;
-            buf.h_new_bm[i] = reinterpret_cast<uint64_t *>(static_cast<char *>(s->slab) + fresh[i]->bm_off);
+            ir.h_new[i] = fresh[i]->rd;
+            ir.h_bm[i] = reinterpret_cast<uint64_t *>(static_cast<char *>(s->slab) + fresh[i]->bm_off);
         }
-        cudaError_t e = cudaMemcpyAsync(s->d_new, buf.h_new, fresh.size() * sizeof(BatchRoadDev),
-                                        cudaMemcpyHostToDevice, s->stream);
+        const cudaStream_t is = s->init_stream;
+        cudaError_t e = cudaMemcpyAsync(ir.d_new, ir.h_new, fresh.size() * sizeof(BatchRoadDev), cudaMemcpyHostToDevice, is);
         if (e == cudaSuccess)
-            e = cudaMemcpyAsync(s->d_new_bm, buf.h_new_bm, fresh.size() * sizeof(uint64_t *),
-                                cudaMemcpyHostToDevice, s->stream);
-        *staged = true;
-        if (e == cudaSuccess) e = launch_batch_floyd(s->d_new, (uint32_t)fresh.size(), s->d_new_bm, s->sms, s->stream);
+            e = cudaMemcpyAsync(ir.d_bm, ir.h_bm, fresh.size() * sizeof(uint64_t *), cudaMemcpyHostToDevice, is);
+        if (e == cudaSuccess) e = launch_batch_floyd(ir.d_new, (uint32_t)fresh.size(), ir.d_bm, s->sms, is);
+        if (e == cudaSuccess) e = cudaEventRecord(ir.ev, is);
         if (e != cudaSuccess) return cuda_fail(e, "initialise admitted roads");
-        // the bit maps were only needed by the initialisation, which the stream
-        // orders before any later use of that memory
+        ir.reqs = fresh;
+        ir.busy = true;
+        // the bit maps were only needed by the initialisation; memory given
+        // out again is first touched by later work on the same stream
+        // (admission clears it there), or by ticks of roads whose own
+        // initialisation the host has seen finish
         for (auto *r : fresh) {
             s->alloc.release(r->bm_off, r->bm_bytes);
             r->bm_bytes = 0;
@@ -480,7 +528,7 @@ int enqueue_tick(nasch_server s, TickBuf &buf)
 {
     std::vector<Request *> act;
     for (auto *r : s->resident)
-        if (!r->canceled && r->done_super < r->super) act.push_back(r);
+        if (!r->canceled && r->initialised && r->done_super < r->super) act.push_back(r);
     if (act.empty()) return NASCH_OK;
     std::stable_sort(act.begin(), act.end(), [](const Request *a, const Request *b) {
         return a->super - a->done_super > b->super - b->done_super;
@@ -562,11 +610,20 @@ int alloc_tick_buf(nasch_server s, TickBuf &b)
 {
     const size_t n = (size_t)s->max_slots;
     cudaError_t e = cudaHostAlloc((void **)&b.h_slots, sizeof(BatchRoadDev) * n, 0);
-    if (e == cudaSuccess) e = cudaHostAlloc((void **)&b.h_new, sizeof(BatchRoadDev) * n, 0);
-    if (e == cudaSuccess) e = cudaHostAlloc((void **)&b.h_new_bm, sizeof(uint64_t *) * n, 0);
     if (e == cudaSuccess)
         e = cudaMalloc(&b.d_counters, sizeof(uint32_t) * (size_t)std::max(s->cfg.max_steps_per_tick, s->cfg.steps_per_tick));
     return e == cudaSuccess ? NASCH_OK : cuda_fail(e, "tick staging buffers");
+}
+
+int alloc_init_round(nasch_server s, InitRound &ir)
+{
+    const size_t n = (size_t)s->max_slots;
+    cudaError_t e = cudaHostAlloc((void **)&ir.h_new, sizeof(BatchRoadDev) * n, 0);
+    if (e == cudaSuccess) e = cudaHostAlloc((void **)&ir.h_bm, sizeof(uint64_t *) * n, 0);
+    if (e == cudaSuccess) e = cudaMalloc(&ir.d_new, sizeof(BatchRoadDev) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&ir.d_bm, sizeof(uint64_t *) * n);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ir.ev, cudaEventDisableTiming);
+    return e == cudaSuccess ? NASCH_OK : cuda_fail(e, "initialisation staging buffers");
 }
 
 }  // namespace
@@ -625,10 +682,9 @@ int nasch_server_create(const nasch_server_config *cfg, nasch_server *out)
     s->max_slots = cfg->max_resident;
     s->padded = (uint32_t)kGridSpan;
     e = cudaStreamCreateWithFlags(&s->copy_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->init_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMalloc(&s->slab, (size_t)cfg->memory_budget);
     if (e == cudaSuccess) e = cudaMalloc(&s->d_slots, sizeof(BatchRoadDev) * (size_t)s->max_slots);
-    if (e == cudaSuccess) e = cudaMalloc(&s->d_new, sizeof(BatchRoadDev) * (size_t)s->max_slots);
-    if (e == cudaSuccess) e = cudaMalloc(&s->d_new_bm, sizeof(uint64_t *) * (size_t)s->max_slots);
     if (e == cudaSuccess) e = cudaHostAlloc((void **)&s->h_cancel, sizeof(uint32_t), cudaHostAllocMapped);
     if (e == cudaSuccess) {
         *s->h_cancel = 0;
@@ -642,6 +698,11 @@ int nasch_server_create(const nasch_server_config *cfg, nasch_server *out)
     }
     for (int i = 0; i < s->depth; ++i)
         if ((st = alloc_tick_buf(s, s->bufs[i]))) {
+            destroy_server(s);
+            return st;
+        }
+    for (auto &ir : s->init)
+        if ((st = alloc_init_round(s, ir))) {
             destroy_server(s);
             return st;
         }
@@ -697,18 +758,13 @@ int nasch_server_step(nasch_server s, int64_t *pending)
         if (st) return st;
     }
     TickBuf &buf = s->bufs[s->tick_seq % s->depth];
-    bool staged = false;
-    const int64_t seq_before = s->tick_seq;
-    st = admit(s, buf, &staged);
+    st = poll_init(s);
+    if (st == NASCH_OK) st = retire_ready(s);   // roads with nothing to run, now initialised
+    if (st) return st;
+    st = admit(s);
     if (st) return st;
     st = enqueue_tick(s, buf);
     if (st) return st;
-    if (staged && s->tick_seq == seq_before) {
-        // no tick took this staging buffer, so the next round reuses it: let
-        // its copies run first
-        const cudaError_t e = cudaStreamSynchronize(s->stream);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
-    }
     if (s->inflight.empty() && !s->resident.empty()) st = retire_ready(s);
     if (pending) *pending = (int64_t)(s->queue.size() + s->resident.size());
     return st;

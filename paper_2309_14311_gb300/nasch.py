@@ -119,6 +119,7 @@ def _declare(lib) -> None:
         "nasch_batch_destroy": (None, [H]),
         "nasch_set_tuning": (ctypes.c_int, [dbl, i32, i32]),
         "nasch_server_poll_series": (ctypes.c_int, [H, P, i64, P, P, i64, P]),
+        "nasch_segment_run": (ctypes.c_int, [P, P, i64, i32, i64, i64, i32, dbl, u64, u32, u64, i32, P, P, P]),
         "nasch_floyd_init_device_noalloc": (ctypes.c_int, [i64, i64, u64, u32, P, P]),
         "nasch_selftest_bounded_wait": (ctypes.c_int, [i64, P]),
         "nasch_server_config_init": (None, [P]),
@@ -173,6 +174,15 @@ def floyd_init_device_noalloc(L: int, N: int, seed: int, road: int, x_dev_ptr: i
     `stream`.  Roads of at most 2^24 cells."""
     _check(load().nasch_floyd_init_device_noalloc(int(L), int(N), int(seed), int(road), ctypes.c_void_p(x_dev_ptr),
                                                   _stream_handle(stream)))
+
+
+def segment_run(in_ptr: int, out_ptr: int, owned: int, halo: int, first_cell: int, L: int, vmax: int, p: float,
+                seed: int, road_id: int, step0: int, k: int, sum_v_ptr: int, crossings_ptr: int, stream=None) -> None:
+    """nasch_segment_run on caller-owned device buffers (raw pointers)."""
+    _check(load().nasch_segment_run(ctypes.c_void_p(in_ptr), ctypes.c_void_p(out_ptr), int(owned), int(halo),
+                                    int(first_cell), int(L), int(vmax), float(p), int(seed), int(road_id),
+                                    int(step0), int(k), ctypes.c_void_p(sum_v_ptr), ctypes.c_void_p(crossings_ptr),
+                                    _stream_handle(stream)))
 
 
 def selftest_bounded_wait(limit_ms: int = 50):
