@@ -268,6 +268,42 @@ void nasch_batch_destroy(nasch_batch b);
 int nasch_set_tuning(double rho_star, int32_t k_agent, int32_t k_grid);
 int nasch_get_tuning(double *rho_star, int32_t *k_agent, int32_t *k_grid);
 
+/* Per-road tuning of batched and served roads (process-wide; the
+ * autotuner fills it from timings of each bucket of roads).  An entry
+ * matches a road with L_min <= L < L_max, rho_min <= N / L < rho_max,
+ * vmax_min <= vmax <= vmax_max and the draw mode `draw` (-1 any p; 0: p = 0;
+ * 1: 0 < p < 1; 2: p = 1); the first matching entry decides, for the
+ * choices the road leaves to the library: the layout of an AUTO road
+ * (NASCH_LAYOUT_AGENT or _GRID; AUTO keeps the density rule), the fusion
+ * depth of a road with k = 0 (0 keeps the default), and the tile of a grid
+ * road with tile = 0 (2048: warp-tiles of the list method; 8192: block-wide
+ * spans; 0 keeps the default).  A road no entry matches uses the global
+ * tuning above.  A batch whose AUTO roads would need more than half of the
+ * free device memory ignores the table's layouts and uses the state-byte
+ * crossover.  The choice never changes a road's result, only its speed. */
+typedef struct nasch_tuning_entry {
+    int64_t L_min, L_max;
+    double rho_min, rho_max;
+    int32_t vmax_min, vmax_max;
+    int32_t draw;
+    int32_t layout;
+    int32_t k;
+    int32_t tile;
+} nasch_tuning_entry;
+
+/* Replace the table by entries[0..n-1] (n = 0 clears it); NASCH_EINVAL for
+ * an entry out of range (empty ranges, k outside 0..64, an unknown layout
+ * or tile), leaving the table as it was. */
+int nasch_set_tuning_table(const nasch_tuning_entry *entries, int64_t n);
+/* Copy up to cap entries to out; *n receives the table's length. */
+int nasch_get_tuning_table(nasch_tuning_entry *out, int64_t cap, int64_t *n);
+/* The layout (NASCH_LAYOUT_AGENT or _GRID), fusion depth and tile a batch
+ * would give `road` from the tuning above and the table, memory permitting
+ * (host arithmetic only; needs no GPU).  tile: 2048 or 8192 for grid roads
+ * on tiles, 256 for agent roads on warp-tiles, 0 for roads stepped as a
+ * whole ring in one item. */
+int nasch_tuned_choice(const nasch_params *road, int32_t *layout, int32_t *k, int32_t *tile);
+
 /* ------------------------------------------------------------------------
  * Serving: a request loop with continuous batching.  Requests (one road
  * each, the paper's parameter set plus a step count) queue in arrival order;

@@ -11,6 +11,12 @@ ABI on this GPU:
 
 Results go to nasch_set_tuning() and to a JSON cache keyed by the GPU name
 and the library build, so later processes reuse them without re-timing.
+
+Per-road tuning of batches and servers (tune_buckets): roads are put in
+buckets by L (decades), density (three bands) and vmax; for each bucket the
+layout, the fusion depth k and the grid tile (warp-tiles or block-wide
+spans) that ran a batch of the bucket's representative roads fastest go into
+a table (nasch_set_tuning_table) that the batch planner consults per road.
 """
 from __future__ import annotations
 
@@ -117,4 +123,97 @@ def load_or_tune(force: bool = False, verbose: bool = False) -> dict:
         with open(CACHE, "w") as f:
             json.dump(cache, f, indent=1)
     apply(cache[key])
+    return cache[key]
+
+
+# --------------------------------------------------------------------------- per-road tuning of batches
+# Buckets of roads: decades of L over the uneven ensemble's range, three
+# density bands and the ensemble's maximum velocities.  Each bucket gets the
+# layout, fusion depth and (grid) tile that ran its representative batch
+# fastest; the table goes to nasch_set_tuning_table, which batches and
+# servers consult per road.
+L_EDGES = (1_000, 10_000, 100_000, 1_000_000, 10_000_001)
+RHO_EDGES = (0.0, 0.2, 0.4, 1.0001)
+VMAX_SET = (3, 5, 8)
+BUCKET_CANDIDATES = ([("agent", k, 0) for k in (4, 8, 16)] +
+                     [("grid", k, t) for k in (4, 8, 16) for t in (0, 8192)])
+BUCKET_CACHE = os.path.join(_build.BUILD, "autotune_buckets.json")
+
+
+def buckets():
+    """Every (L, density, vmax) bucket: dicts with L_min, L_max, rho_min,
+    rho_max, vmax."""
+    out = []
+    for i in range(len(L_EDGES) - 1):
+        for j in range(len(RHO_EDGES) - 1):
+            for v in VMAX_SET:
+                out.append(dict(L_min=L_EDGES[i], L_max=L_EDGES[i + 1], rho_min=RHO_EDGES[j],
+                                rho_max=RHO_EDGES[j + 1], vmax=v))
+    return out
+
+
+def representative_roads(b: dict, cells: int = 1 << 24, p: float = 0.25) -> list[dict]:
+    """Roads at the bucket's middle (geometric in L), enough of them to hold
+    about `cells` cells (at most 512)."""
+    L = int(round((b["L_min"] * min(b["L_max"], 10**7)) ** 0.5))
+    rho = 0.5 * (b["rho_min"] + min(b["rho_max"], 1.0))
+    N = max(1, min(L, int(round(rho * L))))
+    n = max(1, min(512, cells // L))
+    return [dict(L=L, N=N, vmax=b["vmax"], p=p, seed=1, road_id=i) for i in range(n)]
+
+
+def time_batch(roads: list[dict], steps: int, stream=None) -> float:
+    """Vehicle-updates/s of one batched job (GPU time after the start states)."""
+    with NS.Batch(roads, [steps] * len(roads), stream=stream) as b:
+        b.wait()
+        sec = b.info().run_seconds
+    return sum(r["N"] for r in roads) * steps / sec
+
+
+def entry(b: dict, layout: str, k: int, tile: int) -> dict:
+    return dict(L_min=b["L_min"], L_max=b["L_max"], rho_min=b["rho_min"], rho_max=b["rho_max"],
+                vmax_min=b["vmax"], vmax_max=b["vmax"], draw=-1, layout=layout, k=k,
+                tile=(tile or 2048) if layout == "grid" else 0)
+
+
+def tune_buckets(bs=None, steps: int = 64, repeats: int = 2, verbose: bool = False) -> dict:
+    """Time every candidate on each bucket's representative batch; returns
+    {"entries": table, "timings": per bucket}.  The best of `repeats` runs
+    counts for each candidate."""
+    import torch
+    stream = torch.cuda.Stream()
+    table, timings = [], []
+    for b in (bs or buckets()):
+        roads = representative_roads(b)
+        rates = {}
+        for layout, k, tile in BUCKET_CANDIDATES:
+            rs = [dict(r, layout=layout, k=k, tile=tile) for r in roads]
+            rates[(layout, k, tile)] = max(time_batch(rs, steps, stream) for _ in range(repeats))
+        best = max(rates, key=rates.get)
+        table.append(entry(b, *best))
+        timings.append({"bucket": b, "roads": len(roads), "L": roads[0]["L"], "N": roads[0]["N"],
+                        "rates": {f"{l}/k{k}/t{t}": v for (l, k, t), v in rates.items()},
+                        "best": "/".join(map(str, best))})
+        if verbose:
+            print(b, best, f"{rates[best]:.3e}")
+    return {"entries": table, "timings": timings}
+
+
+def load_or_tune_buckets(force: bool = False, verbose: bool = False) -> dict:
+    """Apply the cached per-bucket table for this GPU and build, timing it
+    first if needed."""
+    key = _key()
+    cache = {}
+    if os.path.exists(BUCKET_CACHE):
+        try:
+            with open(BUCKET_CACHE) as f:
+                cache = json.load(f)
+        except Exception:
+            cache = {}
+    if force or key not in cache:
+        cache[key] = tune_buckets(verbose=verbose)
+        os.makedirs(os.path.dirname(BUCKET_CACHE), exist_ok=True)
+        with open(BUCKET_CACHE, "w") as f:
+            json.dump(cache, f, indent=1)
+    NS.set_tuning_table(cache[key]["entries"])
     return cache[key]

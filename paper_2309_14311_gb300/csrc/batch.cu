@@ -37,6 +37,7 @@ double g_rho_star = 1.0;
 constexpr double kBytesRhoStar = 0.2;   // state bytes equal: agent 10 per car, grid 2 per cell
 int g_k_agent = 8;
 int g_k_grid = 8;
+std::vector<nasch_tuning_entry> g_table;   // per-road tuning, first match wins
 constexpr int kRingK = 8;   // steps per item of whole-ring roads
 constexpr int64_t kGraphChunk = 2048;   // super-steps per captured graph
 
@@ -65,22 +66,74 @@ double auto_rho_star(const nasch_params *roads, int64_t n)
     return bytes <= 0.5 * (double)free_b ? rho : kBytesRhoStar;
 }
 
-void get_tuning_values(double *rho_star, int *k_agent, int *k_grid)
+TuningSnapshot tuning_snapshot()
 {
     std::lock_guard<std::mutex> g(g_tuning_mu);
-    *rho_star = g_rho_star;
-    *k_agent = g_k_agent;
-    *k_grid = g_k_grid;
+    TuningSnapshot ts;
+    ts.rho_star = g_rho_star;
+    ts.k_agent = g_k_agent;
+    ts.k_grid = g_k_grid;
+    ts.table = g_table;
+    return ts;
 }
 
-void plan_road(const nasch_params &p, int64_t T, double rho_star, int k_agent, int k_grid, BatchRoadDev *out,
+namespace {
+
+// rule-3 draw mode of a road as the table keys it: 0 never, 1 draws, 2 always
+int draw_key(double p)
+{
+    const uint64_t thr = slow_threshold(p);
+    return thr == 0 ? 0 : (thr > 0xFFFFFFFFull ? 2 : 1);
+}
+
+const nasch_tuning_entry *match_entry(const TuningSnapshot &ts, const nasch_params &p)
+{
+    if (ts.table.empty()) return nullptr;
+    const double rho = (double)p.N / (double)p.L;
+    const int dk = draw_key(p.p);
+    for (const auto &e : ts.table)
+        if (p.L >= e.L_min && p.L < e.L_max && rho >= e.rho_min && rho < e.rho_max && p.vmax >= e.vmax_min &&
+            p.vmax <= e.vmax_max && (e.draw < 0 || e.draw == dk))
+            return &e;
+    return nullptr;
+}
+
+int resolve_layout(const nasch_params &p, const TuningSnapshot &ts, bool memory_short, const nasch_tuning_entry *e)
+{
+    if (p.layout != NASCH_LAYOUT_AUTO) return p.layout;
+    if (!memory_short && e && e->layout != NASCH_LAYOUT_AUTO) return e->layout;
+    const double rho_star = memory_short ? kBytesRhoStar : ts.rho_star;
+    return (double)p.N < rho_star * (double)p.L ? NASCH_LAYOUT_AGENT : NASCH_LAYOUT_GRID;
+}
+
+}  // namespace
+
+bool auto_memory_short(const nasch_params *roads, int64_t n, const TuningSnapshot &ts)
+{
+    double bytes = 0.0;   // state of the AUTO roads as chosen (two buffers each)
+    for (int64_t i = 0; i < n; ++i) {
+        if (roads[i].layout != NASCH_LAYOUT_AUTO) continue;
+        const int lay = resolve_layout(roads[i], ts, false, match_entry(ts, roads[i]));
+        bytes += lay == NASCH_LAYOUT_AGENT ? 10.0 * (double)roads[i].N : 2.0 * (double)roads[i].L;
+    }
+    if (bytes == 0.0) return false;
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+        cudaGetLastError();
+        return true;
+    }
+    return bytes > 0.5 * (double)free_b;
+}
+
+void plan_road(const nasch_params &p, int64_t T, const TuningSnapshot &ts, bool memory_short, BatchRoadDev *out,
                int *layout_out, int64_t *n_items, int64_t *super)
 {
     BatchRoadDev &rd = *out;
     std::memset(&rd, 0, sizeof(rd));
-    int layout = p.layout;
-    if (layout == NASCH_LAYOUT_AUTO) layout = (double)p.N < rho_star * (double)p.L ? NASCH_LAYOUT_AGENT : NASCH_LAYOUT_GRID;
+    const nasch_tuning_entry *e = match_entry(ts, p);
+    const int layout = resolve_layout(p, ts, memory_short, e);
     *layout_out = layout;
+    const int k_tuned = e && e->k > 0 ? e->k : 0;
     rd.L = (uint32_t)p.L;
     rd.N = (uint32_t)p.N;
     rd.vmax = (uint32_t)p.vmax;
@@ -93,11 +146,11 @@ void plan_road(const nasch_params &p, int64_t T, double rho_star, int k_agent, i
     if (layout == NASCH_LAYOUT_AGENT) {
         if (p.N <= (int64_t)kBatchRingCars) {
             rd.type = kBatchAgentRing;
-            k = p.k ? p.k : kRingK;
+            k = p.k ? p.k : (k_tuned ? k_tuned : kRingK);
             *n_items = 1;
         } else {
             rd.type = kBatchAgentTile;
-            k = p.k ? p.k : k_agent;
+            k = p.k ? p.k : (k_tuned ? k_tuned : ts.k_agent);
             rd.halo = round_up((uint32_t)k, (uint32_t)kBatchAgentR);
             rd.tile = kBatchAgentSpan - rd.halo;
             const int64_t per_item = (int64_t)rd.tile * (kBatchThreads / 32) * kBatchWarpTilesPerWarp;
@@ -106,14 +159,16 @@ void plan_road(const nasch_params &p, int64_t T, double rho_star, int k_agent, i
     } else {
         if (p.L <= (int64_t)kBatchRingCells) {
             rd.type = kBatchGridRing;
-            k = p.k ? p.k : kRingK;
+            k = p.k ? p.k : (k_tuned ? k_tuned : kRingK);
             *n_items = 1;
         } else {
-            k = p.k ? p.k : k_grid;
+            k = p.k ? p.k : (k_tuned ? k_tuned : ts.k_grid);
             const int kfit = p.vmax > 0 ? std::max(1, (kGridSpan / 2 - 16) / p.vmax) : kMaxFusedSteps;
             k = std::min(k, kfit);
             rd.halo = grid_halo(k, (uint32_t)p.vmax);
-            if (rd.halo <= kKwMaxHalo) {   // warp-tiles of the list method
+            // tile: the road's own (8192 = block-wide spans), else the table's
+            const int tile = p.tile ? p.tile : (e ? e->tile : 0);
+            if (rd.halo <= kKwMaxHalo && tile != kGridTileCells) {   // warp-tiles of the list method
                 rd.type = kBatchGridWarp;
                 rd.tile = kKwSpan - 2u * rd.halo;
                 const int64_t per_item = (int64_t)rd.tile * (kBatchThreads / 32);
@@ -227,6 +282,59 @@ int nasch_set_tuning(double rho_star, int32_t k_agent, int32_t k_grid)
     return NASCH_OK;
 }
 
+int nasch_set_tuning_table(const nasch_tuning_entry *entries, int64_t n)
+{
+    clear_error();
+    if (n < 0 || (n > 0 && !entries)) return fail(NASCH_EINVAL, "bad table");
+    if (n > (1 << 20)) return fail(NASCH_EINVAL, "table of %lld entries too long", (long long)n);
+    for (int64_t i = 0; i < n; ++i) {
+        const nasch_tuning_entry &e = entries[i];
+        if (!(e.L_min < e.L_max) || !(e.rho_min < e.rho_max) || e.vmax_min > e.vmax_max || e.draw < -1 ||
+            e.draw > 2)
+            return fail(NASCH_EINVAL, "entry %lld: empty or unknown bucket", (long long)i);
+        if (e.layout < NASCH_LAYOUT_AUTO || e.layout > NASCH_LAYOUT_GRID)
+            return fail(NASCH_EINVAL, "entry %lld: layout=%d unknown", (long long)i, e.layout);
+        if (e.k < 0 || e.k > kMaxFusedSteps) return fail(NASCH_EINVAL, "entry %lld: k=%d outside 0..%d", (long long)i, e.k, kMaxFusedSteps);
+        if (e.tile != 0 && e.tile != (int32_t)kKwSpan && e.tile != kGridTileCells)
+            return fail(NASCH_EINVAL, "entry %lld: tile=%d not 0, %u or %d", (long long)i, e.tile, kKwSpan, kGridTileCells);
+    }
+    std::lock_guard<std::mutex> g(g_tuning_mu);
+    g_table.assign(entries, entries + n);
+    return NASCH_OK;
+}
+
+int nasch_get_tuning_table(nasch_tuning_entry *out, int64_t cap, int64_t *n)
+{
+    clear_error();
+    if (!n || cap < 0 || (cap > 0 && !out)) return fail(NASCH_EINVAL, "bad arguments");
+    std::lock_guard<std::mutex> g(g_tuning_mu);
+    *n = (int64_t)g_table.size();
+    for (int64_t i = 0; i < std::min<int64_t>(cap, *n); ++i) out[i] = g_table[(size_t)i];
+    return NASCH_OK;
+}
+
+int nasch_tuned_choice(const nasch_params *road, int32_t *layout, int32_t *k, int32_t *tile)
+{
+    clear_error();
+    int st = validate_params(road);
+    if (st) return st;
+    BatchRoadDev rd;
+    int lay = 0;
+    int64_t items = 0, super = 0;
+    plan_road(*road, 1, tuning_snapshot(), false, &rd, &lay, &items, &super);
+    if (layout) *layout = lay;
+    if (k) *k = (int32_t)rd.k;
+    if (tile) {
+        switch (rd.type) {
+        case kBatchGridWarp: *tile = (int32_t)kKwSpan; break;
+        case kBatchGridTile: *tile = kGridTileCells; break;
+        case kBatchAgentTile: *tile = (int32_t)kBatchAgentSpan; break;
+        default: *tile = 0; break;
+        }
+    }
+    return NASCH_OK;
+}
+
 int nasch_get_tuning(double *rho_star, int32_t *k_agent, int32_t *k_grid)
 {
     clear_error();
@@ -245,12 +353,6 @@ int nasch_submit(const nasch_params *roads, int64_t n_roads, const int64_t *step
     *out = nullptr;
     if (n_roads <= 0 || !roads || !steps) return fail(NASCH_EINVAL, "no roads");
     if (n_roads > (int64_t)0x7FFFFFFF) return fail(NASCH_EINVAL, "too many roads");
-    int k_agent, k_grid;
-    {
-        std::lock_guard<std::mutex> g(g_tuning_mu);
-        k_agent = g_k_agent;
-        k_grid = g_k_grid;
-    }
     for (int64_t i = 0; i < n_roads; ++i) {
         int st = validate_params(&roads[i]);
         if (st) return fail(st, "road %lld: %s", (long long)i, nasch_last_error());
@@ -278,7 +380,8 @@ int nasch_submit(const nasch_params *roads, int64_t n_roads, const int64_t *step
     }
 
     // ---------------------------------------------------------------- plan
-    const double rho_star = auto_rho_star(roads, n_roads);
+    const TuningSnapshot ts = tuning_snapshot();
+    const bool memory_short = auto_memory_short(roads, n_roads, ts);
     b->roads.resize((size_t)n_roads);
     b->layout.resize((size_t)n_roads);
     b->super.resize((size_t)n_roads);
@@ -286,7 +389,7 @@ int nasch_submit(const nasch_params *roads, int64_t n_roads, const int64_t *step
     uint32_t max_vmax_grid = 0;
     for (int64_t i = 0; i < n_roads; ++i) {
         int layout = 0;
-        plan_road(roads[i], steps[i], rho_star, k_agent, k_grid, &b->roads[(size_t)i], &layout, &n_items[(size_t)i],
+        plan_road(roads[i], steps[i], ts, memory_short, &b->roads[(size_t)i], &layout, &n_items[(size_t)i],
                   &b->super[(size_t)i]);
         b->layout[(size_t)i] = layout;
         if (layout == NASCH_LAYOUT_GRID) max_vmax_grid = std::max(max_vmax_grid, (uint32_t)roads[i].vmax);

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "kernels.h"
 #include "nasch.h"
 
@@ -58,12 +60,25 @@ struct BatchLaunch {
     uint32_t padded;                   // grid buffer length (max over the batch's grid roads)
 };
 
-// Per-road plan shared by batches and the server: layout (AUTO by density),
-// item kind, fusion depth, halo/tile geometry, items per super-step and the
-// number of super-steps.  Pointers and sbase are left zero.
-void plan_road(const nasch_params &p, int64_t T, double rho_star, int k_agent, int k_grid, BatchRoadDev *rd,
+// The automatic choices in force when a batch or a server is made: the
+// global tuning and the per-road table (nasch_set_tuning_table).
+struct TuningSnapshot {
+    double rho_star = 1.0;
+    int k_agent = 8, k_grid = 8;
+    std::vector<nasch_tuning_entry> table;
+};
+TuningSnapshot tuning_snapshot();
+// True when the AUTO roads of a batch, laid out as the snapshot chooses,
+// would need more than half of the free device memory: the batch then uses
+// the state-byte crossover density and ignores the table's layouts.
+bool auto_memory_short(const nasch_params *roads, int64_t n, const TuningSnapshot &ts);
+
+// Per-road plan shared by batches and the server: layout (AUTO: the table,
+// else by density), item kind, fusion depth, halo/tile geometry, items per
+// super-step and the number of super-steps.  Pointers and sbase are left
+// zero.
+void plan_road(const nasch_params &p, int64_t T, const TuningSnapshot &ts, bool memory_short, BatchRoadDev *rd,
                int *layout, int64_t *n_items, int64_t *super);
-void get_tuning_values(double *rho_star, int *k_agent, int *k_grid);
 
 size_t batch_smem_bytes(uint32_t padded);
 int batch_blocks_per_sm(uint32_t padded);

@@ -168,8 +168,7 @@ struct nasch_server_s {
     cudaStream_t copy_stream = nullptr;  // reads of finished series
     cudaStream_t init_stream = nullptr;  // start states of admitted roads
     bool own_stream = false;
-    double rho_star = 0.2;
-    int k_agent = 8, k_grid = 8;
+    TuningSnapshot tuning;               // automatic choices in force when the server was made
     void *slab = nullptr;
     SlabAllocator alloc;
     int max_slots = 0;
@@ -662,7 +661,7 @@ int nasch_server_create(const nasch_server_config *cfg, nasch_server *out)
     if (s->cfg.max_steps_per_tick < s->cfg.steps_per_tick) s->cfg.max_steps_per_tick = s->cfg.steps_per_tick;
     s->depth = s->cfg.ticks_in_flight > 0 ? s->cfg.ticks_in_flight : 3;
     s->t0 = std::chrono::steady_clock::now();
-    get_tuning_values(&s->rho_star, &s->k_agent, &s->k_grid);
+    s->tuning = tuning_snapshot();
     int st = device_info(&s->device, &s->sms);
     if (st) {
         delete s;
@@ -733,7 +732,7 @@ int nasch_server_submit(nasch_server s, const nasch_params *road, int64_t steps,
     r->prm = *road;
     r->prm.stream = nullptr;
     r->T = steps;
-    plan_road(r->prm, steps, s->rho_star, s->k_agent, s->k_grid, &r->rd, &r->layout, &r->n_items, &r->super);
+    plan_road(r->prm, steps, s->tuning, false, &r->rd, &r->layout, &r->n_items, &r->super);
     const size_t need = request_bytes(*r) + ((size_t)r->rd.L + 63) / 64 * 8 + 512;
     if (need > (size_t)s->cfg.memory_budget) {
         delete r;

@@ -119,6 +119,9 @@ def _declare(lib) -> None:
         "nasch_batch_destroy": (None, [H]),
         "nasch_set_tuning": (ctypes.c_int, [dbl, i32, i32]),
         "nasch_server_poll_series": (ctypes.c_int, [H, P, i64, P, P, i64, P]),
+        "nasch_set_tuning_table": (ctypes.c_int, [P, i64]),
+        "nasch_get_tuning_table": (ctypes.c_int, [P, i64, P]),
+        "nasch_tuned_choice": (ctypes.c_int, [P, P, P, P]),
         "nasch_segment_run": (ctypes.c_int, [P, P, i64, i32, i64, i64, i32, dbl, u64, u32, u64, i32, P, P, P]),
         "nasch_floyd_init_device_noalloc": (ctypes.c_int, [i64, i64, u64, u32, P, P]),
         "nasch_selftest_bounded_wait": (ctypes.c_int, [i64, P]),
@@ -319,6 +322,35 @@ def get_tuning():
     return r.value, ka.value, kg.value
 
 
+def set_tuning_table(entries: list[dict]) -> None:
+    """Per-road tuning (nasch_set_tuning_table): dicts with the fields of
+    TuningEntry; layout may be given as "auto", "agent" or "grid"."""
+    arr = (TuningEntry * max(len(entries), 1))()
+    for i, e in enumerate(entries):
+        for f in TUNING_FIELDS:
+            v = e.get(f, 0)
+            if f == "layout" and isinstance(v, str):
+                v = LAYOUTS[v]
+            setattr(arr[i], f, v)
+    _check(load().nasch_set_tuning_table(arr, len(entries)))
+
+
+def get_tuning_table() -> list[dict]:
+    n = ctypes.c_int64()
+    _check(load().nasch_get_tuning_table(None, 0, ctypes.byref(n)))
+    arr = (TuningEntry * max(n.value, 1))()
+    _check(load().nasch_get_tuning_table(arr, n.value, ctypes.byref(n)))
+    return [{f: getattr(arr[i], f) for f in TUNING_FIELDS} for i in range(n.value)]
+
+
+def tuned_choice(road: dict) -> tuple[int, int, int]:
+    """(layout, k, tile) a batch would give this road (nasch_tuned_choice)."""
+    prm = make_params(**road)
+    lay, k, tile = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _check(load().nasch_tuned_choice(ctypes.byref(prm), ctypes.byref(lay), ctypes.byref(k), ctypes.byref(tile)))
+    return lay.value, k.value, tile.value
+
+
 def make_params(L, N, vmax=5, p=0.0, seed=0, road_id=0, layout="auto", k=0, tile=0, stream=None) -> Params:
     prm = Params()
     load().nasch_params_init(ctypes.byref(prm))
@@ -422,6 +454,15 @@ class ServerInfo(ctypes.Structure):
                 ("bytes_in_use", ctypes.c_int64), ("ticks", ctypes.c_int64), ("vehicle_steps_done", ctypes.c_int64),
                 ("blocks", ctypes.c_int32), ("now", ctypes.c_double), ("gpu_busy_seconds", ctypes.c_double),
                 ("last_tick_super_steps", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
+class TuningEntry(ctypes.Structure):
+    _fields_ = [("L_min", ctypes.c_int64), ("L_max", ctypes.c_int64), ("rho_min", ctypes.c_double),
+                ("rho_max", ctypes.c_double), ("vmax_min", ctypes.c_int32), ("vmax_max", ctypes.c_int32),
+                ("draw", ctypes.c_int32), ("layout", ctypes.c_int32), ("k", ctypes.c_int32), ("tile", ctypes.c_int32)]
+
+
+TUNING_FIELDS = [f for f, _ in TuningEntry._fields_]
 
 
 class SeriesChunk(ctypes.Structure):

@@ -273,3 +273,56 @@ def test_submit_rejects_bad_roads():
     assert e.value.status == NS.EINVAL
     with pytest.raises(NS.NaschError):
         NS.Batch([dict(L=100, N=20)], [-1])
+
+
+@pytest.fixture
+def clean_tuning():
+    prev_table = NS.get_tuning_table()
+    prev = NS.get_tuning()
+    yield
+    NS.set_tuning_table(prev_table)
+    NS.set_tuning(*prev)
+
+
+def test_tuned_batch_equals_untuned(clean_tuning):
+    """A per-road table that changes every AUTO road's layout, fusion depth
+    and grid tile gives the same cells and statistics as the default."""
+    rs = [_params(r) for r in MIXED]
+    steps = [r["T"] for r in MIXED]
+    with NS.Batch(rs, steps) as a:
+        a.wait()
+        want = [(a.read_grid(i), *a.stats(i)) for i in range(len(rs))]
+        lay0 = [a.layout(i) for i in range(len(rs))]
+    table = []
+    for r, lay in zip(MIXED, lay0):
+        flip = "grid" if lay == NS.LAYOUT_AGENT else "agent"
+        table.append(dict(L_min=r["L"], L_max=r["L"] + 1, rho_min=0.0, rho_max=1.01, vmax_min=r["vmax"],
+                          vmax_max=r["vmax"], draw=-1, layout=flip, k=3 + len(table) % 5, tile=8192))
+    NS.set_tuning_table(table)
+    with NS.Batch(rs, steps) as b:
+        b.wait()
+        for i, r in enumerate(MIXED):
+            if "layout" not in r:
+                assert b.layout(i) != lay0[i], i
+            g, sv, cr = want[i]
+            assert np.array_equal(b.read_grid(i), g), i
+            bsv, bcr = b.stats(i)
+            assert np.array_equal(bsv, sv) and np.array_equal(bcr, cr), i
+
+
+def test_bucket_tuning_is_no_slower_than_the_global_choice(clean_tuning):
+    """Two contrasting buckets (short dense roads with vmax 3; long sparse
+    roads with vmax 8): the tuned table runs each bucket's batch at least
+    0.9 times as fast as the global default (best of three runs each)."""
+    from paper_2309_14311_gb300 import autotune as AT
+    bs = [dict(L_min=1_000, L_max=10_000, rho_min=0.4, rho_max=1.0001, vmax=3),
+          dict(L_min=1_000_000, L_max=10_000_001, rho_min=0.0, rho_max=0.2, vmax=8)]
+    res = AT.tune_buckets(bs, steps=64, repeats=1)
+    assert len(res["entries"]) == 2
+    for b in bs:
+        roads = AT.representative_roads(b)
+        NS.set_tuning_table([])
+        base = max(AT.time_batch(roads, 64) for _ in range(3))
+        NS.set_tuning_table(res["entries"])
+        tuned = max(AT.time_batch(roads, 64) for _ in range(3))
+        assert tuned >= 0.9 * base, (b, tuned, base)
