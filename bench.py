@@ -212,6 +212,10 @@ def time_oracle(spec: WL.RoadSpec, steps_per_sample: int, samples: int, warmup: 
     NaSch steps.  Returns (vehicle-updates/s, cores, seconds timed)."""
     import numpy as np
 
+    # one thread per core, pinned (the OpenMP runtime reads these when the
+    # oracle's OpenMP build is first loaded)
+    os.environ.setdefault("OMP_PROC_BIND", "close")
+    os.environ.setdefault("OMP_PLACES", "cores")
     from oracle import oracle as O
     cores = os.cpu_count() or 1
     used = O.set_threads(cores)
@@ -231,6 +235,39 @@ def time_oracle(spec: WL.RoadSpec, steps_per_sample: int, samples: int, warmup: 
         step += steps_per_sample
     total = sum(times)
     return spec.N * steps_per_sample * samples / total, used, total, times
+
+
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part")):
+                    return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def time_oracle_serial(spec: WL.RoadSpec, steps: int):
+    """The serial oracle build on one core: `steps` NaSch steps of the full
+    ring.  Returns (vehicle-updates/s, seconds)."""
+    import numpy as np
+
+    from oracle import oracle as O
+    x = O.floyd_init(spec.L, spec.N, spec.seed, spec.road_id)
+    v = np.zeros(spec.N, np.uint8)
+    t0 = time.perf_counter()
+    O.agent_run(spec.L, x, v, spec.vmax, spec.p, spec.seed, spec.road_id, 0, steps, openmp=False)
+    sec = time.perf_counter() - t0
+    return spec.N * steps / sec, sec
 
 
 def run_reference(args):
@@ -258,7 +295,7 @@ def run_reference(args):
                    "l2_flush": "not needed: state 640 MiB > 129 MB L2"},
         "cpu_baseline": {"value": rate, "unit": "vehicle-updates/s", "cores": cores, "kind": "oracle",
                          "sample": f"full ring, {args.steps} x {args.ref_steps_per_step} NaSch steps "
-                                   f"of the {spec.N}-car road (OpenMP oracle)"},
+                                   f"of the {spec.N}-car road (OpenMP oracle)", "cpu_model": cpu_model()},
         "e2e": {"value": rate, "unit": "vehicle-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -450,14 +487,23 @@ def run_ours(args):
     serve_res = run_served(args, NS, batch_res) if (not args.no_serve and batch_res) else None
     saturated = (run_serve_vs_batch(args, NS, stream, WL.request_stream()[: args.serve_requests])
                  if not args.no_serve else None)
+    ensemble = None
+    if not args.no_ensemble:
+        ensemble = ensemble_vs_plain(NS, stream, torch, WL.uneven_ensemble(), args.plain_roads)
+        ensemble["sample"] = (f"the whole seed-7 ensemble batched; {args.plain_roads} of its roads (seed 7) run "
+                              f"one per launch")
 
     # ---------------------------------------------------------------- oracle on the host cores (rank 0, N = 1)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, cores, total, _ = time_oracle(spec, args.cpu_steps, 1, 0)
+        srate, ssec = time_oracle_serial(spec, 1)
         cpu = {"value": rate, "unit": "vehicle-updates/s", "cores": cores, "kind": "oracle",
                "sample": f"full ring of {spec.N} cars, {args.cpu_steps} NaSch steps, OpenMP oracle, "
-                         f"{total:.1f} s"}
+                         f"{total:.1f} s",
+               "cpu_model": cpu_model(), "threads": "one per core, pinned (OMP_PROC_BIND=close, OMP_PLACES=cores)",
+               "serial_1core": {"value": srate, "unit": "vehicle-updates/s", "cores": 1,
+                                "sample": f"full ring of {spec.N} cars, 1 NaSch step, serial oracle, {ssec:.1f} s"}}
 
     if rank == 0:
         line = {
@@ -489,6 +535,7 @@ def run_ours(args):
             "batched_vs_plain": batch_res,
             "served": serve_res,
             "served_saturated_vs_batched": saturated,
+            "ensemble_4096": ensemble,
             "gpu_launches": gpu_launches,
             "clocks": clocks,
             "cpu_baseline": cpu,
@@ -548,6 +595,49 @@ def run_served(args, NS, batch_res):
     out["offered_load"] = args.serve_load
     out["steps_per_tick"] = args.serve_steps_per_tick
     out["budget_bytes"] = args.serve_budget_gb << 30
+    return out
+
+
+def ensemble_vs_plain(NS, stream, torch, rows, plain_roads, seed=7):
+    """Roads of the uneven ensemble in one batched job, and a seeded subset of
+    `plain_roads` of them one after another through the single-road API
+    (plain per-road launches); GPU time only on both sides (start states
+    excluded)."""
+    import numpy as np
+    roads = [WL.road_params(r) for r in rows]
+    steps = [r["T"] for r in rows]
+    work = sum(r["N"] * r["T"] for r in rows)
+    t0 = time.perf_counter()
+    with NS.Batch(roads, steps, stream=stream) as b:
+        b.wait()
+        inf = b.info()
+        layouts = [b.layout(i) for i in range(len(rows))]
+    wall = time.perf_counter() - t0
+    out = dict(roads=len(rows), vehicle_updates=work, batched_gpu_seconds=inf.run_seconds, batched_wall_seconds=wall,
+               batched_vehicle_updates_per_s=work / inf.run_seconds, super_steps=int(inf.super_steps),
+               graphs=int(inf.graphs), device_bytes=int(inf.device_bytes),
+               agent_roads=sum(1 for x in layouts if x == NS.LAYOUT_AGENT))
+    if plain_roads <= 0:
+        return out
+    sub = list(range(len(rows)))
+    if plain_roads < len(rows):
+        rng = np.random.default_rng(seed)
+        sub = sorted(rng.choice(len(rows), plain_roads, replace=False).tolist())
+    pwork = sum(rows[i]["N"] * rows[i]["T"] for i in sub)
+    plain = 0.0
+    for i in sub:
+        r = rows[i]
+        with NS.Road(r["L"], r["N"], r["vmax"], r["p"], r["seed"], r["road_id"], stream=stream) as road:
+            road.synchronize()
+            a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            road.run(r["T"])
+            e.record(stream)
+            e.synchronize()
+            plain += a.elapsed_time(e) / 1e3
+    out.update(plain_roads=len(sub), plain_vehicle_updates=pwork, plain_gpu_seconds=plain,
+               plain_vehicle_updates_per_s=pwork / plain,
+               speedup=(work / inf.run_seconds) / (pwork / plain))
     return out
 
 
@@ -692,37 +782,17 @@ def run_workload(args):
         if args.roads < len(rows):
             rng = np.random.default_rng(2309)
             rows = [rows[i] for i in sorted(rng.choice(len(rows), args.roads, replace=False).tolist())]
-        roads = [WL.road_params(r) for r in rows]
-        steps = [r["T"] for r in rows]
-        work = sum(r["N"] * r["T"] for r in rows)
-        t0 = time.perf_counter()
-        with NS.Batch(roads, steps, stream=stream) as b:
-            b.wait()
-            inf = b.info()
-        wall = time.perf_counter() - t0
-        out.update(roads=len(rows), vehicle_updates=work, batched_gpu_seconds=inf.run_seconds,
-                   batched_wall_seconds=wall, batched_vehicle_updates_per_s=work / inf.run_seconds,
-                   super_steps=int(inf.super_steps), graphs=int(inf.graphs), device_bytes=int(inf.device_bytes))
-        # plain: the same roads one after another (a seeded subset if --plain-roads is smaller)
-        sub = list(range(len(rows)))
-        if args.plain_roads < len(rows):
-            rng = np.random.default_rng(7)
-            sub = sorted(rng.choice(len(rows), args.plain_roads, replace=False).tolist())
-        pwork = sum(rows[i]["N"] * rows[i]["T"] for i in sub)
-        plain = 0.0
-        for i in sub:
-            r = rows[i]
-            with NS.Road(r["L"], r["N"], r["vmax"], r["p"], r["seed"], r["road_id"], stream=stream) as road:
-                road.synchronize()
-                a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a.record(stream)
-                road.run(r["T"])
-                e.record(stream)
-                e.synchronize()
-                plain += a.elapsed_time(e) / 1e3
-        out.update(plain_roads=len(sub), plain_vehicle_updates=pwork, plain_gpu_seconds=plain,
-                   plain_vehicle_updates_per_s=pwork / plain,
-                   speedup=(work / inf.run_seconds) / (pwork / plain))
+        if args.autotune:
+            from paper_2309_14311_gb300 import autotune as AT
+            untuned = ensemble_vs_plain(NS, stream, torch, rows, 0)
+            t0 = time.perf_counter()
+            AT.load_or_tune_buckets()
+            out["autotune_seconds"] = time.perf_counter() - t0
+            out["untuned_batched_vehicle_updates_per_s"] = untuned["batched_vehicle_updates_per_s"]
+        out.update(ensemble_vs_plain(NS, stream, torch, rows, args.plain_roads))
+        if args.autotune:
+            out["tuned_over_untuned"] = out["batched_vehicle_updates_per_s"] / out["untuned_batched_vehicle_updates_per_s"]
+            NS.set_tuning_table([])
     elif args.workload == "fundamental-diagram":
         from paper_2309_14311_gb300 import fundamental as FD
         roads = WL.fundamental_diagram_roads(replicas=args.replicas, L=args.fd_L, vmax=args.fd_vmax)
@@ -794,6 +864,8 @@ def main(argv=None):
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--batch-roads", type=int, default=64)
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-ensemble", action="store_true", help="skip the whole-ensemble batched-vs-plain leg")
+    ap.add_argument("--autotune", action="store_true", help="ensemble workload: also per-road tuned")
     ap.add_argument("--serve-requests", type=int, default=300)
     ap.add_argument("--serve-load", type=float, default=0.7)
     ap.add_argument("--serve-budget-gb", type=int, default=40)
