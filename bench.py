@@ -191,12 +191,7 @@ def kernel_source_hash(kernel: str) -> str:
 # streaming kernels grows in proportion).  Keyed by the hash of the kernel's
 # sources (comments and layout aside) when it was captured: a changed kernel
 # reports null until it is captured again.
-NCU_TRAFFIC: dict[str, dict] = {
-    "agent_tiled_k16": {"source_hash": "7bc97511c34927ca", "captured_bytes": 167853312 + 122396416,
-                        "scale": 4, "bytes_per_launch": 4 * (167853312 + 122396416)},
-    "grid_k1": {"source_hash": "abef33d2fb2bfdd1", "captured_bytes": 268510720 + 219353344,
-                "scale": 8, "bytes_per_launch": 8 * (268510720 + 219353344)},
-}
+NCU_TRAFFIC: dict[str, dict] = {}
 
 
 def traffic_for(kernel: str):

@@ -166,4 +166,7 @@ cudaError_t launch_philox_test(const uint32_t *ctr, uint32_t k0, uint32_t k1, ui
     return cudaGetLastError();
 }
 
+// This unit's debug word (zero in release builds).
+NASCH_DEBUG_READER(debug_word_agent)
+
 }  // namespace nasch

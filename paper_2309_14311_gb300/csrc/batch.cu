@@ -260,6 +260,10 @@ int wait_batch(nasch_batch b, int64_t timeout_ms)
             std::this_thread::sleep_for(std::chrono::microseconds(50));
         }
         b->finished = true;
+#ifdef NASCH_DEBUG
+        if (const unsigned int w = debug_word_batch() | debug_word_agent() | debug_word_grid())
+            return fail(NASCH_EINVAL, "debug check failed in the batch kernels (sites 0x%x)", w);
+#endif
     }
     if (b->canceled) return fail(NASCH_ECANCELED, "batch was cancelled");
     return NASCH_OK;

@@ -384,4 +384,7 @@ cudaError_t launch_batch_floyd(const BatchRoadDev *roads, uint32_t n, uint64_t *
     return cudaGetLastError();
 }
 
+// This unit's debug word (zero in release builds).
+NASCH_DEBUG_READER(debug_word_batch)
+
 }  // namespace nasch

@@ -227,7 +227,7 @@ __device__ __forceinline__ void k1_groups(const uint16_t *list, uint32_t lane, c
             vel -= (vel != 0u && u < thr) ? 1u : 0u;                                       // rule 3
         }
         out[r] = kEmptyCell;                                                              // rule 4
-        out[r + vel] = (int8_t)vel;
+        if (NASCH_DCHECK(r + vel < kK1Buf, kDbgGridWrite)) out[r + vel] = (int8_t)vel;
         const bool mine = r - kK1Halo < own;
         tsum += mine ? vel : 0u;
         if (W) tcross += (mine && cell + vel >= L) ? 1u : 0u;
@@ -680,5 +680,8 @@ cudaError_t launch_grid_ring(const GridStep &g, cudaStream_t s)
     grid_ring_kernel<<<1, threads, smem, s>>>(g);
     return cudaGetLastError();
 }
+
+// This unit's debug word (zero in release builds).
+NASCH_DEBUG_READER(debug_word_grid)
 
 }  // namespace nasch

@@ -81,6 +81,14 @@ inline uint32_t agent_tile_owned(int k, int span)
 // Halo cells per side for the grid tile.
 inline uint32_t grid_halo(int k, uint32_t vmax) { return ((uint32_t)k * vmax + 15u) / 16u * 16u; }
 
+// Debug words of the kernels' translation units (read and cleared; always
+// zero in release builds): bits of the DebugSite checks that failed.
+unsigned int debug_word_agent();
+unsigned int debug_word_grid();
+unsigned int debug_word_open();
+unsigned int debug_word_batch();
+unsigned int debug_word_segment();
+
 int agent_tiled_blocks_per_sm();
 int grid_tiled_blocks_per_sm();
 

@@ -3,9 +3,42 @@
 // traffic model", rules 1-4).
 #pragma once
 
+#include <cuda_runtime.h>
 #include <stdint.h>
 
 namespace nasch {
+
+// Debug builds (compiled with -DNASCH_DEBUG) check device-side values and
+// indices at the points where a wrong one would corrupt the state or memory;
+// a failing check sets the bit of its site in a device word of its
+// translation unit and the access it guards is skipped: nothing traps.  The
+// host reads and clears the words after every launch (debug_words()).
+// Release builds compile the checks to `true`.
+enum DebugSite : unsigned int {
+    kDbgAgentPosition = 0,   // a moved car outside [0, L)
+    kDbgAgentVelocity = 1,   // a velocity above vmax
+    kDbgGridWrite = 2,       // a grid kernel's write outside its staged span
+    kDbgSegmentWrite = 3,    // the segment kernel's write outside the owned cells
+    kDbgListVelocity = 4,    // a listed car's velocity above vmax
+};
+#ifdef NASCH_DEBUG
+static __device__ unsigned int g_debug_word;   // one per translation unit
+#define NASCH_DCHECK(cond, site) ((cond) ? true : (atomicOr(&::nasch::g_debug_word, 1u << (site)), false))
+// Defines `unsigned int name()`: this unit's debug word, then cleared.
+#define NASCH_DEBUG_READER(name)                                                        \
+    unsigned int name()                                                                 \
+    {                                                                                   \
+        unsigned int w = 0, z = 0;                                                      \
+        if (cudaMemcpyFromSymbol(&w, ::nasch::g_debug_word, sizeof(w)) != cudaSuccess) \
+            return 0x80000000u;                                                         \
+        cudaMemcpyToSymbol(::nasch::g_debug_word, &z, sizeof(z));                       \
+        return w;                                                                       \
+    }
+#else
+#define NASCH_DCHECK(cond, site) true
+#define NASCH_DEBUG_READER(name) \
+    unsigned int name() { return 0u; }
+#endif
 
 // Philox4x32-10 constants (Salmon, Moraes, Dror & Shaw, SC'11): the two round
 // multipliers and the two Weyl increments of the key schedule.

@@ -129,4 +129,7 @@ cudaError_t launch_grid_open(const GridStep &g, bool exit_open, bool entry, cuda
     return launch_open_variant<Draw::kPhilox>(g, H, n_tiles, exit_open, entry, s);
 }
 
+// This unit's debug word (zero in release builds).
+NASCH_DEBUG_READER(debug_word_open)
+
 }  // namespace nasch

@@ -365,6 +365,46 @@ int upload_checked(nasch_road *h, int64_t N, const int32_t *x, const uint8_t *v)
     return st;
 }
 
+#ifdef NASCH_DEBUG
+// Debug builds, after every nasch_run: wait for the steps, read the kernels'
+// debug words, and check the state now current on the device (agent roads:
+// every car inside the road, no faster than vmax, not on the next car's
+// cell, one descent round the ring; closed grid roads: N occupied cells).
+int debug_after_run(nasch_road *h)
+{
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "debug: steps");
+    const unsigned int w = debug_word_agent() | debug_word_grid() | debug_word_open();
+    if (w) return fail(NASCH_EINVAL, "debug check failed before step %llu (sites 0x%x)", (unsigned long long)h->step, w);
+    if (h->N == 0) return NASCH_OK;
+    if (!h->d_check) e = cudaMalloc(&h->d_check, 3 * sizeof(unsigned long long));
+    unsigned long long res[3] = {~0ull, 0ull, 0ull};
+    if (e == cudaSuccess) e = cudaMemcpy(h->d_check, res, sizeof(res), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        if (h->layout == NASCH_LAYOUT_AGENT)
+            e = launch_check_cars(h->x[h->cur], h->v[h->cur], (uint32_t)h->N, (uint32_t)h->L, (uint32_t)h->vmax,
+                                  h->d_check, h->stream);
+        else if (!h->open)
+            e = launch_count_cars(h->cells[h->cur], (uint32_t)h->L, h->d_check + 2, h->stream);
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(res, h->d_check, sizeof(res), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "debug: state check");
+    if (h->layout == NASCH_LAYOUT_AGENT) {
+        if (res[0] < (unsigned long long)h->N)
+            return fail(NASCH_EINVAL, "debug: car %llu breaks a rule before step %llu", res[0],
+                        (unsigned long long)h->step);
+        if (h->N >= 2 && res[1] != 1)
+            return fail(NASCH_EINVAL, "debug: cyclic order lost before step %llu (%llu descents)",
+                        (unsigned long long)h->step, res[1]);
+    } else if (!h->open && res[2] != (unsigned long long)h->N) {
+        return fail(NASCH_EINVAL, "debug: %llu occupied cells for %lld cars before step %llu", res[2],
+                    (long long)h->N, (unsigned long long)h->step);
+    }
+    return NASCH_OK;
+}
+#endif
+
 int choose_layout(const nasch_params *prm)
 {
     if (prm->layout != NASCH_LAYOUT_AUTO) return prm->layout;
@@ -654,7 +694,11 @@ int nasch_run(nasch_handle h, int64_t steps)
     TraceRange trace("nasch_run");
     if (!h) return fail(NASCH_EINVAL, "handle is NULL");
     if (steps < 0) return fail(NASCH_EINVAL, "steps=%lld < 0", (long long)steps);
-    return run_steps(h, steps);
+    const int st = run_steps(h, steps);
+#ifdef NASCH_DEBUG
+    if (st == NASCH_OK) return debug_after_run(h);
+#endif
+    return st;
 }
 
 int nasch_run_output(nasch_handle h, int64_t steps, int64_t per, int8_t *snap_host, int64_t snap_cap,

@@ -88,7 +88,8 @@ __global__ void __launch_bounds__(32 * kSegWarps) grid_segment_kernel(const Segm
                                if (sum) atomicAdd(&s_sum[s], (unsigned long long)sum);
                                if (cross) atomicAdd(&s_cross[s], (unsigned long long)cross);
                            });
-        for (uint32_t i = lane; i < own; i += 32u) g.out[H + t0 + i] = w.span[H + i];
+        for (uint32_t i = lane; i < own; i += 32u)
+            if (NASCH_DCHECK(H + t0 + i < W, kDbgSegmentWrite)) g.out[H + t0 + i] = w.span[H + i];
         __syncwarp();
     }
     __syncthreads();
@@ -99,6 +100,10 @@ __global__ void __launch_bounds__(32 * kSegWarps) grid_segment_kernel(const Segm
 }
 
 }  // namespace
+
+// This unit's debug word (zero in release builds).
+NASCH_DEBUG_READER(debug_word_segment)
+
 }  // namespace nasch
 
 using namespace nasch;
@@ -155,6 +160,13 @@ extern "C" int nasch_segment_run(const int8_t *seg_in_dev, int8_t *seg_out_dev, 
     case Draw::kAlways: grid_segment_kernel<Draw::kAlways><<<grid, 32 * kSegWarps, 0, s>>>(g); break;
     default: grid_segment_kernel<Draw::kPhilox><<<grid, 32 * kSegWarps, 0, s>>>(g); break;
     }
-    const cudaError_t e = cudaGetLastError();
-    return e == cudaSuccess ? NASCH_OK : cuda_fail(e, "segment kernel");
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "segment kernel");
+#ifdef NASCH_DEBUG
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "segment kernel");
+    if (const unsigned int w = debug_word_segment())
+        return fail(NASCH_EINVAL, "debug check failed in the segment kernel (sites 0x%x)", w);
+#endif
+    return NASCH_OK;
 }

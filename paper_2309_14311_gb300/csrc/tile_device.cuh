@@ -108,6 +108,8 @@ __device__ __forceinline__ void agent_tile_steps(const AgentStep &a, uint32_t (&
                 wrap = nx >= L;
                 nx = wrap ? nx - L : nx;
             }
+            NASCH_DCHECK(nx < L, kDbgAgentPosition);
+            NASCH_DCHECK(vel <= vmax, kDbgAgentVelocity);
             x[r] = nx;
             v[r] = vel;
             if (kFull || (uint32_t)r < n_own) {
@@ -340,6 +342,7 @@ __device__ __forceinline__ void warp_list_groups(uint16_t *pos, uint8_t *vel, ui
             vq -= (vq != 0u && u < thr) ? 1u : 0u;                                 // rule 3
         }
         const uint32_t i = i0 + 32u * (uint32_t)q;
+        NASCH_DCHECK(vq <= vmax, kDbgListVelocity);
         pos[i] = (uint16_t)(x[q] + vq);                                            // rule 4
         vel[i] = (uint8_t)vq;
         const bool mine = x[q] - H < own;

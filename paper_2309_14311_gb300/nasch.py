@@ -64,7 +64,9 @@ _lock = threading.Lock()
 
 
 def library_path() -> str:
-    return _build.LIB
+    """The library this process loads: the debug build when the environment
+    sets NASCH_LIBRARY=debug, else the release build."""
+    return _build.LIB_DEBUG if os.environ.get("NASCH_LIBRARY") == "debug" else _build.LIB
 
 
 def load(build_if_missing: bool = False) -> ctypes.CDLL:
@@ -73,12 +75,13 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     with _lock:
         if _lib is not None:
             return _lib
-        if not os.path.exists(_build.LIB):
+        path = library_path()
+        if not os.path.exists(path):
             if not build_if_missing:
-                raise RuntimeError(f"{_build.LIB} is missing: build it with "
+                raise RuntimeError(f"{path} is missing: build it with "
                                    "`python -m paper_2309_14311_gb300.build` (needs nvcc)")
-            _build.build()
-        lib = ctypes.CDLL(_build.LIB)
+            _build.build(debug=path == _build.LIB_DEBUG)
+        lib = ctypes.CDLL(path)
         _declare(lib)
         _lib = lib
         return lib
