@@ -20,10 +20,11 @@
 // reduced per block and added to the road's series.  A host-mapped flag lets
 // the host cancel: items pulled after it is set do nothing.
 //
-// Initial positions come from Floyd's algorithm run on the GPU, one thread
+// Initial positions come from Floyd's algorithm run on the GPU, one block
 // per road, into a bit map of the road's cells (sorted positions are then
 // the set bits in order).
 #include "batch_internal.h"
+#include "floyd_device.cuh"
 #include "tile_device.cuh"
 
 namespace nasch {
@@ -244,49 +245,17 @@ __global__ void __launch_bounds__(kBatchThreads, 3) batch_kernel(const BatchLaun
     }
 }
 
-// Floyd's algorithm (Bentley & Floyd, CACM 1987), one thread per road: for
-// m = 0..N-1 with j = L-N+m, draw t uniform on 0..j (Lemire's multiply-shift
-// of the Philox word pair of counter (m, 0, road, 1)) and set bit t, or bit
-// j if t is already set.  The draws do not depend on the set, so eight are
-// made at a time and their bit-map words loaded together; the set updates
-// then go in order, an earlier pick of the same group counting as set.
-constexpr int kFloydGroup = 8;
-
-__global__ void batch_floyd_bits_kernel(const BatchRoadDev *roads, uint32_t n, uint64_t *const *bitmaps)
+// Floyd's algorithm (Bentley & Floyd, CACM 1987), one block per road, 1024
+// draws at a time (floyd_road_bits): the road's chosen cells become set bits
+// of its bit map.
+__global__ void __launch_bounds__(kFloydBlock) batch_floyd_bits_kernel(const BatchRoadDev *roads, uint32_t n,
+                                                                       uint64_t *const *bitmaps)
 {
-    const uint32_t r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= n) return;
-    const BatchRoadDev rd = roads[r];
-    uint64_t *bm = bitmaps[r];
-    const uint64_t L = rd.L, N = rd.N;
-    for (uint64_t m0 = 0; m0 < N; m0 += kFloydGroup) {
-        uint64_t t[kFloydGroup], word[kFloydGroup], pick[kFloydGroup];
-#pragma unroll
-        for (int b = 0; b < kFloydGroup; ++b) {
-            const uint64_t m = m0 + (uint64_t)b;
-            t[b] = 0;
-            word[b] = 0;
-            if (m < N) {
-                const uint64_t j = L - N + m;
-                const Words4 w = philox4x32_10((uint32_t)m, 0u, rd.road_id, kTagInit, rd.key0, rd.key1);
-                const uint64_t rr = ((uint64_t)w.w1 << 32) | w.w0;
-                t[b] = __umul64hi(rr, j + 1);
-                word[b] = __ldcg(reinterpret_cast<const unsigned long long *>(bm) + (t[b] >> 6));
-            }
-        }
-#pragma unroll
-        for (int b = 0; b < kFloydGroup; ++b) {
-            const uint64_t m = m0 + (uint64_t)b;
-            pick[b] = 0;
-            if (m < N) {
-                const uint64_t j = L - N + m;
-                bool taken = (word[b] >> (t[b] & 63)) & 1ull;
-#pragma unroll
-                for (int b2 = 0; b2 < b; ++b2) taken = taken || pick[b2] == t[b];
-                pick[b] = taken ? j : t[b];
-                atomicOr(reinterpret_cast<unsigned long long *>(bm + (pick[b] >> 6)), 1ull << (pick[b] & 63));
-            }
-        }
+    __shared__ FloydSmem sm;
+    for (uint32_t r = blockIdx.x; r < n; r += gridDim.x) {
+        const BatchRoadDev rd = roads[r];
+        floyd_road_bits(rd.L, rd.N, rd.road_id, rd.key0, rd.key1,
+                        reinterpret_cast<unsigned long long *>(bitmaps[r]), sm);
     }
 }
 
@@ -376,7 +345,7 @@ cudaError_t launch_batch_super_step(const BatchLaunch &bl, int blocks, cudaStrea
 cudaError_t launch_batch_floyd(const BatchRoadDev *roads, uint32_t n, uint64_t *const *bitmaps, int sms, cudaStream_t s)
 {
     if (n == 0) return cudaSuccess;
-    batch_floyd_bits_kernel<<<(n + 63u) / 64u, 64, 0, s>>>(roads, n, bitmaps);
+    batch_floyd_bits_kernel<<<n < (uint32_t)sms * 2u ? n : (uint32_t)sms * 2u, kFloydBlock, 0, s>>>(roads, n, bitmaps);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const uint32_t blocks = n < (uint32_t)sms * 8u ? n : (uint32_t)sms * 8u;

@@ -12,6 +12,7 @@
 #include <cuda_runtime.h>
 
 #include "nasch.h"
+#include "floyd_device.cuh"
 #include "nasch_device.cuh"
 #include "runtime_internal.h"
 
@@ -38,45 +39,15 @@ int scratch_address(unsigned long long **out)
     return NASCH_OK;
 }
 
-constexpr int kGroup = 8;
-
-// Floyd's algorithm (Bentley & Floyd, CACM 1987) in one thread: for m =
-// 0..N-1 with j = L-N+m, draw t uniform on 0..j (Lemire's multiply-shift of
-// the Philox word pair of counter (m, 0, road, 1)) and set bit t, or bit j
-// if t is already set.  Eight draws are made at a time and their words
-// loaded together; an earlier pick of the same group counts as set.
-__global__ void floyd_bits_single_kernel(uint64_t L, uint64_t N, uint32_t k0, uint32_t k1, uint32_t road,
-                                         unsigned long long *bm)
+// Floyd's algorithm (Bentley & Floyd, CACM 1987) for the road by one block,
+// 1024 draws at a time (floyd_road_bits: the same draws and result as the
+// sequential algorithm), into the scratch bit map.
+__global__ void __launch_bounds__(kFloydBlock) floyd_bits_single_kernel(uint64_t L, uint64_t N, uint32_t k0,
+                                                                        uint32_t k1, uint32_t road,
+                                                                        unsigned long long *bm)
 {
-    for (uint64_t m0 = 0; m0 < N; m0 += kGroup) {
-        uint64_t t[kGroup], word[kGroup], pick[kGroup];
-#pragma unroll
-        for (int b = 0; b < kGroup; ++b) {
-            const uint64_t m = m0 + (uint64_t)b;
-            t[b] = 0;
-            word[b] = 0;
-            if (m < N) {
-                const uint64_t j = L - N + m;
-                const Words4 w = philox4x32_10((uint32_t)m, 0u, road, kTagInit, k0, k1);
-                const uint64_t r = ((uint64_t)w.w1 << 32) | w.w0;
-                t[b] = __umul64hi(r, j + 1);
-                word[b] = __ldcg(bm + (t[b] >> 6));
-            }
-        }
-#pragma unroll
-        for (int b = 0; b < kGroup; ++b) {
-            const uint64_t m = m0 + (uint64_t)b;
-            pick[b] = 0;
-            if (m < N) {
-                const uint64_t j = L - N + m;
-                bool taken = (word[b] >> (t[b] & 63)) & 1ull;
-#pragma unroll
-                for (int b2 = 0; b2 < b; ++b2) taken = taken || pick[b2] == t[b];
-                pick[b] = taken ? j : t[b];
-                atomicOr(bm + (pick[b] >> 6), 1ull << (pick[b] & 63));
-            }
-        }
-    }
+    __shared__ FloydSmem sm;
+    floyd_road_bits(L, N, road, k0, k1, bm, sm);
 }
 
 // Set bits in order -> sorted positions, one block of 256 threads: a
@@ -141,7 +112,7 @@ extern "C" int nasch_floyd_init_device_noalloc(int64_t L, int64_t N, uint64_t se
     // the array keeps the previous call's bits: clear the part this road uses
     cudaError_t e = cudaMemsetAsync(bm, 0, (size_t)words * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return cuda_fail(e, "clear Floyd scratch");
-    floyd_bits_single_kernel<<<1, 1, 0, s>>>((uint64_t)L, (uint64_t)N, (uint32_t)seed, (uint32_t)(seed >> 32), road_id,
+    floyd_bits_single_kernel<<<1, kFloydBlock, 0, s>>>((uint64_t)L, (uint64_t)N, (uint32_t)seed, (uint32_t)(seed >> 32), road_id,
                                              bm);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "Floyd bit-map kernel");
