@@ -326,3 +326,19 @@ def test_bucket_tuning_is_no_slower_than_the_global_choice(clean_tuning):
         NS.set_tuning_table(res["entries"])
         tuned = max(AT.time_batch(roads, 64) for _ in range(3))
         assert tuned >= 0.9 * base, (b, tuned, base)
+
+
+def test_batch_start_states_equal_sequential_floyd():
+    """The batch's start states (Floyd's algorithm by one block per road,
+    1024 draws at a time) equal the oracle's sequential Floyd: sparse and
+    dense roads, a full ring, one car, roads of one and of many groups."""
+    shapes = [(1000, 1), (1000, 999), (3000, 3000), (50_000, 1024), (50_000, 1025), (200_000, 150_000),
+              (2_000_000, 1_200_000), (10_000_000, 300_000), (2**31, 70_000), (4097, 4096)]
+    roads = [dict(L=L, N=N, vmax=5, p=0.1, seed=11 + i, road_id=100 + i, layout="agent")
+             for i, (L, N) in enumerate(shapes)]
+    with NS.Batch(roads, [0] * len(roads)) as b:
+        b.wait()
+        for i, r in enumerate(roads):
+            x, v = b.read_state(i)
+            assert np.array_equal(x, O.floyd_init(r["L"], r["N"], r["seed"], r["road_id"])), shapes[i]
+            assert not v.any()
