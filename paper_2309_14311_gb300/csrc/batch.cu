@@ -151,7 +151,7 @@ void plan_road(const nasch_params &p, int64_t T, const TuningSnapshot &ts, bool 
         } else {
             rd.type = kBatchAgentTile;
             k = p.k ? p.k : (k_tuned ? k_tuned : ts.k_agent);
-            rd.halo = round_up((uint32_t)k, (uint32_t)kBatchAgentR);
+            rd.halo = round_up((uint32_t)k, (uint32_t)kBatchAgentTileR);
             rd.tile = kBatchAgentSpan - rd.halo;
             const int64_t per_item = (int64_t)rd.tile * (kBatchThreads / 32) * kBatchWarpTilesPerWarp;
             *n_items = (p.N + per_item - 1) / per_item;

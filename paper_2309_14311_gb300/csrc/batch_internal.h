@@ -21,8 +21,10 @@ enum BatchType : uint32_t {
 };
 
 constexpr int kBatchThreads = 256;
-constexpr int kBatchAgentR = 8;                                       // cars per lane
-constexpr uint32_t kBatchAgentSpan = 32u * kBatchAgentR;              // cars per warp-tile
+constexpr int kBatchMinBlocks = 3;                                    // launch bound: blocks per SM
+constexpr int kBatchAgentR = 8;                                       // cars per thread of a whole-ring item
+constexpr int kBatchAgentTileR = 8;                                   // cars per lane of an agent warp-tile
+constexpr uint32_t kBatchAgentSpan = 32u * kBatchAgentTileR;          // cars per warp-tile
 constexpr uint32_t kBatchRingCars = kBatchThreads * kBatchAgentR;     // 2048
 constexpr uint32_t kBatchRingCells = (uint32_t)kGridSpan;             // 8192
 constexpr uint32_t kBatchWarpTilesPerWarp = 2;                        // agent warp-tiles per warp per item

@@ -55,9 +55,9 @@ __device__ __forceinline__ void batch_agent_tile(const BatchRoadDev &rd, const R
         const uint32_t t0 = ((item_tile * (uint32_t)(kBatchThreads / 32) + warp) * kBatchWarpTilesPerWarp + w2) * owned;
         if (t0 >= rd.N) return;
         if (t0 + kBatchAgentSpan <= rd.N)
-            agent_warp_tile<kBatchAgentR, D, true>(a, t0, owned, s_sum, s_cross);
+            agent_warp_tile<kBatchAgentTileR, D, true>(a, t0, owned, s_sum, s_cross);
         else
-            agent_warp_tile<kBatchAgentR, D, false>(a, t0, owned, s_sum, s_cross);
+            agent_warp_tile<kBatchAgentTileR, D, false>(a, t0, owned, s_sum, s_cross);
     }
 }
 
@@ -179,7 +179,7 @@ __device__ __forceinline__ void batch_item(const BatchRoadDev &rd, const RoadCon
     }
 }
 
-__global__ void __launch_bounds__(kBatchThreads, 3) batch_kernel(const BatchLaunch bl)
+__global__ void __launch_bounds__(kBatchThreads, kBatchMinBlocks) batch_kernel(const BatchLaunch bl)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ uint32_t s_first[2 * kBatchThreads];
