@@ -260,8 +260,9 @@ def test_large_road_full_size(large_init):
     the first 100 steps equal the oracle's in full (state and per-step
     statistics), the grid layout (one step per launch, and fused) equals
     the agent layout after 100 steps,
-    and after 10^4 steps sampled windows of cars equal the oracle's
-    light-cone evolution of the same cars from the start."""
+    after 10^4 steps sampled windows of cars equal the oracle's
+    light-cone evolution of the same cars from the start, and the fused
+    grid layout equals the agent layout after all 10^4 steps."""
     s = WL.LARGE_ROAD
     x0 = large_init
     T0 = 100
@@ -302,3 +303,11 @@ def test_large_road_full_size(large_init):
                                  openmp=True)
         assert np.array_equal(wx, xT[idx[:M - s.T]]), start
         assert np.array_equal(wv, vT[idx[:M - s.T]]), start
+    # the grid layout (fused) over all 10^4 steps equals the agent layout at T
+    with NS.Road(s.L, s.N, s.vmax, s.p, s.seed, layout="grid", k=WL.LARGE_ROAD_K["grid"]) as g:
+        g.run(s.T)
+        svg, _ = g.stats()
+        assert np.array_equal(svg, svT)
+        xg, vg = g.read_state()   # cars in cell order
+        order = np.argsort(xT, kind="stable")
+        assert np.array_equal(xg, xT[order]) and np.array_equal(vg, vT[order])
