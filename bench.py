@@ -270,6 +270,15 @@ def time_oracle_serial(spec: WL.RoadSpec, steps: int):
     return spec.N * steps / sec, sec
 
 
+def workload_config(spec: WL.RoadSpec, world: int) -> dict:
+    """The benchmark's workload, the same for both arms: the road, its
+    replicas and the state's layout.  How many NaSch steps a benchmark step
+    holds is a property of each arm's timing and goes in its `timing`."""
+    return {"workload": spec.name, "L": spec.L, "N": spec.N, "vmax": spec.vmax, "p": spec.p, "seed": spec.seed,
+            "road_ids": replica_road_ids(world), "layout": "agent", "parallelism": f"replicas{world}",
+            "l2_flush": "not needed: agent state 640 MiB > 129 MB L2"}
+
+
 def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
@@ -290,9 +299,9 @@ def run_reference(args):
         "vs_baseline": None,
         "dtype": "int32",
         "data": "synthetic",
-        "config": {"workload": spec.name, "L": spec.L, "N": spec.N, "vmax": spec.vmax, "p": spec.p,
-                   "seed": spec.seed, "layout": "agent", "steps_per_bench_step": args.ref_steps_per_step,
-                   "l2_flush": "not needed: state 640 MiB > 129 MB L2"},
+        "config": workload_config(spec, world),
+        "timing": {"steps_per_bench_step": args.ref_steps_per_step,
+                   "nasch_steps_timed": args.ref_steps_per_step * args.steps},
         "cpu_baseline": {"value": rate, "unit": "vehicle-updates/s", "cores": cores, "kind": "oracle",
                          "sample": f"full ring, {args.steps} x {args.ref_steps_per_step} NaSch steps "
                                    f"of the {spec.N}-car road (OpenMP oracle)", "cpu_model": cpu_model()},
@@ -519,11 +528,8 @@ def run_ours(args):
             "vs_baseline": None,
             "dtype": "int32",
             "data": "synthetic",
-            "config": {"workload": spec.name, "L": spec.L, "N": spec.N, "vmax": spec.vmax, "p": spec.p,
-                       "seed": spec.seed, "road_ids": replica_road_ids(world), "layout": layout, "k": info.k,
-                       "steps_per_bench_step": chunk, "nasch_steps_timed": chunk * args.steps,
-                       "parallelism": f"replicas{world}",
-                       "l2_flush": "not needed: state 640 MiB (agent) / 4 GiB (grid) > 129 MB L2"},
+            "config": dict(workload_config(spec, world), layout=layout),
+            "timing": {"k": info.k, "steps_per_bench_step": chunk, "nasch_steps_timed": chunk * args.steps},
             "roofline": roofline,
             "roofline_hbm": roofline_hbm,
             "philox_ceiling": {"draws_per_s": philox_rate, "frac": value / world / philox_rate,
