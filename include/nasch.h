@@ -260,9 +260,11 @@ void nasch_batch_destroy(nasch_batch b);
 /* Tuning of the automatic choices (process-wide; the autotuner sets these):
  * rho_star - density below which AUTO picks the agent layout (default 1:
  * with fused steps the agent step is the faster one at every density; a
- * road or batch whose AUTO roads would need more than half of the free
- * device memory at rho_star uses 0.2 instead, the density where the agent
- * state (10 bytes per car) and the grid state (2 per cell) are equal);
+ * single AUTO road whose state would need more than half of the free device
+ * memory at rho_star, or a batch that would need more than 85 % of it
+ * (states, statistics and start-state bit maps), uses 0.2 instead, the
+ * density where the agent state (10 bytes per car) and the grid state (2
+ * per cell) are equal);
  * k_agent, k_grid - fused steps per launch of tiled roads (0 leaves a value
  * unchanged). */
 int nasch_set_tuning(double rho_star, int32_t k_agent, int32_t k_grid);
@@ -278,9 +280,9 @@ int nasch_get_tuning(double *rho_star, int32_t *k_agent, int32_t *k_grid);
  * depth of a road with k = 0 (0 keeps the default), and the tile of a grid
  * road with tile = 0 (2048: warp-tiles of the list method; 8192: block-wide
  * spans; 0 keeps the default).  A road no entry matches uses the global
- * tuning above.  A batch whose AUTO roads would need more than half of the
- * free device memory ignores the table's layouts and uses the state-byte
- * crossover.  The choice never changes a road's result, only its speed. */
+ * tuning above.  A batch that would need more than 85 % of the free device
+ * memory ignores the table's layouts and uses the state-byte crossover.  The
+ * choice never changes a road's result, only its speed. */
 typedef struct nasch_tuning_entry {
     int64_t L_min, L_max;
     double rho_min, rho_max;

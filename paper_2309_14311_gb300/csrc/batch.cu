@@ -35,6 +35,7 @@ std::mutex g_tuning_mu;
 // auto_rho_star falls back to kBytesRhoStar when memory is short.
 double g_rho_star = 1.0;
 constexpr double kBytesRhoStar = 0.2;   // state bytes equal: agent 10 per car, grid 2 per cell
+constexpr double kMemoryShare = 0.85;   // a batch may plan for this share of the free device memory
 int g_k_agent = 8;
 int g_k_grid = 8;
 std::vector<nasch_tuning_entry> g_table;   // per-road tuning, first match wins
@@ -108,21 +109,26 @@ int resolve_layout(const nasch_params &p, const TuningSnapshot &ts, bool memory_
 
 }  // namespace
 
-bool auto_memory_short(const nasch_params *roads, int64_t n, const TuningSnapshot &ts)
+bool auto_memory_short(const nasch_params *roads, int64_t n, const int64_t *steps, const TuningSnapshot &ts)
 {
-    double bytes = 0.0;   // state of the AUTO roads as chosen (two buffers each)
+    // the batch's device memory with its AUTO roads laid out as chosen: two
+    // state buffers, the statistics and (while the start states are built)
+    // the bit maps; explicit layouts count at what they are
+    double state = 0.0, other = 0.0, auto_state = 0.0;
     for (int64_t i = 0; i < n; ++i) {
-        if (roads[i].layout != NASCH_LAYOUT_AUTO) continue;
         const int lay = resolve_layout(roads[i], ts, false, match_entry(ts, roads[i]));
-        bytes += lay == NASCH_LAYOUT_AGENT ? 10.0 * (double)roads[i].N : 2.0 * (double)roads[i].L;
+        const double b = lay == NASCH_LAYOUT_AGENT ? 10.0 * (double)roads[i].N : 2.0 * (double)roads[i].L;
+        state += b;
+        if (roads[i].layout == NASCH_LAYOUT_AUTO) auto_state += b;
+        other += 16.0 * (double)(steps ? std::max<int64_t>(steps[i], 1) : 1) + (double)roads[i].L / 8.0;
     }
-    if (bytes == 0.0) return false;
+    if (auto_state == 0.0) return false;
     size_t free_b = 0, total_b = 0;
     if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
         cudaGetLastError();
         return true;
     }
-    return bytes > 0.5 * (double)free_b;
+    return state + other > kMemoryShare * (double)free_b;
 }
 
 void plan_road(const nasch_params &p, int64_t T, const TuningSnapshot &ts, bool memory_short, BatchRoadDev *out,
@@ -385,7 +391,7 @@ int nasch_submit(const nasch_params *roads, int64_t n_roads, const int64_t *step
 
     // ---------------------------------------------------------------- plan
     const TuningSnapshot ts = tuning_snapshot();
-    const bool memory_short = auto_memory_short(roads, n_roads, ts);
+    const bool memory_short = auto_memory_short(roads, n_roads, steps, ts);
     b->roads.resize((size_t)n_roads);
     b->layout.resize((size_t)n_roads);
     b->super.resize((size_t)n_roads);

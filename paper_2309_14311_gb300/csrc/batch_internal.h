@@ -70,10 +70,11 @@ struct TuningSnapshot {
     std::vector<nasch_tuning_entry> table;
 };
 TuningSnapshot tuning_snapshot();
-// True when the AUTO roads of a batch, laid out as the snapshot chooses,
-// would need more than half of the free device memory: the batch then uses
-// the state-byte crossover density and ignores the table's layouts.
-bool auto_memory_short(const nasch_params *roads, int64_t n, const TuningSnapshot &ts);
+// True when a batch with its AUTO roads laid out as the snapshot chooses
+// (state, statistics of steps[i] steps, start-state bit maps) would need more
+// than 85 % of the free device memory: the batch then uses the state-byte
+// crossover density and ignores the table's layouts.
+bool auto_memory_short(const nasch_params *roads, int64_t n, const int64_t *steps, const TuningSnapshot &ts);
 
 // Per-road plan shared by batches and the server: layout (AUTO: the table,
 // else by density), item kind, fusion depth, halo/tile geometry, items per
