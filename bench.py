@@ -191,12 +191,7 @@ def kernel_source_hash(kernel: str) -> str:
 # streaming kernels grows in proportion).  Keyed by the hash of the kernel's
 # sources (comments and layout aside) when it was captured: a changed kernel
 # reports null until it is captured again.
-NCU_TRAFFIC: dict[str, dict] = {
-    "agent_tiled_k16": {"source_hash": "65e7c4e9cc783579", "captured_bytes": 167856896 + 121494528,
-                        "scale": 4, "bytes_per_launch": 4 * (167856896 + 121494528)},
-    "grid_k1": {"source_hash": "9d52a0fc864e3a9a", "captured_bytes": 268507648 + 219239936,
-                "scale": 8, "bytes_per_launch": 8 * (268507648 + 219239936)},
-}
+NCU_TRAFFIC: dict[str, dict] = {}
 
 
 def traffic_for(kernel: str):

@@ -137,7 +137,8 @@ __device__ __forceinline__ void batch_grid_warp(const BatchRoadDev &rd, const Ro
         }
     }
     __syncwarp();
-    grid_warp_steps<D>(rc, PlainDraws{rc, 0}, w.span, w.pos, w.vel, H, own, base, step0, kk, []() {},
+    grid_warp_steps<D>(rc, PlainDraws{rc, 0}, w.span, WarpList{w.pos, w.vel, kKwList, nullptr, nullptr}, H, own, base, step0,
+                       kk, []() {},
                        [&](int s, uint32_t sum, uint32_t cross) {
                            if (sum) atomicAdd(&s_sum[s], (unsigned long long)sum);
                            if (cross) atomicAdd(&s_cross[s], (unsigned long long)cross);

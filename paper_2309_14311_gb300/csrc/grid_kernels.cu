@@ -430,8 +430,8 @@ constexpr int kKwWarps = 4;                             // warps per block
 
 struct __align__(16) KwWarpSmem {
     int8_t buf[2][kKwBuf];
-    uint16_t pos[kKwList];
-    uint8_t vel[kKwList];
+    uint16_t pos[kKwListSmem];    // the list of a span whose cars fit; denser spans use global scratch
+    uint8_t vel[kKwListSmem];
     uint32_t sum[kMaxFusedSteps];     // statistics of the warp's tiles, by step
     uint32_t cross[kMaxFusedSteps];
     uint64_t full[2];
@@ -493,8 +493,11 @@ __global__ void __launch_bounds__(32 * kKwWarps) grid_warp_kernel(const GridStep
             break;
         }
         __syncwarp();
+        uint8_t *big = g.list_scratch + (size_t)(blockIdx.x * (uint32_t)kKwWarps + warp) * (3u * kKwList);
         grid_warp_steps<D>(
-            g.rc, FoldedDraws{sk, {}}, span, w.pos, w.vel, H, own, base, g.step0, ksteps,
+            g.rc, FoldedDraws{sk, {}}, span,
+            WarpList{w.pos, w.vel, kKwListSmem, reinterpret_cast<uint16_t *>(big), big + 2u * kKwList}, H, own,
+            base, g.step0, ksteps,
             [&]() {   // the next tile goes into the other buffer once the store of the tile before has read it
                 if (lane == 0) {
                     bulk_wait_read_all();
@@ -616,6 +619,24 @@ cudaError_t launch_grid_variant(const GridStep &g, const GridTileGeom &geo, int 
 
 }  // namespace
 
+size_t grid_list_scratch_bytes()
+{
+    int dev = 0, sms = 0, most = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return 0;
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, grid_warp_kernel<Draw::kNever>, 32 * kKwWarps, 0) != cudaSuccess)
+        return 0;
+    most = b;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, grid_warp_kernel<Draw::kAlways>, 32 * kKwWarps, 0) != cudaSuccess)
+        return 0;
+    most = b > most ? b : most;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, grid_warp_kernel<Draw::kPhilox>, 32 * kKwWarps, 0) != cudaSuccess)
+        return 0;
+    most = b > most ? b : most;
+    return (size_t)sms * (size_t)(most > 0 ? most : 1) * (size_t)kKwWarps * 3u * (size_t)kKwList;
+}
+
 int grid_tiled_blocks_per_sm()
 {
     const GridTileGeom geo = make_geom(1, 5, 1u << 20);
@@ -644,6 +665,7 @@ cudaError_t launch_grid_tiled(const GridStep &g, int blocks, cudaStream_t s)
         return launch_k1_variant<Draw::kPhilox, false>(g, n_tiles, s);
     }
     if (geo.halo <= kKwMaxHalo) {
+        if (!g.list_scratch) return cudaErrorInvalidValue;   // dense spans need it
         const uint32_t n_tiles = (g.rc.L + (kKwSpan - 2u * geo.halo) - 1u) / (kKwSpan - 2u * geo.halo);
         if (g.rc.thr == 0) return launch_kw_variant<Draw::kNever>(g, geo.halo, n_tiles, s);
         if (g.rc.thr > 0xFFFFFFFFull) return launch_kw_variant<Draw::kAlways>(g, geo.halo, n_tiles, s);

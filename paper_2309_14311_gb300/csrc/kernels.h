@@ -70,6 +70,10 @@ struct GridStep {
     int ksteps;
     unsigned long long *sum_v;
     unsigned long long *crossings;
+    // the fused grid kernel's car lists of spans too dense for its shared
+    // list, kKwList entries (3 bytes each) per warp of the launch
+    // (grid_list_scratch_bytes()); null for the other kernels
+    uint8_t *list_scratch = nullptr;
 };
 
 // Owned cars per warp-tile of `span` cars (32 lanes x span/32) for fusion depth k.
@@ -78,6 +82,10 @@ inline uint32_t agent_tile_owned(int k, int span)
     const int r = span / 32;
     return (uint32_t)(span - ((k + r - 1) / r) * r);
 }
+// Shared-memory list entries per warp of the fused grid kernel (a span with
+// more cars uses its warp's part of GridStep::list_scratch).
+constexpr uint32_t kKwListSmem = 1024;
+
 // Halo cells per side for the grid tile.
 inline uint32_t grid_halo(int k, uint32_t vmax) { return ((uint32_t)k * vmax + 15u) / 16u * 16u; }
 
@@ -91,6 +99,9 @@ unsigned int debug_word_segment();
 
 int agent_tiled_blocks_per_sm();
 int grid_tiled_blocks_per_sm();
+// Bytes of GridStep::list_scratch a launch of the fused grid kernel needs on
+// the current device (0 if the occupancy query fails).
+size_t grid_list_scratch_bytes();
 
 cudaError_t launch_agent_tiled(const AgentStep &a, int span, int blocks, cudaStream_t s);
 cudaError_t launch_agent_ring(const AgentStep &a, cudaStream_t s);

@@ -68,7 +68,8 @@ __global__ void __launch_bounds__(32 * kOpenWarps) grid_open_kernel(const GridSt
         const int64_t end = (int64_t)L - first;
         if (!exit_open && lane == 0 && end >= 0 && end < (int64_t)kKwSpan) w.span[end] = 0;
         __syncwarp();
-        grid_warp_steps<D>(g.rc, PlainDraws{g.rc, 0}, w.span, w.pos, w.vel, H, own, base, g.step0, 1, []() {},
+        grid_warp_steps<D>(g.rc, PlainDraws{g.rc, 0}, w.span, WarpList{w.pos, w.vel, kKwList, nullptr, nullptr}, H, own,
+                           base, g.step0, 1, []() {},
                            [&](int, uint32_t sum, uint32_t cross) {
                                tsum += sum;
                                tcross += cross;

@@ -146,6 +146,7 @@ struct nasch_road {
     int tile = 0;                       // agent warp-tile span or grid tile cells
     unsigned int *d_status = nullptr;   // kernels set bits here when a bounded wait runs out
     unsigned long long *d_check = nullptr;   // nasch_set_state's device checks (3 words), made on first use
+    uint8_t *d_list = nullptr;          // the fused grid kernel's car lists of dense spans (GridStep::list_scratch)
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     int32_t *x[2] = {nullptr, nullptr};
@@ -210,6 +211,7 @@ void free_road(nasch_road *h)
     cudaFree(h->d_cross);
     cudaFree(h->d_status);
     cudaFree(h->d_check);
+    cudaFree(h->d_list);
     if (h->io_stream) cudaStreamSynchronize(h->io_stream);
     for (int i = 0; i < 2; ++i) {
         cudaFree(h->stage[i]);
@@ -493,6 +495,7 @@ int run_steps(nasch_road *h, int64_t steps)
         GridStep g;
         g.status = h->d_status;
         g.rc = rc;
+        g.list_scratch = h->d_list;
         for (int64_t done = 0; done < steps;) {
             const int kk = h->ring ? (int)std::min<int64_t>(steps - done, 1 << 20)
                                    : (int)std::min<int64_t>(steps - done, h->k);
@@ -584,6 +587,13 @@ int create_road(const nasch_params *prm, bool open, uint64_t thr_entry, uint64_t
         h->blocks = h->sms * grid_tiled_blocks_per_sm();
         e = cudaSuccess;
         for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaMalloc(&h->cells[i], (size_t)h->L + 16);
+        // the fused warp kernel (k >= 2, or vmax above the one-step kernel's,
+        // with halos up to kKwMaxHalo) keeps the lists of dense spans here
+        if (e == cudaSuccess && !open && !h->ring && (h->k >= 2 || h->vmax > 16) &&
+            grid_halo(h->k, (uint32_t)h->vmax) <= kKwMaxHalo) {
+            const size_t bytes = grid_list_scratch_bytes();
+            e = bytes ? cudaMalloc(&h->d_list, bytes) : cudaErrorInvalidValue;
+        }
     }
     if (e == cudaSuccess) e = cudaMalloc(&h->d_status, sizeof(unsigned int));
     if (e == cudaSuccess) e = cudaMemset(h->d_status, 0, sizeof(unsigned int));

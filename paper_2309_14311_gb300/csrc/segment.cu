@@ -83,7 +83,8 @@ __global__ void __launch_bounds__(32 * kSegWarps) grid_segment_kernel(const Segm
             reinterpret_cast<uint4 *>(w.span)[c] = q;
         }
         __syncwarp();
-        grid_warp_steps<D>(g.rc, PlainDraws{g.rc, 0}, w.span, w.pos, w.vel, H, own, base, g.step0, g.ksteps, []() {},
+        grid_warp_steps<D>(g.rc, PlainDraws{g.rc, 0}, w.span, WarpList{w.pos, w.vel, kKwList, nullptr, nullptr}, H, own, base,
+                           g.step0, g.ksteps, []() {},
                            [&](int s, uint32_t sum, uint32_t cross) {
                                if (sum) atomicAdd(&s_sum[s], (unsigned long long)sum);
                                if (cross) atomicAdd(&s_cross[s], (unsigned long long)cross);

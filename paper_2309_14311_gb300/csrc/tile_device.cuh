@@ -369,39 +369,30 @@ __device__ __forceinline__ void warp_list_step(uint16_t *pos, uint8_t *vel, uint
         warp_list_groups<1, D, W>(pos, vel, gi + lane, draws, L, vmax, thr, base, H, own, tsum, tcross);
 }
 
-// Fused steps of one warp-tile.  span: kKwBuf bytes of shared memory holding
-// the staged cells (span index 0 = road cell `base`); on return its cells
-// [H, H + own) hold the result.  pos / vel: kKwList entries of shared memory.
-// draws: FoldedDraws or PlainDraws of the road.  after_list() is called by
-// every lane once the span has been read (it may be reused from then on);
-// add(s, sum, cross) by lane 0 with step s's statistics of this warp-tile.
+// Where grid_warp_steps keeps a warp-tile's car list: `cap` entries at pos /
+// vel (shared memory), and, for a span with more cars, kKwList entries at
+// pos_big / vel_big (this warp's part of a global scratch; null when cap is
+// kKwList, which every span fits).
+struct WarpList {
+    uint16_t *pos;
+    uint8_t *vel;
+    uint32_t cap;
+    uint16_t *pos_big;
+    uint8_t *vel_big;
+};
+
+// Steps 1 (second half) to 3 of grid_warp_steps with the list at pos / vel.
 template <Draw D, class Draws, class AfterList, class Add>
-__device__ __forceinline__ void grid_warp_steps(const RoadConst &rc, Draws draws, int8_t *span, uint16_t *pos,
-                                                uint8_t *vel, uint32_t H, uint32_t own, uint32_t base,
-                                                uint32_t step0, int ksteps, AfterList after_list, Add add)
+__device__ __forceinline__ void grid_warp_list_run(const RoadConst &rc, Draws &draws, int8_t *span, uint16_t *pos,
+                                                   uint8_t *vel, const uint32_t (&m)[kKwSpan / 1024u], uint32_t p,
+                                                   uint32_t total, uint32_t padded, uint32_t H, uint32_t own,
+                                                   uint32_t base, uint32_t step0, int ksteps, AfterList &after_list,
+                                                   Add &add)
 {
-    constexpr uint32_t kWords = kKwSpan / 1024u;          // occupancy words per lane
+    constexpr uint32_t kWords = kKwSpan / 1024u;
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t L = rc.L, vmax = rc.vmax, thr = (uint32_t)rc.thr;
-    // 1. the list: cars in cell order
     const uint32_t c0 = 32u * kWords * lane;
-    const uint4 *q = reinterpret_cast<const uint4 *>(span + c0);
-    uint32_t m[kWords];
-    uint32_t n = 0;
-#pragma unroll
-    for (uint32_t j = 0; j < kWords; ++j) {
-        m[j] = occupancy16(q[2u * j]) | (occupancy16(q[2u * j + 1u]) << 16);
-        n += __popc(m[j]);
-    }
-    uint32_t incl = n;
-#pragma unroll
-    for (uint32_t d = 1; d < 32; d <<= 1) {
-        const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, incl, d);
-        if (lane >= d) incl += t;
-    }
-    const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
-    const uint32_t padded = (total + 31u) & ~31u;   // whole groups
-    uint32_t p = incl - n;
 #pragma unroll
     for (uint32_t j = 0; j < kWords; ++j)
         for (uint32_t mm = m[j]; mm; mm &= mm - 1u, ++p) {
@@ -438,6 +429,47 @@ __device__ __forceinline__ void grid_warp_steps(const RoadConst &rc, Draws draws
         if (x - H < own) span[x] = (int8_t)vel[i];
     }
     __syncwarp();
+}
+
+// Fused steps of one warp-tile.  span: kKwBuf bytes of shared memory holding
+// the staged cells (span index 0 = road cell `base`); on return its cells
+// [H, H + own) hold the result.  wl: where the car list goes (a span whose
+// cars, padded to whole groups and one leader, exceed wl.cap takes the big
+// list).  draws: FoldedDraws or PlainDraws of the road.  after_list() is
+// called by every lane once the span has been read (it may be reused from
+// then on); add(s, sum, cross) by lane 0 with step s's statistics of this
+// warp-tile.
+template <Draw D, class Draws, class AfterList, class Add>
+__device__ __forceinline__ void grid_warp_steps(const RoadConst &rc, Draws draws, int8_t *span, const WarpList wl,
+                                                uint32_t H, uint32_t own, uint32_t base, uint32_t step0, int ksteps,
+                                                AfterList after_list, Add add)
+{
+    constexpr uint32_t kWords = kKwSpan / 1024u;          // occupancy words per lane
+    const uint32_t lane = threadIdx.x & 31u;
+    // 1. the list: cars in cell order
+    const uint32_t c0 = 32u * kWords * lane;
+    const uint4 *q = reinterpret_cast<const uint4 *>(span + c0);
+    uint32_t m[kWords];
+    uint32_t n = 0;
+#pragma unroll
+    for (uint32_t j = 0; j < kWords; ++j) {
+        m[j] = occupancy16(q[2u * j]) | (occupancy16(q[2u * j + 1u]) << 16);
+        n += __popc(m[j]);
+    }
+    uint32_t incl = n;
+#pragma unroll
+    for (uint32_t d = 1; d < 32; d <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+        if (lane >= d) incl += t;
+    }
+    const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+    const uint32_t padded = (total + 31u) & ~31u;   // whole groups
+    if (wl.pos_big == nullptr || padded + 1u <= wl.cap)   // warp-uniform
+        grid_warp_list_run<D>(rc, draws, span, wl.pos, wl.vel, m, incl - n, total, padded, H, own, base, step0,
+                              ksteps, after_list, add);
+    else
+        grid_warp_list_run<D>(rc, draws, span, wl.pos_big, wl.vel_big, m, incl - n, total, padded, H, own, base,
+                              step0, ksteps, after_list, add);
 }
 
 // The span-list method of a grid tile (used when the staged span's cars fit
