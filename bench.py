@@ -745,7 +745,7 @@ def run_workload(args):
         rows_out = []
         for layout, k in (("agent", 16), ("grid", 1)):
             with NS.Road(L, N, 5, 0.13, 1, 0, layout=layout, k=k, stream=stream) as r:
-                r.run_output(2 * k, 0, None, None)   # warm-up
+                r.run_output(2 * k, k, snaps, rows[:2])   # warm-up, and the staging buffers made
                 res = {}
                 for name, per, sn, rw in (("off", 0, None, None), ("snap_every_50", 50, snaps, None),
                                           ("snap_every_10", 10, snaps, None), ("raster_every_1", 1, None, rows)):
