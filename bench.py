@@ -691,6 +691,10 @@ def run_workload(args):
     serve                the seed-11 request stream (first --serve-requests),
                          Poisson arrivals at --serve-load x capacity, 40 GB
                          budget; p50/p99 latency and aggregate rate;
+    decomposed           a 2^30-cell ring split over 1, 2 and 4 cell ranges
+                         (every rank on this GPU, one after another):
+                         the segment kernel's rate per rank and the halo
+                         bytes of an exchange;
     serve-vs-batch       the first --serve-requests requests batched in one
                          job and served all at once (series streamed back):
                          the served rate as a fraction of the batched one;
@@ -811,6 +815,52 @@ def run_workload(args):
         out.update(roads=len(roads), L=args.fd_L, T=T, warmup=WL.FD_WARMUP, vmax=args.fd_vmax,
                    vehicle_updates=work, batched_gpu_seconds=inf.run_seconds, wall_seconds=wall,
                    vehicle_updates_per_s=work / inf.run_seconds, **FD.summary(rows), table=rows)
+    elif args.workload == "decomposed":
+        # one ring split over `world` cell ranges (the multi-GPU domain
+        # decomposition), every rank's buffer on this GPU and the ranks run
+        # one after another; per-rank segment-kernel time by CUDA events, the
+        # halo exchange as device copies between the buffers
+        from paper_2309_14311_gb300 import decomp as DC
+        L, N, vmax, p, k = 1 << 30, 1 << 26, 5, 0.13, 8
+        steps = max(args.other_steps // k, 2) * k
+        x0 = NS.floyd_init(L, N, 1, 0)
+        rows_out = []
+        for world in (1, 2, 4):
+            segs = DC.segments(L, world, k, vmax)
+            bufs = []
+            for sg in segs:
+                b = torch.full((sg.W,), -1, dtype=torch.int8, device="cuda")
+                j = (x0.astype(np.int64) - sg.a) % L
+                b[torch.from_numpy(sg.H + j[j < sg.owned]).cuda()] = 0
+                bufs.append(b)
+            outs = [b.clone() for b in bufs]
+            kernel_s = [0.0] * world
+            base_step = DC.library_step(L, vmax, p, 1, 0, stream=torch.cuda.current_stream())
+
+            def timed(seg, bi, bo, kk, s0, rank):
+                a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                res = base_step(seg, bi, bo, kk, s0, rank)
+                e.record()
+                e.synchronize()
+                kernel_s[rank] += a.elapsed_time(e) / 1e3
+                return res
+
+            DC.run_local(segs, bufs, 2 * k, base_step, spare=outs)            # warm-up
+            torch.cuda.synchronize()
+            kernel_s = [0.0] * world
+            t0 = time.perf_counter()
+            bufs2, _ = DC.run_local(segs, bufs, steps, timed, step0=2 * k, spare=outs)
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t0
+            rows_out.append({"world": world, "steps": steps, "halo_cells": segs[0].H,
+                             "halo_bytes_per_rank_per_launch": 2 * segs[0].H,
+                             "segment_kernel_seconds_per_rank": kernel_s,
+                             "cell_updates_per_s_per_rank_kernel": [sg.owned * steps / t for sg, t in zip(segs, kernel_s)],
+                             "cell_updates_per_s_one_gpu_all_ranks": L * steps / wall})
+        out.update(L=L, N=N, vmax=vmax, p=p, k=k, rows=rows_out,
+                   note="ranks run one after another on one GPU; a rank's kernel rate is what one GPU per rank "
+                        "would run at, before its halo exchange")
     elif args.workload == "serve-vs-batch":
         rows = WL.request_stream()[: args.serve_requests]
         out.update(run_serve_vs_batch(args, NS, stream, rows))
@@ -877,7 +927,7 @@ def main(argv=None):
     ap.add_argument("--ref-steps-per-step", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", choices=["large-road", "ensemble", "fundamental-diagram", "serve", "serve-vs-batch",
-                                           "k-sweep", "snapshots", "open-road"],
+                                           "k-sweep", "snapshots", "open-road", "decomposed"],
                     default="large-road", help="large-road is the benchmark line; the others print their own line")
     ap.add_argument("--sweep-k", default="1,2,4,8,16,32", help="fusion depths of the k-sweep workload")
     ap.add_argument("--roads", type=int, default=4096)
