@@ -587,10 +587,12 @@ int create_road(const nasch_params *prm, bool open, uint64_t thr_entry, uint64_t
         h->blocks = h->sms * grid_tiled_blocks_per_sm();
         e = cudaSuccess;
         for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaMalloc(&h->cells[i], (size_t)h->L + 16);
-        // the fused warp kernel (k >= 2, or vmax above the one-step kernel's,
-        // with halos up to kKwMaxHalo) keeps the lists of dense spans here
-        if (e == cudaSuccess && !open && !h->ring && (h->k >= 2 || h->vmax > 16) &&
-            grid_halo(h->k, (uint32_t)h->vmax) <= kKwMaxHalo) {
+        // the fused warp kernel keeps the lists of dense spans here; any
+        // launch of fewer than the road's k steps may take it (a halo of k
+        // steps above kKwMaxHalo shrinks for a shorter last launch), so every
+        // road that is not stepped one step at a time by the one-step kernel
+        // gets it
+        if (e == cudaSuccess && !open && !h->ring && (h->k >= 2 || h->vmax > 16)) {
             const size_t bytes = grid_list_scratch_bytes();
             e = bytes ? cudaMalloc(&h->d_list, bytes) : cudaErrorInvalidValue;
         }

@@ -129,6 +129,7 @@ GRID_TILED = [  # (L, N, vmax, p, k, T)
     (50000, 2000, 5, 1.0, 3, 20),
     (33000, 1, 5, 0.2, 6, 30),                 # a car alone
     (100000, 5000, 8, 0.13, 64, 70),
+    (70000, 20000, 20, 0.2, 30, 39),           # halo of k steps above 512: block spans, then a shorter last launch
 ]
 
 
