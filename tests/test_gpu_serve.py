@@ -195,3 +195,38 @@ def test_tick_grows_when_few_roads_are_resident():
         osv, ocr, _ = oracle_request(r)
         assert np.array_equal(sv, osv) and np.array_equal(cr, ocr)
 
+
+
+def test_series_stream_with_small_caps_and_release():
+    """poll_series with a step cap smaller than what is ready returns the
+    first part and keeps the rest for the next call; chunks of several
+    requests share one call; a released request's remaining series is
+    dropped."""
+    reqs = [dict(L=100_000, N=8_000, vmax=5, p=0.2, seed=21 + i, road_id=90 + i, T=700) for i in range(3)]
+    with NS.Server(memory_budget=1 << 30, steps_per_tick=4, max_steps_per_tick=4, target_tick_ms=0) as srv:
+        for i, r in enumerate(reqs):
+            srv.submit(WL.road_params(r), r["T"], i)
+        srv.drain(600000)
+        done = {res["request_id"] for res in srv.poll()}
+        assert done == {0, 1, 2}
+        got = {0: [], 1: []}
+        while True:
+            chunks = srv.poll_series(cap_chunks=2, cap_steps=150)   # at most 150 steps, 2 chunks per call
+            if not chunks:
+                break
+            assert len(chunks) <= 2 and sum(len(c[2]) for c in chunks) <= 150
+            for rid, first, sv, cr in chunks:
+                if rid == 2:
+                    continue
+                got[rid].append((first, sv, cr))
+            if 2 in {c[0] for c in chunks}:
+                srv.release(2)                                      # the rest of request 2 is dropped
+        for i in (0, 1):
+            firsts = [c[0] for c in got[i]]
+            sv = np.concatenate([c[1] for c in got[i]])
+            cr = np.concatenate([c[2] for c in got[i]])
+            assert firsts == list(np.cumsum([0] + [len(c[1]) for c in got[i]]))[:-1]
+            fsv, fcr = srv.result(i)
+            assert np.array_equal(sv, fsv) and np.array_equal(cr, fcr), i
+        with pytest.raises((NS.NaschError, KeyError)):   # the request is gone
+            srv.result(2)
