@@ -664,7 +664,12 @@ def run_serve_vs_batch(args, NS, stream, rows):
                          steps_per_tick=args.serve_steps_per_tick, time_limit_s=args.serve_time_limit,
                          stream_series=True)
     served = out["vehicle_updates_per_s"]
+    import torch
+    plain = ensemble_vs_plain(NS, stream, torch, rows, min(64, len(rows)), seed=11)
     return {"requests": len(rows), "vehicle_updates": work, "batched_vehicle_updates_per_s": work / batched_s,
+            "plain_vehicle_updates_per_s": plain.get("plain_vehicle_updates_per_s"),
+            "plain_sample": f"{plain.get('plain_roads')} of the requests (seed 11) run one road per launch",
+            "served_over_plain": served / plain["plain_vehicle_updates_per_s"] if plain.get("plain_roads") else None,
             "batched_with_start_states_vehicle_updates_per_s": work / batched_wall,
             "served_vehicle_updates_per_s": served, "served_over_batched": served / (work / batched_s),
             "served_gpu_busy_fraction": out["gpu_busy_fraction"], "served_span_s": out["span_s"],
