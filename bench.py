@@ -609,7 +609,6 @@ def ensemble_vs_plain(NS, stream, torch, rows, plain_roads, seed=7):
     `plain_roads` of them one after another through the single-road API
     (plain per-road launches); GPU time only on both sides (start states
     excluded)."""
-    import numpy as np
     roads = [WL.road_params(r) for r in rows]
     steps = [r["T"] for r in rows]
     work = sum(r["N"] * r["T"] for r in rows)
@@ -625,6 +624,15 @@ def ensemble_vs_plain(NS, stream, torch, rows, plain_roads, seed=7):
                agent_roads=sum(1 for x in layouts if x == NS.LAYOUT_AGENT))
     if plain_roads <= 0:
         return out
+    out.update(plain_launches(NS, stream, torch, rows, plain_roads, seed))
+    out["speedup"] = (work / inf.run_seconds) / out["plain_vehicle_updates_per_s"]
+    return out
+
+
+def plain_launches(NS, stream, torch, rows, plain_roads, seed):
+    """A seeded subset of `plain_roads` of the roads run one after another
+    through the single-road API (one road per launch), GPU time only."""
+    import numpy as np
     sub = list(range(len(rows)))
     if plain_roads < len(rows):
         rng = np.random.default_rng(seed)
@@ -641,10 +649,8 @@ def ensemble_vs_plain(NS, stream, torch, rows, plain_roads, seed=7):
             e.record(stream)
             e.synchronize()
             plain += a.elapsed_time(e) / 1e3
-    out.update(plain_roads=len(sub), plain_vehicle_updates=pwork, plain_gpu_seconds=plain,
-               plain_vehicle_updates_per_s=pwork / plain,
-               speedup=(work / inf.run_seconds) / (pwork / plain))
-    return out
+    return dict(plain_roads=len(sub), plain_vehicle_updates=pwork, plain_gpu_seconds=plain,
+                plain_vehicle_updates_per_s=pwork / plain)
 
 
 def run_serve_vs_batch(args, NS, stream, rows):
@@ -665,11 +671,11 @@ def run_serve_vs_batch(args, NS, stream, rows):
                          stream_series=True)
     served = out["vehicle_updates_per_s"]
     import torch
-    plain = ensemble_vs_plain(NS, stream, torch, rows, min(64, len(rows)), seed=11)
+    plain = plain_launches(NS, stream, torch, rows, min(64, len(rows)), seed=11)
     return {"requests": len(rows), "vehicle_updates": work, "batched_vehicle_updates_per_s": work / batched_s,
-            "plain_vehicle_updates_per_s": plain.get("plain_vehicle_updates_per_s"),
-            "plain_sample": f"{plain.get('plain_roads')} of the requests (seed 11) run one road per launch",
-            "served_over_plain": served / plain["plain_vehicle_updates_per_s"] if plain.get("plain_roads") else None,
+            "plain_vehicle_updates_per_s": plain["plain_vehicle_updates_per_s"],
+            "plain_sample": f"{plain['plain_roads']} of the requests (seed 11) run one road per launch",
+            "served_over_plain": served / plain["plain_vehicle_updates_per_s"],
             "batched_with_start_states_vehicle_updates_per_s": work / batched_wall,
             "served_vehicle_updates_per_s": served, "served_over_batched": served / (work / batched_s),
             "served_gpu_busy_fraction": out["gpu_busy_fraction"], "served_span_s": out["span_s"],
