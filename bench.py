@@ -192,10 +192,6 @@ def kernel_source_hash(kernel: str) -> str:
 # sources (comments and layout aside) when it was captured: a changed kernel
 # reports null until it is captured again.
 NCU_TRAFFIC: dict[str, dict] = {
-    "agent_tiled_k16": {"source_hash": "b97f2c8ce579c2ab", "captured_bytes": 167857920 + 121763584,
-                        "scale": 4, "bytes_per_launch": 4 * (167857920 + 121763584)},
-    "grid_k1": {"source_hash": "cbfe3efefa578567", "captured_bytes": 268520448 + 219816192,
-                "scale": 8, "bytes_per_launch": 8 * (268520448 + 219816192)},
 }
 
 

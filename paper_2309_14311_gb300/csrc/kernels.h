@@ -17,7 +17,7 @@ constexpr int kMaxFusedSteps = 64;
 // round_up(k, R) are look-ahead halo; blocks of 128 threads (4 independent
 // warps).
 constexpr int kAgentThreads = 128;
-constexpr int kAgentBlocksPerSm = 4;   // register budget: 4 blocks of 128 threads per SM
+constexpr int kAgentBlocksPerSm = 3;   // register budget: 3 blocks of 128 threads per SM
 constexpr int kAgentCarsPerThread = 16;
 constexpr int kAgentTileSpan = 32 * kAgentCarsPerThread;
 constexpr int kAgentTileSpanSmall = 32 * 8;

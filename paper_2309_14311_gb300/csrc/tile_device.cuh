@@ -63,16 +63,9 @@ enum class Draw { kNever, kAlways, kPhilox };
 
 __host__ __device__ __forceinline__ Draw draw_mode(uint64_t thr) { return thr == 0 ? Draw::kNever : (thr > 0xFFFFFFFFull ? Draw::kAlways : Draw::kPhilox); }
 
-// The k fused steps of one warp-tile held in registers (32 lanes x R cars).
-// kInterior: no car of the tile can reach cell L-1 within the launch (the
-// tile does not wrap round the ring and its last car, moving at most vmax a
-// step, stays below L), so every leader in the tile lies ahead of its car in
-// plain cell order, no car crosses L-1 -> 0, and the step needs no modular
-// arithmetic and no crossing count.  The tile's last car takes the next
-// lane's first car as leader, and lane 31's last car is halo whose result is
-// discarded; its velocity stays <= vmax, which keeps its moves inside the
-// bound the interior test assumes.
-template <int R, Draw D, bool kFull, bool kInterior>
+// The k fused steps of one warp-tile held in registers (32 lanes x R cars),
+// on the ring: the gap is taken modulo L and cars crossing L-1 -> 0 wrap.
+template <int R, Draw D, bool kFull>
 __device__ __forceinline__ void agent_tile_steps(const AgentStep &a, uint32_t (&x)[R], uint32_t (&v)[R],
                                                  uint32_t n_own, unsigned long long *s_sum,
                                                  unsigned long long *s_cross)
@@ -94,7 +87,7 @@ __device__ __forceinline__ void agent_tile_steps(const AgentStep &a, uint32_t (&
             // empty cells ahead: (lead - x - 1) mod L, or L - 1 if the car is
             // its own leader; on the ring as the smaller of two unsigned values
             const uint32_t d = lead - xi;
-            const uint32_t gap = kInterior ? d - 1u : min(d - 1u, d + Lm1);
+            const uint32_t gap = min(d - 1u, d + Lm1);
             uint32_t vel = min(min(v[r] + 1u, vmax), gap);            // rules 1, 2
             if (D == Draw::kAlways) {
                 vel -= vel > 0u ? 1u : 0u;                              // rule 3, p = 1
@@ -103,28 +96,88 @@ __device__ __forceinline__ void agent_tile_steps(const AgentStep &a, uint32_t (&
                 vel -= (vel > 0u && u < thr) ? 1u : 0u;                 // rule 3
             }
             uint32_t nx = xi + vel;                                     // rule 4
-            bool wrap = false;
-            if (!kInterior) {
-                wrap = nx >= L;
-                nx = wrap ? nx - L : nx;
-            }
+            const bool wrap = nx >= L;
+            nx = wrap ? nx - L : nx;
             NASCH_DCHECK(nx < L, kDbgAgentPosition);
             NASCH_DCHECK(vel <= vmax, kDbgAgentVelocity);
             x[r] = nx;
             v[r] = vel;
             if (kFull || (uint32_t)r < n_own) {
                 tsum += vel;
-                if (!kInterior) tcross += wrap ? 1u : 0u;
+                tcross += wrap ? 1u : 0u;
             }
         }
         if (kFull && n_own == 0u) tsum = tcross = 0u;   // halo lanes
         tsum = __reduce_add_sync(0xFFFFFFFFu, tsum);
-        if (!kInterior) tcross = __reduce_add_sync(0xFFFFFFFFu, tcross);
+        tcross = __reduce_add_sync(0xFFFFFFFFu, tcross);
         if (lane == 0 && (tsum | tcross)) {
             atomicAdd(&s_sum[s], (unsigned long long)tsum);
-            if (!kInterior) atomicAdd(&s_cross[s], (unsigned long long)tcross);
+            atomicAdd(&s_cross[s], (unsigned long long)tcross);
         }
     }
+}
+
+// The k fused steps of an interior warp-tile: no car of the tile can reach
+// cell L-1 within the launch (the tile does not wrap round the ring and its
+// last car, moving at most vmax a step, stays below L), so every leader lies
+// ahead of its car in plain cell order, no car crosses L-1 -> 0 and the step
+// needs no modular arithmetic and no crossing count.  The tile is full:
+// every lane is all-owned or all-halo.  Lane 31's last car is halo whose
+// result is discarded (its leader is its own lane's first car); its
+// velocity stays <= vmax, which keeps its moves inside the bound the
+// interior test assumes.
+//
+// Two rewrites of the same step keep the per-car work small: during the
+// loop the velocity registers hold w = v + 1, so rule 1's increment is
+// carried from the previous step (the move adds w' - 1 = v'); and a lane's
+// velocity sum at a step is the growth of the sum of its cars' positions,
+// taken mod 2^32 (the true value, at most R x 127, is far below 2^32).
+template <int R, Draw D>
+__device__ __forceinline__ void agent_interior_steps(const AgentStep &a, uint32_t (&x)[R], uint32_t (&v)[R],
+                                                     uint32_t n_own, unsigned long long *s_sum)
+{
+    static_assert(R % 2 == 0, "positions are summed in pairs");
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t vmax = a.rc.vmax;
+    const uint32_t thr = (uint32_t)a.rc.thr;
+    uint32_t X = 0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) X += x[r];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] += 1u;
+    for (int s = 0; s < a.ksteps; ++s) {
+        const uint32_t step = a.step0 + (uint32_t)s;
+        const uint32_t lead_last = __shfl_down_sync(0xFFFFFFFFu, x[0], 1);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const uint32_t xi = x[r];
+            const uint32_t lead = (r + 1 < R) ? x[r + 1] : lead_last;
+            const uint32_t gap = lead - xi - 1u;
+            const uint32_t vel = min(min(v[r], vmax), gap);                         // rules 1, 2
+            bool slow = false;                                                        // rule 3
+            if (D == Draw::kAlways) {
+                slow = vel > 0u;
+            } else if (D == Draw::kPhilox) {
+                const uint32_t u = philox_word0(xi, step, a.rc.road, kTagSlowdown, a.rc.key0, a.rc.key1);
+                slow = vel > 0u && u < thr;
+            }
+            const uint32_t w = vel + (slow ? 0u : 1u);                                // v' + 1
+            x[r] = xi + w - 1u;                                                       // rule 4
+            v[r] = w;
+            NASCH_DCHECK(xi + w - 1u < a.rc.L, kDbgAgentPosition);
+            NASCH_DCHECK(w <= vmax + 1u, kDbgAgentVelocity);
+        }
+        uint32_t Xn = 0;
+#pragma unroll
+        for (int r = 0; r < R; r += 2) Xn = Xn + x[r] + x[r + 1];
+        uint32_t tsum = Xn - X;
+        X = Xn;
+        if (n_own == 0u) tsum = 0u;   // halo lanes
+        tsum = __reduce_add_sync(0xFFFFFFFFu, tsum);
+        if (lane == 0 && tsum) atomicAdd(&s_sum[s], (unsigned long long)tsum);
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] -= 1u;
 }
 
 // One warp-tile: 32 lanes x R consecutive cars in registers.  kFull: the
@@ -160,10 +213,10 @@ __device__ __forceinline__ void agent_warp_tile(const AgentStep &a, uint32_t t0,
         const uint32_t last = __shfl_sync(0xFFFFFFFFu, x[R - 1], 31);
         interior = first <= last && last + (uint32_t)a.ksteps * a.rc.vmax < a.rc.L;
     }
-    if (interior)
-        agent_tile_steps<R, D, kFull, true>(a, x, v, n_own, s_sum, s_cross);
+    if (kFull && interior)
+        agent_interior_steps<R, D>(a, x, v, n_own, s_sum);
     else
-        agent_tile_steps<R, D, kFull, false>(a, x, v, n_own, s_sum, s_cross);
+        agent_tile_steps<R, D, kFull>(a, x, v, n_own, s_sum, s_cross);
 
     if (n_own == (uint32_t)R) {
         store_cars_vec<R>(a.x_out, a.v_out, t0 + e0, x, v);
