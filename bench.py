@@ -192,10 +192,6 @@ def kernel_source_hash(kernel: str) -> str:
 # sources (comments and layout aside) when it was captured: a changed kernel
 # reports null until it is captured again.
 NCU_TRAFFIC: dict[str, dict] = {
-    "agent_tiled_k16": {"source_hash": "472ddfb61da9947b", "captured_bytes": 167843328 + 121984768,
-                        "scale": 4, "bytes_per_launch": 4 * (167843328 + 121984768)},
-    "grid_k1": {"source_hash": "d50aa3fbc0fa5eb9", "captured_bytes": 268510720 + 219135488,
-                "scale": 8, "bytes_per_launch": 8 * (268510720 + 219135488)},
 }
 
 

@@ -26,10 +26,10 @@ namespace nasch {
 namespace {
 
 // Persistent grid of independent warps; warp w takes warp-tiles w, w + W, ...
-template <int R, Draw D>
-__global__ void __launch_bounds__(kAgentThreads, kAgentBlocksPerSm) agent_tiled_kernel(const AgentStep a,
-                                                                                       const uint32_t owned,
-                                                                                       const uint32_t n_tiles)
+template <int R, Draw D, int kMinBlocks>
+__global__ void __launch_bounds__(kAgentThreads, kMinBlocks) agent_tiled_kernel(const AgentStep a,
+                                                                                const uint32_t owned,
+                                                                                const uint32_t n_tiles)
 {
     __shared__ unsigned long long s_sum[kMaxFusedSteps];
     __shared__ unsigned long long s_cross[kMaxFusedSteps];
@@ -89,27 +89,35 @@ __global__ void philox_test_kernel(const uint32_t *__restrict__ ctr, uint32_t k0
 
 }  // namespace
 
-int agent_tiled_blocks_per_sm()
+template <int kMinBlocks>
+static int occupancy_of()
 {
     int n = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &n, agent_tiled_kernel<kAgentCarsPerThread, Draw::kPhilox>, kAgentThreads, 0) != cudaSuccess)
+            &n, agent_tiled_kernel<kAgentCarsPerThread, Draw::kPhilox, kMinBlocks>, kAgentThreads, 0) != cudaSuccess)
         return 1;
     return n > 0 ? n : 1;
 }
 
-template <int R>
+int agent_tiled_blocks_per_sm(int ksteps)
+{
+    static const int deep = occupancy_of<kAgentBlocksPerSm>();
+    static const int shallow = occupancy_of<kAgentBlocksPerSmShallow>();
+    return ksteps >= kAgentDeepSteps ? deep : shallow;
+}
+
+template <int R, int kMinBlocks>
 static void launch_agent_r(const AgentStep &a, uint32_t owned, uint32_t n_tiles, int grid, cudaStream_t s)
 {
     if (a.rc.thr == 0)
-        agent_tiled_kernel<R, Draw::kNever><<<grid, kAgentThreads, 0, s>>>(a, owned, n_tiles);
+        agent_tiled_kernel<R, Draw::kNever, kMinBlocks><<<grid, kAgentThreads, 0, s>>>(a, owned, n_tiles);
     else if (a.rc.thr > 0xFFFFFFFFull)
-        agent_tiled_kernel<R, Draw::kAlways><<<grid, kAgentThreads, 0, s>>>(a, owned, n_tiles);
+        agent_tiled_kernel<R, Draw::kAlways, kMinBlocks><<<grid, kAgentThreads, 0, s>>>(a, owned, n_tiles);
     else
-        agent_tiled_kernel<R, Draw::kPhilox><<<grid, kAgentThreads, 0, s>>>(a, owned, n_tiles);
+        agent_tiled_kernel<R, Draw::kPhilox, kMinBlocks><<<grid, kAgentThreads, 0, s>>>(a, owned, n_tiles);
 }
 
-cudaError_t launch_agent_tiled(const AgentStep &a, int span, int blocks, cudaStream_t s)
+cudaError_t launch_agent_tiled(const AgentStep &a, int span, int sms, cudaStream_t s)
 {
     if (a.N == 0 || a.ksteps <= 0) return cudaSuccess;
     if (a.ksteps > kMaxFusedSteps) return cudaErrorInvalidValue;
@@ -118,11 +126,16 @@ cudaError_t launch_agent_tiled(const AgentStep &a, int span, int blocks, cudaStr
     const uint32_t n_tiles = (a.N + owned - 1) / owned;
     const uint32_t warps_per_block = kAgentThreads / 32;
     const uint32_t need = (n_tiles + warps_per_block - 1) / warps_per_block;
-    const int grid = (int)((uint32_t)blocks < need ? (uint32_t)blocks : need);
-    if (span == kAgentTileSpan)
-        launch_agent_r<kAgentCarsPerThread>(a, owned, n_tiles, grid, s);
-    else
-        launch_agent_r<8>(a, owned, n_tiles, grid, s);
+    const uint32_t blocks = (uint32_t)sms * (uint32_t)agent_tiled_blocks_per_sm(a.ksteps);
+    const int grid = (int)(blocks < need ? blocks : need);
+    const bool deep = a.ksteps >= kAgentDeepSteps;
+    if (span == kAgentTileSpan) {
+        if (deep) launch_agent_r<kAgentCarsPerThread, kAgentBlocksPerSm>(a, owned, n_tiles, grid, s);
+        else launch_agent_r<kAgentCarsPerThread, kAgentBlocksPerSmShallow>(a, owned, n_tiles, grid, s);
+    } else {
+        if (deep) launch_agent_r<8, kAgentBlocksPerSm>(a, owned, n_tiles, grid, s);
+        else launch_agent_r<8, kAgentBlocksPerSmShallow>(a, owned, n_tiles, grid, s);
+    }
     return cudaGetLastError();
 }
 

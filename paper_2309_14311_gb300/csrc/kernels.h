@@ -17,7 +17,13 @@ constexpr int kMaxFusedSteps = 64;
 // round_up(k, R) are look-ahead halo; blocks of 128 threads (4 independent
 // warps).
 constexpr int kAgentThreads = 128;
-constexpr int kAgentBlocksPerSm = 3;   // register budget: 3 blocks of 128 threads per SM
+// Register budget by fusion depth: launches of at least kAgentDeepSteps
+// steps are bound by the Philox multiplies and run fastest at 3 blocks of
+// 128 threads per SM (up to 168 registers); shallower launches move more
+// bytes per car-step and gain from the fourth block's warps (127 registers).
+constexpr int kAgentDeepSteps = 8;
+constexpr int kAgentBlocksPerSm = 3;          // ksteps >= kAgentDeepSteps
+constexpr int kAgentBlocksPerSmShallow = 4;   // ksteps < kAgentDeepSteps
 constexpr int kAgentCarsPerThread = 16;
 constexpr int kAgentTileSpan = 32 * kAgentCarsPerThread;
 constexpr int kAgentTileSpanSmall = 32 * 8;
@@ -97,13 +103,15 @@ unsigned int debug_word_open();
 unsigned int debug_word_batch();
 unsigned int debug_word_segment();
 
-int agent_tiled_blocks_per_sm();
+// Resident blocks per SM of the agent tiled kernel for launches of `ksteps` steps.
+int agent_tiled_blocks_per_sm(int ksteps);
 int grid_tiled_blocks_per_sm();
 // Bytes of GridStep::list_scratch a launch of the fused grid kernel needs on
 // the current device (0 if the occupancy query fails).
 size_t grid_list_scratch_bytes();
 
-cudaError_t launch_agent_tiled(const AgentStep &a, int span, int blocks, cudaStream_t s);
+// A persistent grid of sms x agent_tiled_blocks_per_sm(a.ksteps) blocks at most.
+cudaError_t launch_agent_tiled(const AgentStep &a, int span, int sms, cudaStream_t s);
 cudaError_t launch_agent_ring(const AgentStep &a, cudaStream_t s);
 cudaError_t launch_grid_tiled(const GridStep &g, int blocks, cudaStream_t s);
 cudaError_t launch_grid_ring(const GridStep &g, cudaStream_t s);

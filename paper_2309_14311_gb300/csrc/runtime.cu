@@ -465,7 +465,7 @@ int run_steps(nasch_road *h, int64_t steps)
                 a.ksteps = kk;
                 a.sum_v = sum + done;
                 a.crossings = cross + done;
-                e = launch_agent_tiled(a, h->tile, h->blocks, h->stream);
+                e = launch_agent_tiled(a, h->tile, h->sms, h->stream);
                 if (e != cudaSuccess) return cuda_fail(e, "agent tiled kernel");
                 h->cur ^= 1;
                 done += kk;
@@ -560,7 +560,7 @@ int create_road(const nasch_params *prm, bool open, uint64_t thr_entry, uint64_t
         h->ring = prm->tile == 0 && h->N <= kAgentRingMaxCars;
         h->tile = prm->tile ? prm->tile : kAgentTileSpan;
         h->k = prm->k ? prm->k : 16;   // fastest on the large road (the Philox multiplies bound every k >= 8)
-        h->blocks = h->sms * agent_tiled_blocks_per_sm();
+        h->blocks = h->sms * agent_tiled_blocks_per_sm(h->k);
         const size_t n = (size_t)std::max<int64_t>(h->N, 1);
         e = cudaSuccess;
         for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
