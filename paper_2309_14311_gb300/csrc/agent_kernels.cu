@@ -26,11 +26,14 @@ namespace nasch {
 namespace {
 
 // Persistent grid of independent warps; warp w takes warp-tiles w, w + W, ...
+// Launches of at least kAgentDeepSteps steps (kMinBlocks = kAgentBlocksPerSm)
+// step interior tiles in the carried form, shallower ones in plain cell order.
 template <int R, Draw D, int kMinBlocks>
 __global__ void __launch_bounds__(kAgentThreads, kMinBlocks) agent_tiled_kernel(const AgentStep a,
                                                                                 const uint32_t owned,
                                                                                 const uint32_t n_tiles)
 {
+    constexpr bool kCarry = kMinBlocks == kAgentBlocksPerSm;
     __shared__ unsigned long long s_sum[kMaxFusedSteps];
     __shared__ unsigned long long s_cross[kMaxFusedSteps];
     for (int i = threadIdx.x; i < a.ksteps; i += blockDim.x) {
@@ -44,9 +47,9 @@ __global__ void __launch_bounds__(kAgentThreads, kMinBlocks) agent_tiled_kernel(
     for (uint32_t tile = blockIdx.x * warps_per_block + (threadIdx.x >> 5); tile < n_tiles; tile += n_warps) {
         const uint32_t t0 = tile * owned;
         if (t0 + kSpan <= a.N)
-            agent_warp_tile<R, D, true>(a, t0, owned, s_sum, s_cross);
+            agent_warp_tile<R, D, true, kCarry>(a, t0, owned, s_sum, s_cross);
         else
-            agent_warp_tile<R, D, false>(a, t0, owned, s_sum, s_cross);
+            agent_warp_tile<R, D, false, kCarry>(a, t0, owned, s_sum, s_cross);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < a.ksteps; i += blockDim.x) {

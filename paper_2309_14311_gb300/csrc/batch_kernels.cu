@@ -55,9 +55,9 @@ __device__ __forceinline__ void batch_agent_tile(const BatchRoadDev &rd, const R
         const uint32_t t0 = ((item_tile * (uint32_t)(kBatchThreads / 32) + warp) * kBatchWarpTilesPerWarp + w2) * owned;
         if (t0 >= rd.N) return;
         if (t0 + kBatchAgentSpan <= rd.N)
-            agent_warp_tile<kBatchAgentTileR, D, true>(a, t0, owned, s_sum, s_cross);
+            agent_warp_tile<kBatchAgentTileR, D, true, true>(a, t0, owned, s_sum, s_cross);
         else
-            agent_warp_tile<kBatchAgentTileR, D, false>(a, t0, owned, s_sum, s_cross);
+            agent_warp_tile<kBatchAgentTileR, D, false, true>(a, t0, owned, s_sum, s_cross);
     }
 }
 

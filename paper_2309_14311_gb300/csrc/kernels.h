@@ -24,6 +24,7 @@ constexpr int kAgentThreads = 128;
 constexpr int kAgentDeepSteps = 8;
 constexpr int kAgentBlocksPerSm = 3;          // ksteps >= kAgentDeepSteps
 constexpr int kAgentBlocksPerSmShallow = 4;   // ksteps < kAgentDeepSteps
+static_assert(kAgentBlocksPerSm != kAgentBlocksPerSmShallow, "the budget names the launch's form");
 constexpr int kAgentCarsPerThread = 16;
 constexpr int kAgentTileSpan = 32 * kAgentCarsPerThread;
 constexpr int kAgentTileSpanSmall = 32 * 8;

@@ -63,9 +63,11 @@ enum class Draw { kNever, kAlways, kPhilox };
 
 __host__ __device__ __forceinline__ Draw draw_mode(uint64_t thr) { return thr == 0 ? Draw::kNever : (thr > 0xFFFFFFFFull ? Draw::kAlways : Draw::kPhilox); }
 
-// The k fused steps of one warp-tile held in registers (32 lanes x R cars),
-// on the ring: the gap is taken modulo L and cars crossing L-1 -> 0 wrap.
-template <int R, Draw D, bool kFull>
+// The k fused steps of one warp-tile held in registers (32 lanes x R cars).
+// On the ring (kInterior false) the gap is taken modulo L and cars crossing
+// L-1 -> 0 wrap.  kInterior: the tile is interior (agent_interior_steps
+// states the condition) and steps in plain cell order, with no crossings.
+template <int R, Draw D, bool kFull, bool kInterior>
 __device__ __forceinline__ void agent_tile_steps(const AgentStep &a, uint32_t (&x)[R], uint32_t (&v)[R],
                                                  uint32_t n_own, unsigned long long *s_sum,
                                                  unsigned long long *s_cross)
@@ -87,7 +89,7 @@ __device__ __forceinline__ void agent_tile_steps(const AgentStep &a, uint32_t (&
             // empty cells ahead: (lead - x - 1) mod L, or L - 1 if the car is
             // its own leader; on the ring as the smaller of two unsigned values
             const uint32_t d = lead - xi;
-            const uint32_t gap = min(d - 1u, d + Lm1);
+            const uint32_t gap = kInterior ? d - 1u : min(d - 1u, d + Lm1);
             uint32_t vel = min(min(v[r] + 1u, vmax), gap);            // rules 1, 2
             if (D == Draw::kAlways) {
                 vel -= vel > 0u ? 1u : 0u;                              // rule 3, p = 1
@@ -96,23 +98,26 @@ __device__ __forceinline__ void agent_tile_steps(const AgentStep &a, uint32_t (&
                 vel -= (vel > 0u && u < thr) ? 1u : 0u;                 // rule 3
             }
             uint32_t nx = xi + vel;                                     // rule 4
-            const bool wrap = nx >= L;
-            nx = wrap ? nx - L : nx;
+            bool wrap = false;
+            if (!kInterior) {
+                wrap = nx >= L;
+                nx = wrap ? nx - L : nx;
+            }
             NASCH_DCHECK(nx < L, kDbgAgentPosition);
             NASCH_DCHECK(vel <= vmax, kDbgAgentVelocity);
             x[r] = nx;
             v[r] = vel;
             if (kFull || (uint32_t)r < n_own) {
                 tsum += vel;
-                tcross += wrap ? 1u : 0u;
+                if (!kInterior) tcross += wrap ? 1u : 0u;
             }
         }
         if (kFull && n_own == 0u) tsum = tcross = 0u;   // halo lanes
         tsum = __reduce_add_sync(0xFFFFFFFFu, tsum);
-        tcross = __reduce_add_sync(0xFFFFFFFFu, tcross);
+        if (!kInterior) tcross = __reduce_add_sync(0xFFFFFFFFu, tcross);
         if (lane == 0 && (tsum | tcross)) {
             atomicAdd(&s_sum[s], (unsigned long long)tsum);
-            atomicAdd(&s_cross[s], (unsigned long long)tcross);
+            if (!kInterior) atomicAdd(&s_cross[s], (unsigned long long)tcross);
         }
     }
 }
@@ -132,6 +137,9 @@ __device__ __forceinline__ void agent_tile_steps(const AgentStep &a, uint32_t (&
 // carried from the previous step (the move adds w' - 1 = v'); and a lane's
 // velocity sum at a step is the growth of the sum of its cars' positions,
 // taken mod 2^32 (the true value, at most R x 127, is far below 2^32).
+// They cost a few operations per car at the launch's start and end, which
+// launches of few steps do not win back (agent_tile_steps with kInterior
+// serves those).
 template <int R, Draw D>
 __device__ __forceinline__ void agent_interior_steps(const AgentStep &a, uint32_t (&x)[R], uint32_t (&v)[R],
                                                      uint32_t n_own, unsigned long long *s_sum)
@@ -183,7 +191,9 @@ __device__ __forceinline__ void agent_interior_steps(const AgentStep &a, uint32_
 // One warp-tile: 32 lanes x R consecutive cars in registers.  kFull: the
 // tile lies inside [0, N) and every owned car of a lane is owned (lanes are
 // either all-owned or all-halo), so no per-car ownership test is needed.
-template <int R, Draw D, bool kFull>
+// kCarry: an interior tile steps by agent_interior_steps (for launches of
+// many steps), else by agent_tile_steps in plain cell order.
+template <int R, Draw D, bool kFull, bool kCarry>
 __device__ __forceinline__ void agent_warp_tile(const AgentStep &a, uint32_t t0, uint32_t owned,
                                                 unsigned long long *s_sum, unsigned long long *s_cross)
 {
@@ -213,10 +223,14 @@ __device__ __forceinline__ void agent_warp_tile(const AgentStep &a, uint32_t t0,
         const uint32_t last = __shfl_sync(0xFFFFFFFFu, x[R - 1], 31);
         interior = first <= last && last + (uint32_t)a.ksteps * a.rc.vmax < a.rc.L;
     }
-    if (kFull && interior)
-        agent_interior_steps<R, D>(a, x, v, n_own, s_sum);
-    else
-        agent_tile_steps<R, D, kFull>(a, x, v, n_own, s_sum, s_cross);
+    if (kFull && interior) {
+        if (kCarry)
+            agent_interior_steps<R, D>(a, x, v, n_own, s_sum);
+        else
+            agent_tile_steps<R, D, true, true>(a, x, v, n_own, s_sum, s_cross);
+    } else {
+        agent_tile_steps<R, D, kFull, false>(a, x, v, n_own, s_sum, s_cross);
+    }
 
     if (n_own == (uint32_t)R) {
         store_cars_vec<R>(a.x_out, a.v_out, t0 + e0, x, v);
