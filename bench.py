@@ -311,13 +311,14 @@ def run_reference(args):
 # The agent step is bound by the SM's heavy integer-multiply pipe
 # (fmaheavy), which runs Philox4x32-10's 32x32->64 products.  Per SM it
 # takes 4 schedulers x 16 lanes = 64 lane-slots per clock; a 32x32->64
-# product (IMAD.WIDE) occupies two slots, a high half alone one (the ncu
-# pipe counters fit this: busy cycles = 2 x wide + 1 x narrow instructions,
-# per 16 lanes).  Algorithmic work of one car-step: word 0 of Philox with
-# counter (cell, step, road, 0) needs 16 wide products (rounds 1-9, less the
-# product of the launch-constant road word in round 1 and of the
-# step-constant word 0 in round 2) and one high half (round 10) = 33
-# lane-slots; the rules, the move and the statistics need none.
+# product (IMAD.WIDE) occupies two slots, and so does a high half alone; a
+# low half, an add or a move one (the ncu pipe counters fit these weights).
+# Algorithmic work of one car-step: word 0 of Philox with counter (cell,
+# step, road, 0) needs 13 wide products (rounds 1-7, less the product of the
+# launch-constant road word in round 1 and of the step-constant word 0 in
+# round 2, and round 8's word-0 product), 3 high halves (rounds 8, 9, 10)
+# and 1 low half (round 9) = 26 + 6 + 1 = 33 lane-slots; the rules, the
+# move and the statistics need none.
 HEAVY_SLOTS_PER_CAR_STEP = 33
 HEAVY_SLOTS_PER_SM_CLOCK = 64
 # Algorithmic integer instructions of one car-step (issue view, kept beside
