@@ -166,8 +166,7 @@ __global__ void __launch_bounds__(kGridThreads) grid_tiled_kernel(const GridStep
 // (beyond the span) but moves only further right.  The last owned car sees
 // its leader, or the dummy at least vmax cells ahead.
 // Two buffers alternate: the tile being stepped and the next tile, whose
-// copy is issued as soon as the tile's car count shows it is stepped in
-// place and the tile before has been read by its store.  The
+// copy is issued once the tile before has been read by its store.  The
 // rule-3 draw uses the counter-independent parts of Philox computed on the
 // host (SlowdownKey).
 // Open (an open road, cells 0..L-1): cells off the road read as empty, a
@@ -341,15 +340,7 @@ __global__ void __launch_bounds__(32 * kK1Warps) grid_k1_kernel(const GridStep g
         // store of the tile before has read it) and the next copy waits
         const bool dense = total > kK1ListCap;   // warp-uniform
         int8_t *out = span;
-        if (!dense) {
-            // the tile is stepped in place: copy the next tile into the other
-            // buffer as soon as the store of the tile before has read it
-            if (lane == 0) {
-                bulk_wait_read_all();
-                const uint32_t nx = tile + nw;
-                if (nx < n_tiles && bulk_ok(nx)) issue_load(nx, bn);
-            }
-        } else {
+        if (dense) {
             if (lane == 0) bulk_wait_read_all();
             __syncwarp();
             out = w.buf[bn];
@@ -375,6 +366,16 @@ __global__ void __launch_bounds__(32 * kK1Warps) grid_k1_kernel(const GridStep g
             // (a pass before the last is a whole number of groups, its leader entry a car)
             if (chunk + count == total && lane <= padded - count) w.list[count + lane] = (uint16_t)kK1Dummy;
             __syncwarp();
+            if (!dense) {
+                // every car is listed: copy the next tile into the other
+                // buffer once the store of the tile before has read it
+                if (lane == 0) {
+                    bulk_wait_read_all();
+                    const uint32_t nx = tile + nw;
+                    if (nx < n_tiles && bulk_ok(nx)) issue_load(nx, bn);
+                }
+                __syncwarp();
+            }
             // 3. the cars, 32 at a time, three groups interleaved
             if (wraps)
                 k1_cars<D, true>(w.list, padded, lane, span, out, base, L, vmax, thr, sk, own, tsum, tcross);
