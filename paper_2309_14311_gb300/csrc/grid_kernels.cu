@@ -182,7 +182,7 @@ constexpr uint32_t kK1Buf = kK1Span + 32u;               // + padding: the dummy
 constexpr uint32_t kK1ListCap = 112u * kK1Words / 32u * 32u;   // cars per pass; a denser tile is done in passes
 constexpr uint32_t kK1ListLen = kK1ListCap + 32u;        // + padding to whole groups and one leader
 constexpr uint32_t kK1Dummy = kK1Span;                   // span index of the dummy cars (padding)
-constexpr uint32_t kK1Bufs = 2;
+constexpr uint32_t kK1Bufs = 3;                          // buffers per warp: the tile stepped and the copies ahead
 constexpr int8_t kEmptyCell = -1;
 constexpr int kK1Warps = 4;                              // warps per block
 static_assert(kK1ListCap % 32u == 0u, "whole groups");
@@ -277,12 +277,23 @@ __global__ void __launch_bounds__(32 * kK1Warps) grid_k1_kernel(const GridStep g
         bulk_load(w.buf[b], g.c_in + (t * kK1Cells - kK1Halo), kK1Span, &w.full[b]);
     };
     uint32_t tile = blockIdx.x * (uint32_t)kK1Warps + warp;
-    if (lane == 0 && tile < n_tiles && bulk_ok(tile)) issue_load(tile, 0);
+    // the ring of buffers: this warp's n-th tile goes to buffer n mod kK1Bufs,
+    // and the copies of the next kK1Bufs - 1 tiles are in flight while a tile
+    // is stepped
+    uint32_t pending = 0;                // lane 0: bit b, a copy into buffer b not yet waited for
+    if (lane == 0)
+        for (uint32_t b = 0; b + 1u < kK1Bufs; ++b) {
+            const uint32_t t = tile + b * nw;
+            if (t < n_tiles && bulk_ok(t)) {
+                issue_load(t, b);
+                pending |= 1u << b;
+            }
+        }
     uint32_t parity = 0;                 // bit b: phase parity of full[b]
     uint32_t bi = 0;                     // buffer of the tile being stepped
     uint32_t tsum = 0, tcross = 0;       // statistics of this lane's cars
     for (; tile < n_tiles; tile += nw) {
-        const uint32_t bn = bi ^ 1u;     // the other buffer: the next tile, or a dense tile's result
+        const uint32_t bp = bi == 0u ? kK1Bufs - 1u : bi - 1u;   // the tile before's buffer: the copy ahead goes there
         int8_t *span = w.buf[bi];
         const uint32_t t0 = tile * kK1Cells;
         const uint32_t own = min(kK1Cells, L - t0);
@@ -290,7 +301,10 @@ __global__ void __launch_bounds__(32 * kK1Warps) grid_k1_kernel(const GridStep g
         const uint32_t base = Open ? t0 - kK1Halo : (t0 >= kK1Halo ? t0 - kK1Halo : t0 + L - kK1Halo);
         bool ok = true;
         if (bulk_ok(tile)) {
-            if (lane == 0) ok = mbar_wait_bounded(&w.full[bi], (parity >> bi) & 1u);
+            if (lane == 0) {
+                ok = mbar_wait_bounded(&w.full[bi], (parity >> bi) & 1u);
+                if (ok) pending &= ~(1u << bi);
+            }
             parity ^= 1u << bi;
         } else {
             for (uint32_t i = lane; i < kK1Span; i += 32u) {
@@ -311,6 +325,9 @@ __global__ void __launch_bounds__(32 * kK1Warps) grid_k1_kernel(const GridStep g
         if (!__all_sync(0xFFFFFFFFu, ok)) {
             if (lane == 0) {
                 atomicOr(g.status, kStatusTimeout);
+                // let the other copies in flight land (bounded) before the block's memory is released
+                for (uint32_t b = 0; b < kK1Bufs; ++b)
+                    if (b != bi && (pending >> b & 1u)) mbar_wait_bounded(&w.full[b], (parity >> b) & 1u);
                 bulk_wait_all();
             }
             break;
@@ -335,18 +352,10 @@ __global__ void __launch_bounds__(32 * kK1Warps) grid_k1_kernel(const GridStep g
         }
         const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
         const bool wraps = base + kK1Buf > L;   // the span holds cell L - 1: crossings possible
-        // a tile with more cars than the list holds is listed in passes from
-        // the intact span, so its result goes to the other buffer (once the
-        // store of the tile before has read it) and the next copy waits
+        // a tile with more cars than the list holds is listed and stepped in
+        // passes (in cell order, in place: a pass's cars read only their own
+        // cells, which no car of an earlier pass writes)
         const bool dense = total > kK1ListCap;   // warp-uniform
-        int8_t *out = span;
-        if (dense) {
-            if (lane == 0) bulk_wait_read_all();
-            __syncwarp();
-            out = w.buf[bn];
-#pragma unroll
-            for (uint32_t k = 0; k < 2u * kK1Words; ++k) reinterpret_cast<uint4 *>(out)[lane + 32u * k] = kEmpty4;
-        }
         for (uint32_t chunk = 0; chunk == 0u || chunk < total; chunk += kK1ListCap) {
             const uint32_t count = total > chunk ? min(kK1ListCap, total - chunk) : 0u;
             const uint32_t padded = (count + 31u) & ~31u;
@@ -366,46 +375,39 @@ __global__ void __launch_bounds__(32 * kK1Warps) grid_k1_kernel(const GridStep g
             // (a pass before the last is a whole number of groups, its leader entry a car)
             if (chunk + count == total && lane <= padded - count) w.list[count + lane] = (uint16_t)kK1Dummy;
             __syncwarp();
-            if (!dense) {
-                // every car is listed: copy the next tile into the other
-                // buffer once the store of the tile before has read it
-                if (lane == 0) {
-                    bulk_wait_read_all();
-                    const uint32_t nx = tile + nw;
-                    if (nx < n_tiles && bulk_ok(nx)) issue_load(nx, bn);
+            if (chunk == 0u && lane == 0) {
+                // the copy kK1Bufs - 1 tiles ahead, into the tile before's
+                // buffer once its store has read it
+                bulk_wait_read_all();
+                const uint32_t nx = tile + (kK1Bufs - 1u) * nw;
+                if (nx < n_tiles && bulk_ok(nx)) {
+                    issue_load(nx, bp);
+                    pending |= 1u << bp;
                 }
-                __syncwarp();
             }
             // 3. the cars, 32 at a time, three groups interleaved
             if (wraps)
-                k1_cars<D, true>(w.list, padded, lane, span, out, base, L, vmax, thr, sk, own, tsum, tcross);
+                k1_cars<D, true>(w.list, padded, lane, span, span, base, L, vmax, thr, sk, own, tsum, tcross);
             else
-                k1_cars<D, false>(w.list, padded, lane, span, out, base, L, vmax, thr, sk, own, tsum, tcross);
+                k1_cars<D, false>(w.list, padded, lane, span, span, base, L, vmax, thr, sk, own, tsum, tcross);
             __syncwarp();   // the list is rewritten by the next pass
         }
         if (Open && entry && tile == 0) {   // a car enters cell 0 at rest
             __syncwarp();
-            if (lane == 0 && out[kK1Halo] < 0) out[kK1Halo] = 0;
+            if (lane == 0 && span[kK1Halo] < 0) span[kK1Halo] = 0;
         }
         // 4. the result leaves by bulk store (or plain stores for a short last tile)
         fence_proxy_async();
         __syncwarp();
         if (own == kK1Cells) {
             if (lane == 0) {
-                bulk_store(g.c_out + t0, out + kK1Halo, kK1Cells);
+                bulk_store(g.c_out + t0, span + kK1Halo, kK1Cells);
                 bulk_commit();
             }
         } else {
-            for (uint32_t i = lane; i < own; i += 32u) g.c_out[t0 + i] = out[kK1Halo + i];
+            for (uint32_t i = lane; i < own; i += 32u) g.c_out[t0 + i] = span[kK1Halo + i];
         }
-        if (dense) {   // the span is free: the next tile goes there
-            if (lane == 0) {
-                const uint32_t nx = tile + nw;
-                if (nx < n_tiles && bulk_ok(nx)) issue_load(nx, bi);
-            }
-        } else {
-            bi = bn;
-        }
+        bi = bi + 1u == kK1Bufs ? 0u : bi + 1u;
     }
     if (lane == 0) bulk_wait_all();
     unsigned long long acc_sum = tsum, acc_cross = tcross;

@@ -103,8 +103,8 @@ __device__ __forceinline__ void agent_tile_steps(const AgentStep &a, uint32_t (&
                 wrap = nx >= L;
                 nx = wrap ? nx - L : nx;
             }
-            NASCH_DCHECK(nx < L, kDbgAgentPosition);
-            NASCH_DCHECK(vel <= vmax, kDbgAgentVelocity);
+            (void)NASCH_DCHECK(nx < L, kDbgAgentPosition);
+            (void)NASCH_DCHECK(vel <= vmax, kDbgAgentVelocity);
             x[r] = nx;
             v[r] = vel;
             if (kFull || (uint32_t)r < n_own) {
@@ -172,8 +172,8 @@ __device__ __forceinline__ void agent_interior_steps(const AgentStep &a, uint32_
             const uint32_t w = vel + (slow ? 0u : 1u);                                // v' + 1
             x[r] = xi + w - 1u;                                                       // rule 4
             v[r] = w;
-            NASCH_DCHECK(xi + w - 1u < a.rc.L, kDbgAgentPosition);
-            NASCH_DCHECK(w <= vmax + 1u, kDbgAgentVelocity);
+            (void)NASCH_DCHECK(xi + w - 1u < a.rc.L, kDbgAgentPosition);
+            (void)NASCH_DCHECK(w <= vmax + 1u, kDbgAgentVelocity);
         }
         uint32_t Xn = 0;
 #pragma unroll
@@ -409,7 +409,7 @@ __device__ __forceinline__ void warp_list_groups(uint16_t *pos, uint8_t *vel, ui
             vq -= (vq != 0u && u < thr) ? 1u : 0u;                                 // rule 3
         }
         const uint32_t i = i0 + 32u * (uint32_t)q;
-        NASCH_DCHECK(vq <= vmax, kDbgListVelocity);
+        (void)NASCH_DCHECK(vq <= vmax, kDbgListVelocity);
         pos[i] = (uint16_t)(x[q] + vq);                                            // rule 4
         vel[i] = (uint8_t)vq;
         const bool mine = x[q] - H < own;

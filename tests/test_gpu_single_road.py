@@ -165,6 +165,28 @@ def test_grid_one_step_matches_oracle(L, N, vmax, p, T):
     assert_same(lib, orc, L, "grid")
 
 
+def test_grid_one_step_many_tiles_per_warp_mixed_density():
+    """The one-step kernel over enough tiles that every warp steps many in
+    turn (its copies run ahead of the tile it steps), with dense tiles
+    (listed and stepped in passes) and sparse ones along the same ring, and
+    the ring's first and last tiles loaded across the wrap point."""
+    L = 2**26
+    rng = np.random.default_rng(77)
+    occ = np.concatenate([rng.random(L // 4) < 0.03, rng.random(L // 4) < 0.5,
+                          rng.random(L // 4) < 0.2, rng.random(L - 3 * (L // 4)) < 0.9])
+    x = np.flatnonzero(occ).astype(np.int32)
+    v = rng.integers(0, 6, x.size).astype(np.uint8)
+    cells = np.full(L, -1, np.int8)
+    cells[x] = v.astype(np.int8)
+    orc, osv, ocr = O.grid_run(cells, 5, 0.2, 3, 9, 100, 6, openmp=True)
+    with NS.Road(L, x.size, 5, 0.2, 3, 9, layout="grid", k=1) as r:
+        r.set_state(x, v, 100)
+        r.run(6)
+        sv, cr = r.stats()
+        assert np.array_equal(r.read_grid(), orc)
+    assert np.array_equal(sv, osv) and np.array_equal(cr, ocr)
+
+
 @pytest.mark.parametrize("L,N,vmax,p,T", [(200, 50, 5, 0.13, 300), (3, 2, 127, 0.5, 50), (1, 1, 3, 0.5, 5),
                                           (32768, 4000, 20, 0.3, 40), (8192, 8192, 5, 0.5, 3),
                                           (9000, 8192, 2, 0.2, 60), (500, 0, 5, 0.5, 10)])
