@@ -192,10 +192,6 @@ def kernel_source_hash(kernel: str) -> str:
 # sources (comments and layout aside) when it was captured: a changed kernel
 # reports null until it is captured again.
 NCU_TRAFFIC: dict[str, dict] = {
-    "agent_tiled_k16": {"source_hash": "6212362526103343", "captured_bytes": 167842560 + 121975040,
-                        "scale": 4, "bytes_per_launch": 4 * (167842560 + 121975040)},
-    "grid_k1": {"source_hash": "2be3ad7a8e9cda0e", "captured_bytes": 268506624 + 219117312,
-                "scale": 8, "bytes_per_launch": 8 * (268506624 + 219117312)},
 }
 
 

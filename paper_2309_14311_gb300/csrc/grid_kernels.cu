@@ -182,7 +182,7 @@ constexpr uint32_t kK1Buf = kK1Span + 32u;               // + padding: the dummy
 constexpr uint32_t kK1ListCap = 112u * kK1Words / 32u * 32u;   // cars per pass; a denser tile is done in passes
 constexpr uint32_t kK1ListLen = kK1ListCap + 32u;        // + padding to whole groups and one leader
 constexpr uint32_t kK1Dummy = kK1Span;                   // span index of the dummy cars (padding)
-constexpr uint32_t kK1Bufs = 3;                          // buffers per warp: the tile stepped and the copies ahead
+constexpr uint32_t kK1Bufs = 2;                          // buffers per warp: the tile stepped and the copy ahead (a third buffer costs more in resident warps than it gains)
 constexpr int8_t kEmptyCell = -1;
 constexpr int kK1Warps = 4;                              // warps per block
 static_assert(kK1ListCap % 32u == 0u, "whole groups");
