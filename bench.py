@@ -448,7 +448,7 @@ def run_ours(args):
     g1 = NS.Road(spec.L, spec.N, spec.vmax, spec.p, spec.seed, road_id, layout="grid", k=1, stream=stream)
     g1.run(5)
     g1.synchronize()
-    s1 = timed_device_run(g1, 1, args.k1_steps)
+    s1 = timed_device_run(g1, args.k1_steps, 1)   # k1_steps launches of one step, back to back
     b1 = GRID_BYTES_PER_CELL * spec.L
     roofline_hbm = {"bound": "hbm", "kernel": "grid_k1", "achieved": b1 * args.k1_steps / s1 / 1e9,
                     "peak": hbm_peak, "unit": "GB/s", "frac": b1 * args.k1_steps / s1 / 1e9 / hbm_peak,

@@ -157,6 +157,9 @@ struct nasch_road {
     uint64_t stats_first = 0;
     unsigned long long *d_sum = nullptr, *d_cross = nullptr;
     int64_t stats_cap = 0;
+    // slots [stats_dirty, stats_cap) of both series are zero; lower ones may
+    // hold the statistics of steps before a reset of stats_first
+    int64_t stats_dirty = 0;
     // open road (nasch_create_open): grid layout, one step per launch
     bool open = false;
     uint64_t thr_entry = 0, thr_exit = 0;
@@ -231,8 +234,11 @@ int ensure_stats(nasch_road *h, int64_t needed)
     unsigned long long *ns = nullptr, *nc = nullptr;
     cudaError_t e = cudaMalloc(&ns, (size_t)cap * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMalloc(&nc, (size_t)cap * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemsetAsync(ns, 0, (size_t)cap * sizeof(unsigned long long), h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(nc, 0, (size_t)cap * sizeof(unsigned long long), h->stream);
     if (e != cudaSuccess) {
         cudaFree(ns);
+        cudaFree(nc);
         return cuda_fail(e, "cudaMalloc(statistics)");
     }
     const int64_t used = (int64_t)(h->step - h->stats_first);
@@ -252,6 +258,7 @@ int ensure_stats(nasch_road *h, int64_t needed)
     h->d_sum = ns;
     h->d_cross = nc;
     h->stats_cap = cap;
+    h->stats_dirty = std::max<int64_t>(used, 0);
     return NASCH_OK;
 }
 
@@ -423,9 +430,14 @@ int run_steps(nasch_road *h, int64_t steps)
     if (st) return st;
     unsigned long long *sum = h->d_sum + used;
     unsigned long long *cross = h->d_cross + used;
-    cudaError_t e = cudaMemsetAsync(sum, 0, (size_t)steps * 8, h->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(cross, 0, (size_t)steps * 8, h->stream);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(statistics)");
+    cudaError_t e = cudaSuccess;
+    if (used < h->stats_dirty) {   // slots written before a reset of stats_first: clear them
+        const size_t n = (size_t)(std::min<int64_t>(h->stats_dirty, used + steps) - used) * 8;
+        e = cudaMemsetAsync(sum, 0, n, h->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(cross, 0, n, h->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(statistics)");
+    }
+    h->stats_dirty = std::max<int64_t>(h->stats_dirty, used + steps);
     const RoadConst rc = road_const(h);
 
     if (h->layout == NASCH_LAYOUT_AGENT) {

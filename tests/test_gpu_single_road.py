@@ -165,6 +165,26 @@ def test_grid_one_step_matches_oracle(L, N, vmax, p, T):
     assert_same(lib, orc, L, "grid")
 
 
+@pytest.mark.parametrize("layout,k", [("agent", 8), ("grid", 1), ("grid", 4)])
+def test_statistics_after_a_reset_and_growth(layout, k):
+    """The per-step series' slots are cleared once, not per call: after
+    set_state resets the series, slots that held the earlier steps are
+    cleared before reuse (runs below, across and past the old high mark),
+    and a series that outgrows its buffer keeps what it held."""
+    L, N, vmax, p, seed, road = 30000, 3000, 5, 0.3, 12, 4
+    x0 = O.floyd_init(L, N, seed, road)
+    v0 = np.zeros(N, np.uint8)
+    with NS.Road(L, N, vmax, p, seed, road, layout=layout, k=k, tile=8192 if layout == "grid" else 512) as r:
+        r.run(700)
+        r.set_state(x0, v0, 0)
+        for steps in (5, 300, 1500, 1):
+            r.run(steps)
+        sv, cr = r.stats()
+    _, _, osv, ocr = O.agent_run(L, x0, v0, vmax, p, seed, road, 0, 1806)
+    assert len(sv) == 1806
+    assert np.array_equal(sv, osv) and np.array_equal(cr, ocr)
+
+
 def test_grid_one_step_many_tiles_per_warp_mixed_density():
     """The one-step kernel over enough tiles that every warp steps many in
     turn (its copies run ahead of the tile it steps), with dense tiles
