@@ -252,7 +252,7 @@ __device__ __forceinline__ void k1_cars(const uint16_t *list, uint32_t padded, u
 template <Draw D, bool Open>
 __global__ void __launch_bounds__(32 * kK1Warps) grid_k1_kernel(const GridStep g, const uint32_t n_tiles,
                                                                 const SlowdownKey sk, const int exit_open,
-                                                                const int entry, const int reverse)
+                                                                const int entry)
 {
     __shared__ K1WarpSmem s_w[kK1Warps];
     const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
@@ -267,19 +267,14 @@ __global__ void __launch_bounds__(32 * kK1Warps) grid_k1_kernel(const GridStep g
     for (uint32_t b = 0; b < kK1Bufs; ++b) w.buf[b][kK1Span + lane] = kEmptyCell;   // the dummies' cells
     __syncthreads();
 
-    // Tiles are visited in road order on even steps and in reverse on odd
-    // ones, so a launch starts where the one before ended and reads the
-    // cells that launch wrote last while they are still in L2.  `t` below is
-    // a visit index; road_tile(t) is the tile of the road it stands for.
-    auto road_tile = [&](uint32_t t) { return reverse ? n_tiles - 1u - t : t; };
     auto bulk_ok = [&](uint32_t t) {
-        const uint32_t t0 = road_tile(t) * kK1Cells;
+        const uint32_t t0 = t * kK1Cells;
         return t0 >= kK1Halo && t0 + kK1Cells + kK1Halo <= L;
     };
     auto issue_load = [&](uint32_t t, uint32_t b) {   // lane 0
         fence_proxy_async();
         mbar_expect_tx(&w.full[b], kK1Span);
-        bulk_load(w.buf[b], g.c_in + (road_tile(t) * kK1Cells - kK1Halo), kK1Span, &w.full[b]);
+        bulk_load(w.buf[b], g.c_in + (t * kK1Cells - kK1Halo), kK1Span, &w.full[b]);
     };
     uint32_t tile = blockIdx.x * (uint32_t)kK1Warps + warp;
     // the ring of buffers: this warp's n-th tile goes to buffer n mod kK1Bufs,
@@ -300,7 +295,7 @@ __global__ void __launch_bounds__(32 * kK1Warps) grid_k1_kernel(const GridStep g
     for (; tile < n_tiles; tile += nw) {
         const uint32_t bp = bi == 0u ? kK1Bufs - 1u : bi - 1u;   // the tile before's buffer: the copy ahead goes there
         int8_t *span = w.buf[bi];
-        const uint32_t t0 = road_tile(tile) * kK1Cells;
+        const uint32_t t0 = tile * kK1Cells;
         const uint32_t own = min(kK1Cells, L - t0);
         // road cell of span index 0 (an open road: modulo 2^32, before the road on tile 0)
         const uint32_t base = Open ? t0 - kK1Halo : (t0 >= kK1Halo ? t0 - kK1Halo : t0 + L - kK1Halo);
@@ -397,7 +392,7 @@ __global__ void __launch_bounds__(32 * kK1Warps) grid_k1_kernel(const GridStep g
                 k1_cars<D, false>(w.list, padded, lane, span, span, base, L, vmax, thr, sk, own, tsum, tcross);
             __syncwarp();   // the list is rewritten by the next pass
         }
-        if (Open && entry && t0 == 0) {   // a car enters cell 0 at rest
+        if (Open && entry && tile == 0) {   // a car enters cell 0 at rest
             __syncwarp();
             if (lane == 0 && span[kK1Halo] < 0) span[kK1Halo] = 0;
         }
@@ -584,8 +579,7 @@ cudaError_t launch_k1_variant(const GridStep &g, uint32_t n_tiles, cudaStream_t 
     const uint32_t need = (n_tiles + (uint32_t)kK1Warps - 1u) / (uint32_t)kK1Warps;
     const int grid = (int)((uint32_t)n < need ? (uint32_t)n : need);
     const SlowdownKey sk = make_slowdown_key(g.step0, g.rc.road, g.rc.key0, g.rc.key1);
-    grid_k1_kernel<D, Open><<<grid, 32 * kK1Warps, 0, s>>>(g, n_tiles, sk, exit_open ? 1 : 0, entry ? 1 : 0,
-                                                           (int)(g.step0 & 1u));
+    grid_k1_kernel<D, Open><<<grid, 32 * kK1Warps, 0, s>>>(g, n_tiles, sk, exit_open ? 1 : 0, entry ? 1 : 0);
     return cudaGetLastError();
 }
 
