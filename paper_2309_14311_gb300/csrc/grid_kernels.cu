@@ -165,10 +165,12 @@ __global__ void __launch_bounds__(kGridThreads) grid_tiled_kernel(const GridStep
 // tile and is stepped exactly, a car in the right halo may lack its leader
 // (beyond the span) but moves only further right.  The last owned car sees
 // its leader, or the dummy at least vmax cells ahead.
-// Two buffers alternate: the tile being stepped and the next tile, whose
-// copy is issued once the tile before has been read by its store.  The
-// rule-3 draw uses the counter-independent parts of Philox computed on the
-// host (SlowdownKey).
+// A tile with more cars than the list holds is listed and stepped in passes,
+// in cell order and in place like the groups of one pass.  The warp's
+// buffers form a ring (kK1Bufs = 2: the tile being stepped and the next
+// tile), and a tile's copy is issued once the tile that last used its buffer
+// has been read by its store.  The rule-3 draw uses the counter-independent
+// parts of Philox computed on the host (SlowdownKey).
 // Open (an open road, cells 0..L-1): cells off the road read as empty, a
 // closed exit is a car standing on cell L (seen by the car behind it, never
 // written back), cars that pass cell L - 1 leave and are counted as
