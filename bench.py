@@ -194,6 +194,8 @@ def kernel_source_hash(kernel: str) -> str:
 NCU_TRAFFIC: dict[str, dict] = {
     "agent_tiled_k16": {"source_hash": "73442a51b6bf5fae", "captured_bytes": 167842816 + 122001920,
                         "scale": 4, "bytes_per_launch": 4 * (167842816 + 122001920)},
+    "grid_k1": {"source_hash": "2d862bad5c83bbfc", "captured_bytes": 268503040 + 219495680,
+                "scale": 8, "bytes_per_launch": 8 * (268503040 + 219495680)},
 }
 
 

@@ -361,25 +361,17 @@ __global__ void __launch_bounds__(32 * kK1Warps) grid_k1_kernel(const GridStep g
         for (uint32_t chunk = 0; chunk == 0u || chunk < total; chunk += kK1ListCap) {
             const uint32_t count = total > chunk ? min(kK1ListCap, total - chunk) : 0u;
             const uint32_t padded = (count + 31u) & ~31u;
-            // each word bit-reversed once: its leading zeros count to the
-            // lowest occupied cell not yet listed, which is then cleared
             uint32_t pos = incl - n;
             if (!dense) {
 #pragma unroll
                 for (uint32_t j = 0; j < kK1Words; ++j)
-                    for (uint32_t mr = __brev(m[j]); mr;) {
-                        const uint32_t b = __clz(mr);
-                        w.list[pos++] = (uint16_t)(c0 + 32u * j + b);
-                        mr ^= 0x80000000u >> b;
-                    }
+                    for (uint32_t mm = m[j]; mm; mm &= mm - 1u)
+                        w.list[pos++] = (uint16_t)(c0 + 32u * j + __clz(__brev(mm)));
             } else {   // ranks chunk .. chunk + count (the last one: the pass's leader entry)
 #pragma unroll
                 for (uint32_t j = 0; j < kK1Words; ++j)
-                    for (uint32_t mr = __brev(m[j]); mr; ++pos) {
-                        const uint32_t b = __clz(mr);
-                        if (pos - chunk <= count) w.list[pos - chunk] = (uint16_t)(c0 + 32u * j + b);
-                        mr ^= 0x80000000u >> b;
-                    }
+                    for (uint32_t mm = m[j]; mm; mm &= mm - 1u, ++pos)
+                        if (pos - chunk <= count) w.list[pos - chunk] = (uint16_t)(c0 + 32u * j + __clz(__brev(mm)));
             }
             // dummies after the last car, and the leader of the last group
             // (a pass before the last is a whole number of groups, its leader entry a car)
