@@ -24,3 +24,16 @@ def test_recorded_traffic_is_current():
     to a kernel its record is taken again or dropped."""
     for k in bench.NCU_TRAFFIC:
         assert bench.traffic_for(k) == bench.NCU_TRAFFIC[k]["bytes_per_launch"] > 0, k
+
+
+def test_both_arms_name_the_same_workload():
+    """The reference arm prints workload_config as it is and the GPU arm
+    with its layout, which defaults to the agent layout: the two configs are
+    equal at every world size, one replica road per rank."""
+    spec = bench.WL.LARGE_ROAD
+    for world in (1, 2, 8):
+        ref = bench.workload_config(spec, world)
+        assert dict(ref, layout="agent") == ref
+        assert (ref["L"], ref["N"], ref["vmax"], ref["p"]) == (2**31, 2**27, 5, 0.13)
+        assert len(ref["road_ids"]) == world and len(set(ref["road_ids"])) == world
+        assert ref["parallelism"] == f"replicas{world}"
