@@ -3,7 +3,8 @@ and the request stream (seed 11, 20000 requests) follow the recipe their
 generator states, and the generator reproduces them: L and T log-uniform on
 [10^3, 10^7] and [10^3, 10^5], density uniform on [0.05, 0.6] with N =
 round(rho L), vmax uniform on {3, 5, 8}, p uniform on [0, 0.5) stored as its
-slowdown threshold, and unit-rate Poisson arrivals."""
+slowdown threshold, and unit-rate Poisson arrivals.  The density sweep's
+roads follow its exact integer rounding."""
 import math
 
 import numpy as np
@@ -69,3 +70,28 @@ def test_generator_reproduces_the_tables(tables):
     arrival = np.rint(np.cumsum(rng.exponential(1.0, len(roads))) * 1e6).astype(np.int64)
     assert np.array_equal(roads, req[:, :6])
     assert np.array_equal(arrival, req[:, 6])
+
+
+def test_density_sweep_roads():
+    """The density sweep: rho_i = 0.02 + 0.88 i / 63 for i = 0..63, N_i =
+    L rho_i rounded half up (computed here with exact rationals), p in
+    {0, 0.13, 0.25, 0.5}, 128 replicas with seeds 1..128, road ids the flat
+    index, density-major."""
+    from fractions import Fraction
+
+    from paper_2309_14311_gb300 import workloads as WL
+
+    roads = WL.fundamental_diagram_roads()
+    assert len(roads) == 64 * 4 * 128
+    assert [r["road_id"] for r in roads] == list(range(len(roads)))
+    for i in range(64):
+        rho = Fraction(2, 100) + Fraction(88, 100) * i / 63
+        want = math.floor(10**6 * rho + Fraction(1, 2))
+        block = roads[i * 512:(i + 1) * 512]
+        assert {r["N"] for r in block} == {want}, i
+        assert [r["p"] for r in block] == [p for p in (0.0, 0.13, 0.25, 0.5) for _ in range(128)]
+        assert [r["seed"] for r in block] == list(range(1, 129)) * 4
+        assert all(r["L"] == 10**6 and r["vmax"] == 5 for r in block)
+    assert roads[0]["N"] == 20000 and roads[-1]["N"] == 900000
+    # a short road rounds half up and stays in [1, L]
+    assert WL.fd_cars(0, 25) == 1 and WL.fd_cars(63, 10) == 9 and WL.fd_cars(0, 1) == 1
